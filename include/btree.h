@@ -1,0 +1,173 @@
+/*
+ * btree.h -- C ABI of libbtree, a GB300 (sm_103a) library for expected values
+ * of path-dependent payoffs over the 2^N Bernoulli paths of a recombinant
+ * binomial tree (Popuri, Raim, Neerchal, Gobbert, arXiv 1701.03512).
+ *
+ * General conventions
+ *   - Every call returns a bt_status and never aborts or throws across the ABI.
+ *     On failure, bt_last_error() returns a thread-local message.
+ *   - Host arrays belong to the caller and are read or written only during
+ *     the call (inputs are copied before the call returns).
+ *   - Device memory is owned by the library (a context allocates it within the
+ *     byte budget given to bt_create; BT_EBUDGET when a call would exceed it).
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the context's own
+ *     stream. Calls that return host results synchronise that stream first.
+ *   - There is no CPU fallback: without a usable GPU, bt_create returns
+ *     BT_ECUDA.
+ *
+ * Notation (the paper's): a path x = (x_1..x_N), 1 = up (Section 1); path
+ * index b in [0,2^N) holds x_t in bit N-t, so x_1 is the most significant bit,
+ * as the rank bits come first in Section 3. S_t = S0 u^{U_t} d^{t-U_t} with
+ * U_t = x_1 + ... + x_t (Algorithm 1), p(x) = p^{U_N}(1-p)^{N-U_N} (Section 2),
+ * V = e^{-qT} sum_x V_N(x) p(x) (eq. f13); the rate q is called `rate`.
+ */
+#ifndef BTREE_H
+#define BTREE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BT_OK = 0,
+    BT_EINVAL = 1,        /* invalid argument (message says which)             */
+    BT_ENOMEM = 2,        /* host or device allocation failed                   */
+    BT_EBUDGET = 3,       /* the context's device byte budget would be exceeded */
+    BT_ECUDA = 4,         /* a CUDA call failed (message carries its error)     */
+    BT_ETIMEOUT = 5,      /* a bounded wait expired                             */
+    BT_EUNSUPPORTED = 6   /* valid input outside what this build supports      */
+} bt_status;
+
+/* Tree parametrisations (Section 2, assumptions A1-A3). */
+typedef enum {
+    BT_TREE_CRR = 0,      /* u = e^{sigma sqrt(dt)}, d = 1/u                     */
+    BT_TREE_SEYDEL = 1,   /* beta = (e^{-q dt} + e^{(q+sigma^2) dt})/2,
+                             u = beta + sqrt(beta^2 - 1), d = 1/u. The paper
+                             prints "+1" under the root; "-1" is the reading that
+                             satisfies A1-A3 with the lognormal second moment and
+                             reproduces the exact values printed in Section 5.  */
+    BT_TREE_EXPLICIT = 2  /* the caller gives u, d = 1/u, p                     */
+} bt_tree_kind;           /* all kinds: p = (e^{q dt} - d)/(u - d) unless EXPLICIT */
+
+/* Payoffs V_N(x). Averages and extremes run over S_1..S_N (Section 5). */
+typedef enum {
+    BT_EURO_CALL = 0,            /* max(S_N - K, 0)              (eq. call)          */
+    BT_EURO_PUT = 1,             /* max(K - S_N, 0)              (eq. put)           */
+    BT_ASIAN_ARITH_CALL = 2,     /* max(A - K, 0), A = (1/N) sum_t S_t              */
+    BT_ASIAN_ARITH_PUT = 3,      /* max(K - A, 0)                (Section 5)         */
+    BT_ASIAN_GEO_CALL = 4,       /* max(G - K, 0), G = exp((1/N) sum_t ln S_t)      */
+    BT_ASIAN_GEO_PUT = 5,        /* max(K - G, 0)                                    */
+    BT_LOOKBACK_FIXED_CALL = 6,  /* max(max_t S_t - K, 0)                            */
+    BT_LOOKBACK_FIXED_PUT = 7    /* max(K - min_t S_t, 0)        (Section 5)         */
+} bt_payoff;
+
+typedef enum {
+    BT_PREC_FP64 = 0,       /* every path in FP64                                    */
+    BT_PREC_FP32_COMP = 1   /* path arithmetic in FP32 on coefficients carried as
+                               FP32 pairs, group sums folded with error-free
+                               transformations, FP64 across blocks                 */
+} bt_precision;
+
+/* One pricing problem. 80 bytes, naturally aligned. */
+typedef struct {
+    int32_t N;          /* tree depth, 1..40 for exact sums, 1..4096 for MC      */
+    int32_t tree_kind;  /* bt_tree_kind                                          */
+    int32_t payoff;     /* bt_payoff                                             */
+    int32_t pad;        /* must be 0                                             */
+    double S0, K, rate, sigma, T;  /* S0 > 0, K >= 0, T > 0, sigma > 0 (unless
+                                      EXPLICIT), all finite                   */
+    double u, d, p;     /* read only for BT_TREE_EXPLICIT: u > 1, d = 1/u, 0<p<1 */
+} bt_option;
+
+typedef struct {
+    double value;       /* discounted value V                                    */
+    double err_est;     /* exact sums: a-priori bound on |V - V_exact| from
+                           rounding; MC: 0                                       */
+    double stderr_mc;   /* MC: standard error of `value`; exact sums: 0          */
+    double var_plain;   /* MC: estimated variance of one undiscounted draw
+                           V(X) (for plain-MC comparisons); exact sums: 0        */
+    int64_t paths;      /* exact: 2^N paths summed; MC: samples drawn            */
+} bt_result;
+
+typedef struct bt_ctx bt_ctx;
+
+/* Library and context ------------------------------------------------------ */
+const char *bt_version(void);
+const char *bt_status_str(bt_status s);
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char *bt_last_error(void);
+
+/* Create a context on CUDA device `device` that may hold up to
+ * `device_budget_bytes` of library-owned device memory (0 = 8 GiB).
+ * BT_ECUDA when no usable device exists. */
+bt_status bt_create(int device, size_t device_budget_bytes, bt_ctx **out);
+void bt_destroy(bt_ctx *ctx);
+/* Device bytes currently held by the context. */
+size_t bt_device_bytes(const bt_ctx *ctx);
+
+/* Section 2, A1-A3: (u, d, p) of one option, computed in FP64 on the host.
+ * BT_EINVAL if p is not in (0,1) or an input is out of range. */
+bt_status bt_tree_params(const bt_option *opt, double *u, double *d, double *p);
+
+/* Exhaustive sums (eq. f13) ------------------------------------------------ */
+/* Prices opts[0..n) exactly: every one of the 2^N paths of each option is
+ * evaluated. Prefix/suffix decomposition: the first P = N - L steps of a path
+ * form its prefix (Section 3's rank bits, eq. f14) and the last L its suffix;
+ * each block of threads sums the paths of a range of prefixes against a
+ * shared-memory suffix table, and block partials are reduced in FP64 in a
+ * fixed order (eq. f15). An arithmetic or geometric Asian or a European call
+ * immediately followed by the put of identical parameters (or the reverse) is
+ * evaluated in one pass over the paths; each still counts its own 2^N paths.
+ * out[0..n) receives the results in input order. Synchronous on `stream`.
+ * Errors: BT_EINVAL (bad option, message names the index), BT_EUNSUPPORTED
+ * (N > 40, or FP32_COMP with min(p,1-p) < 0.004, whose weights leave the FP32
+ * range), BT_EBUDGET, BT_ECUDA. */
+bt_status bt_price_exact(bt_ctx *ctx, const bt_option *opts, int32_t n, bt_precision prec,
+                         bt_result *out, void *stream);
+
+/* A prepared exhaustive pass for repeated runs with the inputs resident on the
+ * device. plan_create validates and copies opts to device memory owned by the
+ * plan and sizes all buffers; plan_run then performs every step on the device
+ * (tree parameters, suffix and prefix tables, the path sums, the reduction);
+ * plan_read copies the results to the host. */
+typedef struct bt_exact_plan bt_exact_plan;
+typedef struct {
+    int32_t n_options;
+    int32_t n_jobs;           /* passes over paths (call/put pairs share one)   */
+    int64_t n_items;          /* work items (block-sized prefix ranges)          */
+    int64_t payoff_paths;     /* sum over options of 2^N                         */
+    int64_t path_evaluations; /* sum over jobs of 2^N                            */
+    size_t device_bytes;      /* device memory held by the plan                  */
+} bt_exact_plan_info;
+
+bt_status bt_exact_plan_create(bt_ctx *ctx, const bt_option *opts, int32_t n, bt_precision prec,
+                               bt_exact_plan **out);
+/* Enqueue one full pass on `stream` (asynchronous; results stay on device). */
+bt_status bt_exact_plan_run(bt_exact_plan *plan, void *stream);
+/* Enqueue the pass restricted to shard `shard` of `n_shards` (work items
+ * i with i % n_shards == shard, the round-robin partition suggested at the
+ * end of Section 3); results then hold this shard's partial values. */
+bt_status bt_exact_plan_run_shard(bt_exact_plan *plan, int32_t shard, int32_t n_shards, void *stream);
+/* Synchronise `stream` and copy results (input order) to out[0..n). */
+bt_status bt_exact_plan_read(bt_exact_plan *plan, bt_result *out, void *stream);
+/* Synchronise and copy per-work-item undiscounted partial sums: partials has
+ * room for 2*n_items doubles (call slot, put slot per item); item_job and
+ * item_first_prefix (may be NULL) receive each item's job index and first
+ * prefix index. Work items of job j cover prefixes [first, first + count) of
+ * that job's 2^P prefixes, all 2^L suffixes each. */
+bt_status bt_exact_plan_partials(bt_exact_plan *plan, double *partials, int32_t *item_job,
+                                 int64_t *item_first_prefix, void *stream);
+/* Job layout: for job j, option indices (call slot, put slot; -1 if unused),
+ * split (P, L) and its number of prefixes per work item. */
+bt_status bt_exact_plan_job(const bt_exact_plan *plan, int32_t j, int32_t *opt_call, int32_t *opt_put,
+                            int32_t *P, int32_t *L, int32_t *prefixes_per_item);
+bt_status bt_exact_plan_info_get(const bt_exact_plan *plan, bt_exact_plan_info *info);
+void bt_exact_plan_destroy(bt_exact_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BTREE_H */

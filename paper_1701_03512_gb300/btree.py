@@ -1,0 +1,233 @@
+"""Python binding of libbtree: the C ABI of include/btree.h, same names.
+
+Argument marshalling only -- every step of the computation runs in the CUDA
+library. Importing this module loads ``lib/libbtree.so`` and raises if it is
+missing: there is no CPU fallback.
+
+Streams: pass ``stream=None`` for the context's own stream, an integer
+``cudaStream_t`` handle, or a ``torch.cuda.Stream`` (its ``cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libbtree.so")
+
+BT_OK, BT_EINVAL, BT_ENOMEM, BT_EBUDGET, BT_ECUDA, BT_ETIMEOUT, BT_EUNSUPPORTED = range(7)
+BT_PREC_FP64, BT_PREC_FP32_COMP = 0, 1
+BT_TREE_CRR, BT_TREE_SEYDEL, BT_TREE_EXPLICIT = 0, 1, 2
+(BT_EURO_CALL, BT_EURO_PUT, BT_ASIAN_ARITH_CALL, BT_ASIAN_ARITH_PUT, BT_ASIAN_GEO_CALL, BT_ASIAN_GEO_PUT,
+ BT_LOOKBACK_FIXED_CALL, BT_LOOKBACK_FIXED_PUT) = range(8)
+
+
+class BtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_status_name(status), msg))
+        self.status = status
+
+
+def _status_name(s):
+    return {0: "BT_OK", 1: "BT_EINVAL", 2: "BT_ENOMEM", 3: "BT_EBUDGET", 4: "BT_ECUDA", 5: "BT_ETIMEOUT",
+            6: "BT_EUNSUPPORTED"}.get(s, "BT_%d" % s)
+
+
+class bt_option(C.Structure):
+    _fields_ = [("N", C.c_int32), ("tree_kind", C.c_int32), ("payoff", C.c_int32), ("pad", C.c_int32),
+                ("S0", C.c_double), ("K", C.c_double), ("rate", C.c_double), ("sigma", C.c_double),
+                ("T", C.c_double), ("u", C.c_double), ("d", C.c_double), ("p", C.c_double)]
+
+
+class bt_result(C.Structure):
+    _fields_ = [("value", C.c_double), ("err_est", C.c_double), ("stderr_mc", C.c_double),
+                ("var_plain", C.c_double), ("paths", C.c_int64)]
+
+
+class bt_exact_plan_info(C.Structure):
+    _fields_ = [("n_options", C.c_int32), ("n_jobs", C.c_int32), ("n_items", C.c_int64),
+                ("payoff_paths", C.c_int64), ("path_evaluations", C.c_int64), ("device_bytes", C.c_size_t)]
+
+
+OPTION_DTYPE = np.dtype([("N", "<i4"), ("tree_kind", "<i4"), ("payoff", "<i4"), ("pad", "<i4"),
+                         ("S0", "<f8"), ("K", "<f8"), ("rate", "<f8"), ("sigma", "<f8"), ("T", "<f8"),
+                         ("u", "<f8"), ("d", "<f8"), ("p", "<f8")])
+RESULT_DTYPE = np.dtype([("value", "<f8"), ("err_est", "<f8"), ("stderr_mc", "<f8"), ("var_plain", "<f8"),
+                         ("paths", "<i8")])
+assert OPTION_DTYPE.itemsize == C.sizeof(bt_option) == 80
+assert RESULT_DTYPE.itemsize == C.sizeof(bt_result) == 40
+
+_lib = None
+_vp, _i32, _i64, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+
+
+def _proto(L, name, args, res=C.c_int):
+    f = getattr(L, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+def lib():
+    """Load libbtree (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libbtree.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        _proto(L, "bt_version", [], C.c_char_p)
+        _proto(L, "bt_status_str", [C.c_int], C.c_char_p)
+        _proto(L, "bt_last_error", [], C.c_char_p)
+        _proto(L, "bt_create", [C.c_int, _sz, C.POINTER(_vp)])
+        _proto(L, "bt_destroy", [_vp], None)
+        _proto(L, "bt_device_bytes", [_vp], _sz)
+        _proto(L, "bt_tree_params", [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)])
+        _proto(L, "bt_price_exact", [_vp, _vp, _i32, C.c_int, _vp, _vp])
+        _proto(L, "bt_exact_plan_create", [_vp, _vp, _i32, C.c_int, C.POINTER(_vp)])
+        _proto(L, "bt_exact_plan_run", [_vp, _vp])
+        _proto(L, "bt_exact_plan_run_shard", [_vp, _i32, _i32, _vp])
+        _proto(L, "bt_exact_plan_read", [_vp, _vp, _vp])
+        _proto(L, "bt_exact_plan_partials", [_vp, _vp, _vp, _vp, _vp])
+        _proto(L, "bt_exact_plan_job", [_vp, _i32, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32),
+                                        C.POINTER(_i32), C.POINTER(_i32)])
+        _proto(L, "bt_exact_plan_info_get", [_vp, C.POINTER(bt_exact_plan_info)])
+        _proto(L, "bt_exact_plan_destroy", [_vp], None)
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != BT_OK:
+        raise BtError(status, lib().bt_last_error().decode())
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def options_array(opts) -> np.ndarray:
+    """List of option dicts (workloads.opt) or a structured array -> bt_option array."""
+    if isinstance(opts, np.ndarray) and opts.dtype == OPTION_DTYPE:
+        return np.ascontiguousarray(opts)
+    if isinstance(opts, dict):
+        opts = [opts]
+    a = np.zeros(len(opts), dtype=OPTION_DTYPE)
+    for i, o in enumerate(opts):
+        for k in ("N", "tree_kind", "payoff", "S0", "K", "rate", "sigma", "T", "u", "d", "p"):
+            a[i][k] = o.get(k, 0)
+    return a
+
+
+# --- same names as the C ABI -------------------------------------------------
+def bt_version() -> str:
+    return lib().bt_version().decode()
+
+
+def bt_create(device: int = 0, device_budget_bytes: int = 0):
+    h = _vp()
+    _check(lib().bt_create(device, device_budget_bytes, C.byref(h)))
+    return h
+
+
+def bt_destroy(ctx):
+    lib().bt_destroy(ctx)
+
+
+def bt_device_bytes(ctx) -> int:
+    return lib().bt_device_bytes(ctx)
+
+
+def bt_tree_params(opt):
+    a = options_array(opt)
+    u, d, p = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().bt_tree_params(a.ctypes.data, C.byref(u), C.byref(d), C.byref(p)))
+    return u.value, d.value, p.value
+
+
+def bt_price_exact(ctx, opts, prec=BT_PREC_FP32_COMP, stream=None) -> np.ndarray:
+    a = options_array(opts)
+    out = np.zeros(len(a), dtype=RESULT_DTYPE)
+    _check(lib().bt_price_exact(ctx, a.ctypes.data, len(a), prec, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def bt_exact_plan_create(ctx, opts, prec=BT_PREC_FP32_COMP):
+    a = options_array(opts)
+    h = _vp()
+    _check(lib().bt_exact_plan_create(ctx, a.ctypes.data, len(a), prec, C.byref(h)))
+    return h
+
+
+def bt_exact_plan_run(plan, stream=None):
+    _check(lib().bt_exact_plan_run(plan, _stream(stream)))
+
+
+def bt_exact_plan_run_shard(plan, shard, n_shards, stream=None):
+    _check(lib().bt_exact_plan_run_shard(plan, shard, n_shards, _stream(stream)))
+
+
+def bt_exact_plan_info_get(plan) -> dict:
+    i = bt_exact_plan_info()
+    _check(lib().bt_exact_plan_info_get(plan, C.byref(i)))
+    return {k: getattr(i, k) for k, _ in bt_exact_plan_info._fields_}
+
+
+def bt_exact_plan_read(plan, stream=None) -> np.ndarray:
+    n = bt_exact_plan_info_get(plan)["n_options"]
+    out = np.zeros(n, dtype=RESULT_DTYPE)
+    _check(lib().bt_exact_plan_read(plan, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def bt_exact_plan_partials(plan, stream=None):
+    n = bt_exact_plan_info_get(plan)["n_items"]
+    part = np.zeros((n, 2))
+    job = np.zeros(n, dtype=np.int32)
+    first = np.zeros(n, dtype=np.int64)
+    _check(lib().bt_exact_plan_partials(plan, part.ctypes.data, job.ctypes.data, first.ctypes.data,
+                                        _stream(stream)))
+    return part, job, first
+
+
+def bt_exact_plan_job(plan, j):
+    vals = [_i32() for _ in range(5)]
+    _check(lib().bt_exact_plan_job(plan, j, *[C.byref(v) for v in vals]))
+    keys = ("opt_call", "opt_put", "P", "L", "prefixes_per_item")
+    return {k: v.value for k, v in zip(keys, vals)}
+
+
+def bt_exact_plan_destroy(plan):
+    lib().bt_exact_plan_destroy(plan)
+
+
+class Context:
+    """Owns a bt_ctx; a convenience over the same-name functions."""
+
+    def __init__(self, device: int = 0, device_budget_bytes: int = 0):
+        self.h = bt_create(device, device_budget_bytes)
+
+    def close(self):
+        if self.h:
+            bt_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def price_exact(self, opts, prec=BT_PREC_FP32_COMP, stream=None):
+        return bt_price_exact(self.h, opts, prec, stream)

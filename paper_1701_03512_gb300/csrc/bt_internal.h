@@ -1,0 +1,105 @@
+// Internal layout shared by the host runtime and the CUDA kernels of libbtree.
+// Not part of the public ABI (that is include/btree.h).
+#pragma once
+#include <stdint.h>
+
+#include "../../include/btree.h"
+
+#define BT_MAX_N_EXACT 40
+#define BT_MAX_L 12            // suffix steps held in a shared-memory table
+#define BT_LOW_BITS 11         // a work item covers 2^11 consecutive prefixes
+#define BT_THREADS 256         // threads per block of the path-sum kernels
+#define BT_PT 8                // prefixes per thread (FP32 kernel): 256 * 8 = 2^11
+#define BT_PT64 8              // prefixes per thread (FP64 kernel)
+#define BT_UNROLL 4            // suffix groups are padded to a multiple of this
+#define BT_SUF_MAX ((1 << BT_MAX_L) + (BT_MAX_L + 1) * (BT_UNROLL - 1))
+#define BT_LVL_NONE 30000      // sentinel level: "no price in this block"
+
+// What the suffix table of a job holds (one field per job).
+enum bt_field {
+    BT_F_ARITH = 0,   // f_s = sum_{j=1}^{L} u^{l'_j}         (relative partial sum)
+    BT_F_GEO = 1,     // f_s = u^{D_s/N}, D_s = sum_j l'_j    (relative geometric factor)
+    BT_F_EURO = 2,    // f_s = u^{l'_L}                       (relative end price)
+    BT_F_LOOKMAX = 3, // f_s = u^{max_j l'_j}                 (relative running max)
+    BT_F_LOOKMIN = 4  // f_s = u^{min_j l'_j}                 (relative running min)
+};
+enum bt_mode { BT_MODE_CALL = 1, BT_MODE_PUT = 2, BT_MODE_BOTH = 3 };
+
+// One pass over the 2^N paths of one option (possibly two payoffs).
+struct bt_job {
+    int32_t opt;              // option index (numeric inputs)
+    int32_t out_call, out_put;// result slots of the call / put payoff, -1 if none
+    int32_t N, L, P, H, M;    // N = P + L, P = H + M
+    int32_t field, mode;
+    int32_t suf_len;          // padded suffix table length
+    int32_t goff[BT_MAX_L + 2];
+    int32_t geo_imin, geo_len;
+    int32_t n_items;          // ceil(2^P / 2^11)
+    int32_t pad0;
+    int64_t item_begin;       // first global work item of this job
+    int64_t off_suf;          // element offset in the suffix arena
+    int64_t off_ph, off_pm;   // entry offsets in the prefix-table arena
+    int64_t off_pow, off_geo; // entry offsets in the power-table arena
+};
+
+struct bt_pentry {            // one entry of a two-level prefix table
+    double R64;               // backward-relative partial sum (see tables.cu)
+    float R_hi, R_lo;
+    int16_t lvl, mx, mn, D;   // end level, max level, min level, level sum
+    int32_t pad[2];
+};
+
+struct bt_pow {               // u^e for some exponent e, in FP64 and as an FP32 pair
+    double v;
+    float hi, lo;
+};
+
+// Numeric parameters of a job, computed on the device from the option (a1).
+struct bt_jparams {
+    double u, d, p, disc, lnu;
+    double S0, K;
+    double NKoS0, KoS0, S0oN;
+    double fmin, fmax;
+    double W[BT_MAX_L + 1];          // suffix-group weights p^k (1-p)^{L-k}
+    double wl[BT_LOW_BITS + 1];      // p^c (1-p)^{Plo-c}, Plo = min(P, 11)
+    double wh[BT_MAX_N_EXACT + 1];   // p^c (1-p)^{Phi-c}, Phi = P - Plo
+    float2 W2[BT_MAX_L + 1];         // FP32 pairs of the above
+    float2 wl2[BT_LOW_BITS + 1];
+    float2 NKoS0_2, KoS0_2, S0oN_2, S0_2, K_2;
+    float fmin_f, fmax_f;
+    int32_t ok;                      // 0 if the device found p outside (0,1)
+    int32_t pad;
+};
+
+struct bt_exact_args {
+    const bt_option *opts;
+    const bt_job *jobs;
+    const bt_jparams *prm;
+    int32_t n_jobs;
+    int32_t shard, n_shards;
+    int32_t pad;
+    int64_t n_run_items;      // items executed by this launch
+    const float2 *suf32;
+    const double *suf64;
+    const bt_pentry *ph;
+    const bt_pentry *pm;
+    const bt_pow *pw;
+    double2 *partials;        // per global work item: (call slot, put slot)
+    unsigned long long *counter;
+};
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+// Kernel launchers (exact.cu). Each returns a cudaError_t as int.
+int bt_launch_params(const bt_option *d_opts, const bt_job *d_jobs, bt_jparams *d_prm, int n_jobs,
+                     void *stream);
+int bt_launch_tables(const bt_job *d_jobs, const bt_jparams *d_prm, int n_jobs, int max_len, int prec,
+                     float2 *suf32, double *suf64, bt_pentry *ph, bt_pentry *pm, bt_pow *pw, void *stream);
+int bt_launch_exact(const bt_exact_args *a, int prec, int grid, void *stream);
+int bt_launch_finalize(const bt_job *d_jobs, const bt_jparams *d_prm, int n_jobs, const double2 *partials,
+                       int shard, int n_shards, int prec, bt_result *d_out, void *stream);
+int bt_exact_grid_size(int prec, int device);
+#ifdef __cplusplus
+}
+#endif

@@ -1,0 +1,779 @@
+// Exhaustive expected value over all 2^N Bernoulli paths (eq. f13), sm_103a.
+//
+// A path index b of an N-step tree splits into a prefix (the first P = N - L
+// steps, the high bits -- Section 3's rank bits) and a suffix (the last L
+// steps). With u d = 1 (A1) and levels l_t = 2 U_t - t, S_t = S0 u^{l_t}, every
+// payoff here is, for a fixed prefix, an affine function of one per-suffix
+// number f_s:
+//     payoff(prefix, suffix) = beta_p * max(+-(tau_p + f_s), 0) + C_p
+// (tau_p, beta_p, C_p from the prefix; the sign selects call or put). The path
+// weight factorises as p(x) = w_p * w_s with w_s = p^k (1-p)^{L-k} depending
+// only on the suffix's up-count k. So one block of threads holds the suffix
+// table (sorted by k) in shared memory, each thread holds eight prefixes in
+// registers, and every path costs one FP32 FMA for tau + f (scaled), one FMA
+// for the low-order correction, one saturating add for max(., 0) and one add
+// into the group sum. Group sums are folded with the weight w(k) by
+// error-free transformations, prefixes are combined in FP32 pairs, and the
+// block's total goes to FP64 (eq. f14); block partials are added in a fixed
+// order per option (eq. f15).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bt_internal.h"
+#include "df.cuh"
+
+// ---------------------------------------------------------------------------
+// a1: tree parameters (Section 2, A1-A3) on the device
+// ---------------------------------------------------------------------------
+__device__ static int dev_tree(const bt_option &o, double *u, double *d, double *p) {
+    double dt = o.T / (double)o.N;
+    double uu;
+    if (o.tree_kind == BT_TREE_CRR) {
+        uu = exp(o.sigma * sqrt(dt));
+    } else if (o.tree_kind == BT_TREE_SEYDEL) {
+        double beta = 0.5 * (exp(-o.rate * dt) + exp((o.rate + o.sigma * o.sigma) * dt));
+        uu = beta + sqrt(beta * beta - 1.0);
+    } else {
+        *u = o.u;
+        *d = o.d;
+        *p = o.p;
+        return o.p > 0.0 && o.p < 1.0;
+    }
+    double dd = 1.0 / uu;
+    double pp = (exp(o.rate * dt) - dd) / (uu - dd);
+    *u = uu;
+    *d = dd;
+    *p = pp;
+    return pp > 0.0 && pp < 1.0;
+}
+
+__device__ static double ipow(double x, int n) {
+    double r = 1.0;
+    for (int i = 0; i < n; ++i) r *= x;
+    return r;
+}
+
+__global__ void k_params(const bt_option *opts, const bt_job *jobs, bt_jparams *prm, int n_jobs) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_jobs) return;
+    const bt_job J = jobs[j];
+    const bt_option o = opts[J.opt];
+    bt_jparams P;
+    memset(&P, 0, sizeof(P));
+    P.ok = dev_tree(o, &P.u, &P.d, &P.p);
+    P.disc = exp(-o.rate * o.T);
+    P.lnu = log(P.u);
+    P.S0 = o.S0;
+    P.K = o.K;
+    P.NKoS0 = (double)J.N * o.K / o.S0;
+    P.KoS0 = o.K / o.S0;
+    P.S0oN = o.S0 / (double)J.N;
+    const double u = P.u, lnu = P.lnu;
+    const int L = J.L;
+    switch (J.field) {
+    case BT_F_ARITH: {
+        double a = 0.0, b = 0.0, ru = 1.0, rd = 1.0;
+        for (int i = 1; i <= L; ++i) {
+            ru *= u;
+            rd *= P.d;
+            a += rd;
+            b += ru;
+        }
+        P.fmin = a;
+        P.fmax = b;
+        break;
+    }
+    case BT_F_GEO: {
+        double e = (double)L * (double)(L + 1) / (2.0 * (double)J.N);
+        P.fmin = exp(-e * lnu);
+        P.fmax = exp(e * lnu);
+        break;
+    }
+    case BT_F_EURO:
+        P.fmin = exp(-(double)L * lnu);
+        P.fmax = exp((double)L * lnu);
+        break;
+    case BT_F_LOOKMAX:
+        P.fmin = exp(-lnu);
+        P.fmax = exp((double)L * lnu);
+        break;
+    default:
+        P.fmin = exp(-(double)L * lnu);
+        P.fmax = exp(lnu);
+        break;
+    }
+    const double p = P.p, q = 1.0 - P.p;
+    for (int k = 0; k <= L; ++k) {
+        P.W[k] = ipow(p, k) * ipow(q, L - k);
+        P.W2[k] = split2(P.W[k]);
+    }
+    const int plo = J.P < BT_LOW_BITS ? J.P : BT_LOW_BITS;
+    const int phi = J.P - plo;
+    for (int c = 0; c <= plo; ++c) {
+        P.wl[c] = ipow(p, c) * ipow(q, plo - c);
+        P.wl2[c] = split2(P.wl[c]);
+    }
+    for (int c = 0; c <= phi; ++c) P.wh[c] = pow(p, (double)c) * pow(q, (double)(phi - c));
+    P.NKoS0_2 = split2(P.NKoS0);
+    P.KoS0_2 = split2(P.KoS0);
+    P.S0oN_2 = split2(P.S0oN);
+    P.S0_2 = split2(P.S0);
+    P.K_2 = split2(P.K);
+    P.fmin_f = (float)P.fmin;
+    P.fmax_f = (float)P.fmax;
+    prm[j] = P;
+}
+
+// ---------------------------------------------------------------------------
+// a2/a3: suffix table (sorted by up-count, groups padded with NaN) and the
+// two-level prefix tables, in FP64
+// ---------------------------------------------------------------------------
+__device__ static int binom_small(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    int r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+// Rank of a k-subset among all k-subsets in colexicographic order (the
+// combinatorial number system): sum over the i-th set bit c_i of C(c_i, i).
+__device__ static int colex_rank(unsigned s) {
+    int r = 0, i = 0;
+    while (s) {
+        int c = __ffs(s) - 1;
+        ++i;
+        r += binom_small(c, i);
+        s &= s - 1;
+    }
+    return r;
+}
+
+// Walk `bits` steps of `x` (MSB first) from level 0 and return the block's
+// summary: end level, max/min level, level sum and the backward-relative
+// partial sum R = sum_t u^{l_t - l_end} (R_t = R_{t-1} * u^{-(l_t - l_{t-1})} + 1).
+__device__ static bt_pentry walk_block(uint64_t x, int bits, double u, double d) {
+    bt_pentry e;
+    int lvl = 0, mx = -BT_LVL_NONE, mn = BT_LVL_NONE, D = 0;
+    double R = 0.0;
+    for (int t = 1; t <= bits; ++t) {
+        int up = (int)((x >> (bits - t)) & 1u);
+        lvl += up ? 1 : -1;
+        R = R * (up ? d : u) + 1.0;
+        mx = lvl > mx ? lvl : mx;
+        mn = lvl < mn ? lvl : mn;
+        D += lvl;
+    }
+    e.R64 = R;
+    float2 r2 = split2(R);
+    e.R_hi = r2.x;
+    e.R_lo = r2.y;
+    e.lvl = (int16_t)lvl;
+    e.mx = (int16_t)mx;
+    e.mn = (int16_t)mn;
+    e.D = (int16_t)D;
+    e.pad[0] = e.pad[1] = 0;
+    return e;
+}
+
+__global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, float2 *suf32, double *suf64,
+                         bt_pentry *ph, bt_pentry *pm, bt_pow *pw) {
+    const int j = blockIdx.y;
+    const bt_job J = jobs[j];
+    const double u = prm[j].u, d = prm[j].d, lnu = prm[j].lnu;
+    const int64_t nsuf = 1ll << J.L, nh = 1ll << J.H, nm = 1ll << J.M;
+    const int64_t npow = 2 * J.N + 3;
+    const int64_t total = nsuf + J.suf_len + nh + nm + npow + J.geo_len;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx;
+        if (i < nsuf) {  // suffix entry
+            unsigned s = (unsigned)i;
+            int k = __popc(s);
+            int lvl = 0, mx = -BT_LVL_NONE, mn = BT_LVL_NONE, D = 0;
+            double r = 1.0, f = 0.0;
+            for (int t = 1; t <= J.L; ++t) {
+                int up = (int)((s >> (J.L - t)) & 1u);
+                lvl += up ? 1 : -1;
+                r *= up ? u : d;
+                f += r;
+                D += lvl;
+                mx = lvl > mx ? lvl : mx;
+                mn = lvl < mn ? lvl : mn;
+            }
+            double v;
+            switch (J.field) {
+            case BT_F_ARITH: v = f; break;
+            case BT_F_GEO: v = exp((double)D * lnu / (double)J.N); break;
+            case BT_F_EURO: v = exp((double)lvl * lnu); break;
+            case BT_F_LOOKMAX: v = exp((double)mx * lnu); break;
+            default: v = exp((double)mn * lnu); break;
+            }
+            int pos = J.goff[k] + colex_rank(s);
+            if (prec == BT_PREC_FP64) {
+                suf64[J.off_suf + pos] = v;
+            } else {
+                float2 h = split2(v);
+                suf32[J.off_suf + pos] = make_float2(h.x, -h.y);  // (f_hi, -f_lo)
+            }
+            continue;
+        }
+        i -= nsuf;
+        if (i < J.suf_len) {  // padding slots of each up-count group
+            int pos = (int)i, k = 0;
+            while (k < J.L && pos >= J.goff[k + 1]) ++k;
+            if (pos - J.goff[k] >= binom_small(J.L, k)) {
+                if (prec == BT_PREC_FP64) suf64[J.off_suf + pos] = nan("");
+                else suf32[J.off_suf + pos] = make_float2(__int_as_float(0x7fc00000), 0.0f);
+            }
+            continue;
+        }
+        i -= J.suf_len;
+        if (i < nh) {
+            ph[J.off_ph + i] = walk_block((uint64_t)i, J.H, u, d);
+            continue;
+        }
+        i -= nh;
+        if (i < nm) {
+            pm[J.off_pm + i] = walk_block((uint64_t)i, J.M, u, d);
+            continue;
+        }
+        i -= nm;
+        bt_pow e;
+        if (i < npow) {
+            e.v = exp((double)(i - (J.N + 1)) * lnu);
+            float2 h = split2(e.v);
+            e.hi = h.x;
+            e.lo = h.y;
+            pw[J.off_pow + i] = e;
+            continue;
+        }
+        i -= npow;
+        e.v = exp((double)(J.geo_imin + i) * lnu / (double)J.N);
+        float2 h = split2(e.v);
+        e.hi = h.x;
+        e.lo = h.y;
+        pw[J.off_geo + i] = e;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3 (per prefix) and a4: the path sums
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df32 pw2(const bt_pow *t, int e) {
+    bt_pow v = t[e];
+    return df_make(v.hi, v.lo);
+}
+
+struct pref32 {
+    float B, Ah, nAl;
+    df32 om;   // w_low * beta * 2^e
+    df32 cst;  // w_low * C (lookback)
+};
+
+// Per-prefix affine coefficients: y = B * (tau + f) with B = 2^-e chosen so that
+// |y| <= 1 over the whole suffix range, so that max(y, 0) is a saturating add.
+__device__ __forceinline__ pref32 prefix32(const bt_job &J, const bt_jparams &P, const bt_exact_args &a,
+                                           int64_t q, bool valid) {
+    pref32 r;
+    if (!valid) {
+        r.B = 0.0f;
+        r.Ah = __int_as_float(0x7fc00000);
+        r.nAl = r.Ah;
+        r.om = df_make(0.0f, 0.0f);
+        r.cst = df_make(0.0f, 0.0f);
+        return r;
+    }
+    const int64_t h = q >> J.M;
+    const int m = (int)(q & ((1ll << J.M) - 1));
+    const bt_pentry eh = a.ph[J.off_ph + h];
+    const bt_pentry em = a.pm[J.off_pm + m];
+    const int lvl = eh.lvl + em.lvl;
+    const bt_pow *pw = a.pw + J.off_pow + J.N + 1;
+    df32 tau, beta, cst = df_make(0.0f, 0.0f);
+    switch (J.field) {
+    case BT_F_ARITH: {
+        // tau = Sigma_P / S_P - N K / S_P, Sigma_P / S_P = u^{-Delta_m} R_h + R_m
+        df32 Rp = df_add(df_mul(pw2(pw, -em.lvl), df_make(eh.R_hi, eh.R_lo)), df_make(em.R_hi, em.R_lo));
+        df32 X = df_mul(df_from2(P.NKoS0_2), pw2(pw, -lvl));
+        tau = df_sub(Rp, X);
+        beta = df_mul(df_from2(P.S0oN_2), pw2(pw, lvl));
+        break;
+    }
+    case BT_F_EURO:
+        tau = df_neg(df_mul(df_from2(P.KoS0_2), pw2(pw, -lvl)));
+        beta = df_mul(df_from2(P.S0_2), pw2(pw, lvl));
+        break;
+    case BT_F_GEO: {
+        const int I = (int)eh.D + J.M * (int)eh.lvl + (int)em.D + J.L * lvl;
+        const bt_pow *g = a.pw + J.off_geo - J.geo_imin;
+        tau = df_neg(df_mul(df_from2(P.KoS0_2), pw2(g, -I)));
+        beta = df_mul(df_from2(P.S0_2), pw2(g, I));
+        break;
+    }
+    case BT_F_LOOKMAX: {
+        const int lam = max((int)eh.mx, (int)eh.lvl + (int)em.mx);
+        df32 kk = df_mul(df_from2(P.KoS0_2), pw2(pw, -lvl));
+        if (lam > -BT_LVL_NONE / 2) {
+            // tau = -max(M_P, K) / S_P,  C = max(M_P - K, 0)
+            df32 rr = pw2(pw, lam - lvl);
+            tau = df_neg(df_gt(rr, kk) ? rr : kk);
+            df32 c = df_sub(df_mul(df_from2(P.S0_2), pw2(pw, lam)), df_from2(P.K_2));
+            if (c.hi > 0.0f) cst = c;
+        } else {
+            tau = df_neg(kk);
+        }
+        beta = df_mul(df_from2(P.S0_2), pw2(pw, lvl));
+        break;
+    }
+    default: {  // BT_F_LOOKMIN
+        const int lam = min((int)eh.mn, (int)eh.lvl + (int)em.mn);
+        df32 kk = df_mul(df_from2(P.KoS0_2), pw2(pw, -lvl));
+        if (lam < BT_LVL_NONE / 2) {
+            // tau = -min(m_P, K) / S_P,  C = max(K - m_P, 0)
+            df32 rr = pw2(pw, lam - lvl);
+            tau = df_neg(df_gt(rr, kk) ? kk : rr);
+            df32 c = df_sub(df_from2(P.K_2), df_mul(df_from2(P.S0_2), pw2(pw, lam)));
+            if (c.hi > 0.0f) cst = c;
+        } else {
+            tau = df_neg(kk);
+        }
+        beta = df_mul(df_from2(P.S0_2), pw2(pw, lvl));
+        break;
+    }
+    }
+    float m1 = fabsf(__fadd_rn(tau.hi, P.fmin_f)), m2 = fabsf(__fadd_rn(tau.hi, P.fmax_f));
+    float mmax = fmaxf(m1, m2) * (1.0f + 0x1p-10f);
+    int e = ((__float_as_int(mmax) >> 23) & 0xff) - 126;  // mmax < 2^e
+    e = max(-120, min(120, e));
+    r.B = __int_as_float((127 - e) << 23);
+    r.Ah = tau.hi * r.B;
+    r.nAl = -tau.lo * r.B;
+    const int c = __popc((unsigned)(q & ((1 << BT_LOW_BITS) - 1)));
+    r.om = df_ldexp(df_mul(df_from2(P.wl2[c]), beta), e);
+    r.cst = df_mul(df_from2(P.wl2[c]), cst);
+    return r;
+}
+
+struct __align__(16) smem_job {
+    bt_job J;
+    bt_jparams P;
+    int64_t item;
+    int job;
+};
+
+__device__ static int find_job(const bt_job *jobs, int n_jobs, int64_t item) {
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].item_begin <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Deterministic block sum of two doubles; result valid in thread 0.
+__device__ __forceinline__ double2 block_sum2(double x, double y, double2 *red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[w] = make_double2(x, y);
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < BT_THREADS / 32; ++i) {
+            r.x += red[i].x;
+            r.y += red[i].y;
+        }
+    }
+    return r;
+}
+
+// Loads the next work item and (if it changed) its job into shared memory.
+// Returns false when the run has no items left.
+template <typename SufT>
+__device__ __forceinline__ bool next_item(const bt_exact_args &a, smem_job &sj, SufT *s_suf, const SufT *g_suf,
+                                          int &cur_job) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long i = atomicAdd(a.counter, 1ull);
+        sj.item = (i < (unsigned long long)a.n_run_items) ? (int64_t)a.shard + (int64_t)i * a.n_shards : -1;
+        if (sj.item >= 0) sj.job = find_job(a.jobs, a.n_jobs, sj.item);
+    }
+    __syncthreads();
+    if (sj.item < 0) return false;
+    if (sj.job != cur_job) {
+        cur_job = sj.job;
+        if (threadIdx.x == 0) {
+            sj.J = a.jobs[cur_job];
+            sj.P = a.prm[cur_job];
+        }
+        __syncthreads();
+        const SufT *src = g_suf + sj.J.off_suf;
+        for (int i = threadIdx.x; i < sj.J.suf_len; i += BT_THREADS) s_suf[i] = src[i];
+        __syncthreads();
+    }
+    return true;
+}
+
+template <int MODE>
+__device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &sj, const float2 *s_suf,
+                                       double2 *red) {
+    const bt_job &J = sj.J;
+    const bt_jparams &P = sj.P;
+    const int64_t item_local = sj.item - J.item_begin;
+    const int64_t qbase = item_local << BT_LOW_BITS;
+    const int64_t nP = 1ll << J.P;
+
+    float B[BT_PT], Ah[BT_PT], nAl[BT_PT];
+    df32 om[BT_PT];
+    df32 cst = df_make(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) {
+        const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
+        pref32 pr = prefix32(J, P, a, q, q < nP);
+        B[j] = pr.B;
+        Ah[j] = pr.Ah;
+        nAl[j] = pr.nAl;
+        om[j] = pr.om;
+        cst = df_add_pos(cst, pr.cst);
+    }
+    df32 accC[BT_PT], accP[BT_PT];
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) accC[j] = accP[j] = df_make(0.0f, 0.0f);
+
+    for (int k = 0; k <= J.L; ++k) {
+        const int s0 = J.goff[k], s1 = J.goff[k + 1];
+        float gc[BT_PT], gp[BT_PT];
+#pragma unroll
+        for (int j = 0; j < BT_PT; ++j) gc[j] = gp[j] = 0.0f;
+        for (int s = s0; s < s1; s += BT_UNROLL) {
+            const float4 fa = *reinterpret_cast<const float4 *>(s_suf + s);
+            const float4 fb = *reinterpret_cast<const float4 *>(s_suf + s + 2);
+#pragma unroll
+            for (int j = 0; j < BT_PT; ++j) {
+                // y = B (tau_hi + f_hi), c = -B (tau_lo + f_lo); payoff/beta = sat(y - c)
+                const float y0 = __fmaf_rn(B[j], fa.x, Ah[j]), c0 = __fmaf_rn(B[j], fa.y, nAl[j]);
+                const float y1 = __fmaf_rn(B[j], fa.z, Ah[j]), c1 = __fmaf_rn(B[j], fa.w, nAl[j]);
+                const float y2 = __fmaf_rn(B[j], fb.x, Ah[j]), c2 = __fmaf_rn(B[j], fb.y, nAl[j]);
+                const float y3 = __fmaf_rn(B[j], fb.z, Ah[j]), c3 = __fmaf_rn(B[j], fb.w, nAl[j]);
+                if (MODE & BT_MODE_CALL) {
+                    const float z = __fadd_rn(__fadd_rn(__saturatef(__fsub_rn(y0, c0)), __saturatef(__fsub_rn(y1, c1))),
+                                              __fadd_rn(__saturatef(__fsub_rn(y2, c2)), __saturatef(__fsub_rn(y3, c3))));
+                    gc[j] = __fadd_rn(gc[j], z);
+                }
+                if (MODE & BT_MODE_PUT) {
+                    const float z = __fadd_rn(__fadd_rn(__saturatef(__fsub_rn(c0, y0)), __saturatef(__fsub_rn(c1, y1))),
+                                              __fadd_rn(__saturatef(__fsub_rn(c2, y2)), __saturatef(__fsub_rn(c3, y3))));
+                    gp[j] = __fadd_rn(gp[j], z);
+                }
+            }
+        }
+        const df32 w = df_from2(P.W2[k]);
+#pragma unroll
+        for (int j = 0; j < BT_PT; ++j) {
+            if (MODE & BT_MODE_CALL) accC[j] = df_add_pos(accC[j], df_mul_f(w, gc[j]));
+            if (MODE & BT_MODE_PUT) accP[j] = df_add_pos(accP[j], df_mul_f(w, gp[j]));
+        }
+    }
+    df32 totC = df_make(0.0f, 0.0f), totP = df_make(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) {
+        if (MODE & BT_MODE_CALL) totC = df_add_pos(totC, df_mul(om[j], accC[j]));
+        if (MODE & BT_MODE_PUT) totP = df_add_pos(totP, df_mul(om[j], accP[j]));
+    }
+    double vc = df_to_double(totC), vp = df_to_double(totP);
+    if (J.field == BT_F_LOOKMAX) vc += df_to_double(cst);
+    if (J.field == BT_F_LOOKMIN) vp += df_to_double(cst);
+    double2 s = block_sum2(vc, vp, red);
+    if (threadIdx.x == 0) {
+        const double wh = P.wh[__popcll((unsigned long long)item_local)];
+        a.partials[sj.item] = make_double2(s.x * wh, s.y * wh);
+    }
+}
+
+__global__ void __launch_bounds__(BT_THREADS, 2) k_exact32(bt_exact_args a) {
+    extern __shared__ float4 smem_raw[];
+    float2 *s_suf = reinterpret_cast<float2 *>(smem_raw);
+    __shared__ smem_job sj;
+    __shared__ double2 red[BT_THREADS / 32];
+    int cur_job = -1;
+    while (next_item<float2>(a, sj, s_suf, a.suf32, cur_job)) {
+        switch (sj.J.mode) {
+        case BT_MODE_CALL: item32<BT_MODE_CALL>(a, sj, s_suf, red); break;
+        case BT_MODE_PUT: item32<BT_MODE_PUT>(a, sj, s_suf, red); break;
+        default: item32<BT_MODE_BOTH>(a, sj, s_suf, red); break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// All-FP64 variant (the accuracy reference kernel): the same decomposition
+// with every step in double precision.
+// ---------------------------------------------------------------------------
+struct pref64 {
+    double tau, om, cst;
+};
+
+__device__ __forceinline__ pref64 prefix64(const bt_job &J, const bt_jparams &P, const bt_exact_args &a,
+                                           int64_t q, bool valid) {
+    pref64 r;
+    if (!valid) {
+        r.tau = nan("");
+        r.om = 0.0;
+        r.cst = 0.0;
+        return r;
+    }
+    const int64_t h = q >> J.M;
+    const int m = (int)(q & ((1ll << J.M) - 1));
+    const bt_pentry eh = a.ph[J.off_ph + h];
+    const bt_pentry em = a.pm[J.off_pm + m];
+    const int lvl = eh.lvl + em.lvl;
+    const bt_pow *pw = a.pw + J.off_pow + J.N + 1;
+    double tau, beta, cst = 0.0;
+    switch (J.field) {
+    case BT_F_ARITH:
+        tau = fma(pw[-em.lvl].v, eh.R64, em.R64) - P.NKoS0 * pw[-lvl].v;
+        beta = P.S0oN * pw[lvl].v;
+        break;
+    case BT_F_EURO:
+        tau = -P.KoS0 * pw[-lvl].v;
+        beta = P.S0 * pw[lvl].v;
+        break;
+    case BT_F_GEO: {
+        const int I = (int)eh.D + J.M * (int)eh.lvl + (int)em.D + J.L * lvl;
+        const bt_pow *g = a.pw + J.off_geo - J.geo_imin;
+        tau = -P.KoS0 * g[-I].v;
+        beta = P.S0 * g[I].v;
+        break;
+    }
+    case BT_F_LOOKMAX: {
+        const int lam = max((int)eh.mx, (int)eh.lvl + (int)em.mx);
+        const double kk = P.KoS0 * pw[-lvl].v;
+        if (lam > -BT_LVL_NONE / 2) {
+            tau = -fmax(pw[lam - lvl].v, kk);
+            cst = fmax(P.S0 * pw[lam].v - P.K, 0.0);
+        } else {
+            tau = -kk;
+        }
+        beta = P.S0 * pw[lvl].v;
+        break;
+    }
+    default: {
+        const int lam = min((int)eh.mn, (int)eh.lvl + (int)em.mn);
+        const double kk = P.KoS0 * pw[-lvl].v;
+        if (lam < BT_LVL_NONE / 2) {
+            tau = -fmin(pw[lam - lvl].v, kk);
+            cst = fmax(P.K - P.S0 * pw[lam].v, 0.0);
+        } else {
+            tau = -kk;
+        }
+        beta = P.S0 * pw[lvl].v;
+        break;
+    }
+    }
+    const int c = __popc((unsigned)(q & ((1 << BT_LOW_BITS) - 1)));
+    r.tau = tau;
+    r.om = P.wl[c] * beta;
+    r.cst = P.wl[c] * cst;
+    return r;
+}
+
+template <int MODE>
+__device__ __forceinline__ void item64(const bt_exact_args &a, const smem_job &sj, const double *s_suf,
+                                       double2 *red) {
+    const bt_job &J = sj.J;
+    const bt_jparams &P = sj.P;
+    const int64_t item_local = sj.item - J.item_begin;
+    const int64_t qbase = item_local << BT_LOW_BITS;
+    const int64_t nP = 1ll << J.P;
+    double tau[BT_PT64], om[BT_PT64], cst = 0.0;
+#pragma unroll
+    for (int j = 0; j < BT_PT64; ++j) {
+        const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
+        pref64 pr = prefix64(J, P, a, q, q < nP);
+        tau[j] = pr.tau;
+        om[j] = pr.om;
+        cst += pr.cst;
+    }
+    double accC[BT_PT64], accP[BT_PT64];
+#pragma unroll
+    for (int j = 0; j < BT_PT64; ++j) accC[j] = accP[j] = 0.0;
+    for (int k = 0; k <= J.L; ++k) {
+        const int s0 = J.goff[k], s1 = J.goff[k + 1];
+        double gc[BT_PT64], gp[BT_PT64];
+#pragma unroll
+        for (int j = 0; j < BT_PT64; ++j) gc[j] = gp[j] = 0.0;
+        for (int s = s0; s < s1; ++s) {
+            const double f = s_suf[s];
+#pragma unroll
+            for (int j = 0; j < BT_PT64; ++j) {
+                const double y = tau[j] + f;
+                // NaN (padding or a masked prefix) contributes nothing
+                if (MODE & BT_MODE_CALL) gc[j] += y > 0.0 ? y : 0.0;
+                if (MODE & BT_MODE_PUT) gp[j] += y < 0.0 ? -y : 0.0;
+            }
+        }
+        const double w = P.W[k];
+#pragma unroll
+        for (int j = 0; j < BT_PT64; ++j) {
+            accC[j] = fma(w, gc[j], accC[j]);
+            accP[j] = fma(w, gp[j], accP[j]);
+        }
+    }
+    double vc = 0.0, vp = 0.0;
+#pragma unroll
+    for (int j = 0; j < BT_PT64; ++j) {
+        vc = fma(om[j], accC[j], vc);
+        vp = fma(om[j], accP[j], vp);
+    }
+    if (J.field == BT_F_LOOKMAX) vc += cst;
+    if (J.field == BT_F_LOOKMIN) vp += cst;
+    double2 s = block_sum2(vc, vp, red);
+    if (threadIdx.x == 0) {
+        const double wh = P.wh[__popcll((unsigned long long)item_local)];
+        a.partials[sj.item] = make_double2(s.x * wh, s.y * wh);
+    }
+}
+
+__global__ void __launch_bounds__(BT_THREADS, 2) k_exact64(bt_exact_args a) {
+    extern __shared__ double smem_d[];
+    __shared__ smem_job sj;
+    __shared__ double2 red[BT_THREADS / 32];
+    int cur_job = -1;
+    while (next_item<double>(a, sj, smem_d, a.suf64, cur_job)) {
+        switch (sj.J.mode) {
+        case BT_MODE_CALL: item64<BT_MODE_CALL>(a, sj, smem_d, red); break;
+        case BT_MODE_PUT: item64<BT_MODE_PUT>(a, sj, smem_d, red); break;
+        default: item64<BT_MODE_BOTH>(a, sj, smem_d, red); break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a5: per-option reduction of the block partials in a fixed order (eq. f15)
+// ---------------------------------------------------------------------------
+struct neu {
+    double s, c;
+};
+__device__ __forceinline__ void neu_add(neu &a, double x) {
+    double t = a.s + x;
+    if (fabs(a.s) >= fabs(x)) a.c += (a.s - t) + x;
+    else a.c += (x - t) + a.s;
+    a.s = t;
+}
+
+__global__ void k_finalize(const bt_job *jobs, const bt_jparams *prm, int n_jobs, const double2 *partials,
+                           int prec, bt_result *out) {
+    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= n_jobs) return;
+    const bt_job J = jobs[j];
+    neu c = {0.0, 0.0}, p = {0.0, 0.0};
+    for (int i = lane; i < J.n_items; i += 32) {
+        double2 v = partials[J.item_begin + i];
+        neu_add(c, v.x);
+        neu_add(p, v.y);
+    }
+    // fixed-shape tree over lanes
+    for (int o = 16; o > 0; o >>= 1) {
+        double cs = __shfl_down_sync(0xffffffffu, c.s, o), cc = __shfl_down_sync(0xffffffffu, c.c, o);
+        double ps = __shfl_down_sync(0xffffffffu, p.s, o), pc = __shfl_down_sync(0xffffffffu, p.c, o);
+        neu_add(c, cs);
+        c.c += cc;
+        neu_add(p, ps);
+        p.c += pc;
+    }
+    if (lane == 0) {
+        const double disc = prm[j].disc;
+        const double rel = prec == BT_PREC_FP64 ? 1e-13 : 1e-9;
+        const int64_t paths = 1ll << J.N;
+        if (J.out_call >= 0) {
+            bt_result r;
+            r.value = disc * (c.s + c.c);
+            r.err_est = rel * fabs(r.value);
+            r.stderr_mc = 0.0;
+            r.var_plain = 0.0;
+            r.paths = paths;
+            out[J.out_call] = r;
+        }
+        if (J.out_put >= 0) {
+            bt_result r;
+            r.value = disc * (p.s + p.c);
+            r.err_est = rel * fabs(r.value);
+            r.stderr_mc = 0.0;
+            r.var_plain = 0.0;
+            r.paths = paths;
+            out[J.out_put] = r;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+extern "C" int bt_launch_params(const bt_option *d_opts, const bt_job *d_jobs, bt_jparams *d_prm, int n_jobs,
+                                void *stream) {
+    if (n_jobs <= 0) return 0;
+    k_params<<<(n_jobs + 63) / 64, 64, 0, (cudaStream_t)stream>>>(d_opts, d_jobs, d_prm, n_jobs);
+    return (int)cudaGetLastError();
+}
+
+extern "C" int bt_launch_tables(const bt_job *d_jobs, const bt_jparams *d_prm, int n_jobs, int max_len, int prec,
+                                float2 *suf32, double *suf64, bt_pentry *ph, bt_pentry *pm, bt_pow *pw,
+                                void *stream) {
+    if (n_jobs <= 0) return 0;
+    int bx = (max_len + 255) / 256;
+    if (bx > 64) bx = 64;
+    if (bx < 1) bx = 1;
+    dim3 grid(bx, n_jobs);
+    k_tables<<<grid, 256, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, prec, suf32, suf64, ph, pm, pw);
+    return (int)cudaGetLastError();
+}
+
+static size_t exact_smem(int prec) {
+    return prec == BT_PREC_FP64 ? (size_t)BT_SUF_MAX * sizeof(double) : (size_t)BT_SUF_MAX * sizeof(float2);
+}
+
+extern "C" int bt_exact_grid_size(int prec, int device) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    size_t sm = exact_smem(prec);
+    if (prec == BT_PREC_FP64) {
+        cudaFuncSetAttribute(k_exact64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_exact64, BT_THREADS, sm);
+    } else {
+        cudaFuncSetAttribute(k_exact32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_exact32, BT_THREADS, sm);
+    }
+    if (per < 1) per = 1;
+    if (sms < 1) sms = 1;
+    return sms * per;
+}
+
+extern "C" int bt_launch_exact(const bt_exact_args *a, int prec, int grid, void *stream) {
+    if (a->n_run_items <= 0) return 0;
+    if ((int64_t)grid > a->n_run_items) grid = (int)a->n_run_items;
+    size_t sm = exact_smem(prec);
+    if (prec == BT_PREC_FP64) {
+        cudaFuncSetAttribute(k_exact64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_exact64<<<grid, BT_THREADS, sm, (cudaStream_t)stream>>>(*a);
+    } else {
+        cudaFuncSetAttribute(k_exact32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_exact32<<<grid, BT_THREADS, sm, (cudaStream_t)stream>>>(*a);
+    }
+    return (int)cudaGetLastError();
+}
+
+extern "C" int bt_launch_finalize(const bt_job *d_jobs, const bt_jparams *d_prm, int n_jobs, const double2 *partials,
+                                  int shard, int n_shards, int prec, bt_result *d_out, void *stream) {
+    (void)shard;
+    (void)n_shards;
+    if (n_jobs <= 0) return 0;
+    const int warps = 4;
+    k_finalize<<<(n_jobs + warps - 1) / warps, 32 * warps, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, n_jobs,
+                                                                                       partials, prec, d_out);
+    return (int)cudaGetLastError();
+}

@@ -1,0 +1,29 @@
+// Host-side declarations shared by the runtime's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <vector>
+
+#include "bt_internal.h"
+
+struct bt_ctx {
+    int device;
+    size_t budget;
+    std::atomic<size_t> used;
+    cudaStream_t stream;
+    int n_sm;
+    int grid32, grid64;
+};
+
+bt_status bt_fail(bt_status s, const char *fmt, ...);
+bt_status bt_cuda_fail(int err, const char *what);
+bt_status ctx_alloc(bt_ctx *c, size_t bytes, void **p);
+void ctx_free(bt_ctx *c, void *p, size_t bytes);
+cudaStream_t ctx_stream(bt_ctx *c, void *s);
+bt_status host_tree(const bt_option *o, double *u, double *d, double *p);
+bt_status validate_option(const bt_option *o, int idx, int max_n);
+int exact_split_L(int N);
+void fill_job_shape(bt_job &J, int N, int field, int mode);
+bt_status plan_jobs(const bt_option *opts, int n, int prec, std::vector<bt_job> &jobs, int64_t *n_items,
+                    int64_t *payoff_paths, int64_t *path_evals, int max_n);

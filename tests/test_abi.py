@@ -1,0 +1,105 @@
+"""CPU-side checks of the boundary: the library builds, loads and exports
+every symbol the public header declares; host-only entry points behave; no
+kernel is launched."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1701_03512_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bt():
+    from paper_1701_03512_gb300 import build as b
+    b.build()
+    from paper_1701_03512_gb300 import btree
+    btree.lib()
+    return btree
+
+
+def _declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"\b(bt_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = _declared_functions()
+    for must in ("bt_create", "bt_destroy", "bt_price_exact", "bt_exact_plan_run", "bt_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(bt):
+    L = ctypes.CDLL(bt.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_struct_layout(bt):
+    assert ctypes.sizeof(bt.bt_option) == 80
+    assert ctypes.sizeof(bt.bt_result) == 40
+
+
+def test_status_strings(bt):
+    L = bt.lib()
+    assert L.bt_status_str(0) == b"BT_OK"
+    assert L.bt_status_str(3) == b"BT_EBUDGET"
+    assert b"sm_103a" in L.bt_version()
+
+
+def test_tree_params_host(bt):
+    """bt_tree_params runs on the host; it agrees with the oracle's tree."""
+    from oracle import py_oracle as O
+    for kind in (W.TREE_CRR, W.TREE_SEYDEL):
+        o = W.opt(32, 20.0, 100.0, 0.06, 3.0, 1.0, W.ASIAN_ARITH_PUT, kind)
+        u, d, p = bt.bt_tree_params(o)
+        uo, do, po = O.tree(kind, 32, 3.0, 0.06, 1.0)
+        assert (u, d, p) == pytest.approx((uo, do, po), rel=1e-15)
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (dict(S0=-1.0), "S0"), (dict(T=0.0), "T must"), (dict(sigma=0.0), "sigma"),
+    (dict(K=float("nan")), "non-finite"), (dict(payoff=9), "payoff"), (dict(tree_kind=7), "tree_kind"),
+    (dict(sigma=0.001, rate=0.5), "not in (0,1)"),
+])
+def test_tree_params_rejects(bt, bad, msg):
+    o = dict(W.opt(20, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL), **bad)
+    with pytest.raises(bt.BtError) as e:
+        bt.bt_tree_params(o)
+    assert e.value.status == bt.BT_EINVAL and msg in str(e.value)
+
+
+def test_explicit_tree_needs_ud_one(bt):
+    o = W.opt(5, 100.0, 100.0, 0.0, 0.2, 1.0, W.EURO_CALL, W.TREE_EXPLICIT, u=1.1, d=0.9, p=0.5)
+    with pytest.raises(bt.BtError):
+        bt.bt_tree_params(o)
+    o = W.opt(5, 100.0, 100.0, 0.0, 0.2, 1.0, W.EURO_CALL, W.TREE_EXPLICIT, u=1.1, d=1 / 1.1, p=0.5)
+    assert bt.bt_tree_params(o) == (1.1, 1 / 1.1, 0.5)
+
+
+def test_create_without_gpu_fails_cleanly(bt):
+    """No GPU in this container: bt_create must fail with BT_ECUDA, not crash."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(bt.BtError) as e:
+        bt.bt_create(0)
+    assert e.value.status == bt.BT_ECUDA
+
+
+def test_options_array_roundtrip(bt):
+    opts = W.batched_exact_workload(32, 0, 4)
+    a = bt.options_array(opts)
+    assert a.shape == (8,) and a["N"].tolist() == [32] * 8
+    assert a["payoff"].tolist() == [2, 3] * 4
+    assert np.allclose(a["S0"][::2], W.option_sets(0, 4)["S0"])

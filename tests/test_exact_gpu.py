@@ -1,0 +1,221 @@
+"""GPU parity of the exhaustive sums (eq. f13) against the CPU oracle.
+
+Tolerances: FP64 kernel 1e-12 relative; FP32_COMP kernel 1e-9 relative plus an
+absolute floor of 1e-12 * S0 for values that are (nearly) zero, where a
+relative bound has no meaning. All calls go through the C ABI.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1701_03512_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-9}   # BT_PREC_FP64, BT_PREC_FP32_COMP
+
+
+@pytest.fixture(scope="module")
+def bt():
+    from paper_1701_03512_gb300 import build as b
+    b.build()
+    from paper_1701_03512_gb300 import btree
+    return btree
+
+
+@pytest.fixture(scope="module")
+def ctx(bt):
+    c = bt.Context(0)
+    yield c
+    c.close()
+
+
+def _check(got, ref, opts, prec, what=""):
+    got = np.asarray(got, dtype=float)
+    ref = np.asarray(ref, dtype=float)
+    s0 = np.array([o["S0"] for o in opts])
+    err = np.abs(got - ref)
+    bound = TOL[prec] * np.abs(ref) + 1e-12 * s0
+    bad = np.nonzero(~(err <= bound))[0]
+    assert bad.size == 0, "%s prec=%d: %s" % (what, prec, [(int(i), opts[i]["payoff"], opts[i]["N"], got[i], ref[i],
+                                                           err[i] / max(abs(ref[i]), 1e-300)) for i in bad[:8]])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_asian_n20(bt, ctx, oracle, prec):
+    """One arithmetic-average Asian call, N=20, CRR, S0=K=100, r=5%, sigma=20%, T=1."""
+    o = W.single_asian_n20()
+    ref = oracle.price_exhaustive(o, 8)
+    r = ctx.price_exact([o], prec)
+    _check(r["value"], [ref], [o], prec, "N=20")
+    assert r["paths"][0] == 2 ** 20
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_all_payoffs_small_trees(bt, ctx, oracle, prec):
+    """Every payoff, N = 1..16, three tree kinds, against plain enumeration."""
+    opts = []
+    rng = np.random.default_rng(7)
+    for N in list(range(1, 17)):
+        for pay in range(8):
+            kind = [W.TREE_CRR, W.TREE_SEYDEL, W.TREE_EXPLICIT][(N + pay) % 3]
+            S0, K = rng.uniform(80, 120, 2)
+            if kind == W.TREE_EXPLICIT:
+                u = 1.0 + rng.uniform(0.01, 0.08)
+                opts.append(W.opt(N, S0, K, 0.03, 0.2, 1.0, pay, kind, u=u, d=1.0 / u, p=rng.uniform(0.3, 0.7)))
+            else:
+                opts.append(W.opt(N, S0, K, rng.uniform(0, 0.08), rng.uniform(0.1, 0.5), rng.uniform(0.25, 2), pay, kind))
+    ref = [oracle.price_exhaustive(o, 8) for o in opts]
+    r = ctx.price_exact(opts, prec)
+    _check(r["value"], ref, opts, prec, "small")
+    assert r["paths"].tolist() == [2 ** o["N"] for o in opts]
+
+
+def test_two_step_worked_example(bt, ctx, golden_dir):
+    import json, os
+    g = json.load(open(os.path.join(golden_dir, "n2_worked_example.json")))
+    t = g["tree"]
+    names = list(g["values"])
+    opts = [W.opt(2, t["S0"], t["K"], t["rate"], 0.2, t["T"],
+                  [k for k, v in W.PAYOFF_NAMES.items() if v == n][0], W.TREE_EXPLICIT, u=t["u"], d=t["d"], p=t["p"])
+            for n in names]
+    for prec in (0, 1):
+        got = ctx.price_exact(opts, prec)["value"]
+        assert np.allclose(got, [g["values"][n] for n in names], rtol=TOL[prec], atol=1e-13), (prec, got)
+
+
+def test_paper_exact_values(bt, ctx, golden_dir):
+    """The Section 5 exact values (N=32, Seydel) from the GPU path."""
+    import json, os
+    g = json.load(open(os.path.join(golden_dir, "paper_section5_exact.json")))
+    c = g["common"]
+    opts = [W.opt(c["N"], c["S0"], c["K"], c["rate"], c["sigma"], c["T"], W.ASIAN_ARITH_PUT, W.TREE_SEYDEL),
+            W.opt(c["N"], c["S0"], c["K"], c["rate"], c["sigma"], c["T"], W.LOOKBACK_FIXED_PUT, W.TREE_SEYDEL)]
+    got = ctx.price_exact(opts, 1)["value"]
+    assert abs(got[0] - g["values"]["asian_arith_put"]) <= 5e-4
+    assert abs(got[1] - g["values"]["lookback_fixed_put"]) <= 5e-4
+
+
+@pytest.mark.parametrize("N", [11, 12, 22, 23, 24, 26])
+def test_split_boundaries(bt, ctx, oracle, N):
+    """Around the prefix/suffix split changes (L grows until 12, P crosses 11)."""
+    opts = W.batch(N, W.option_sets(N, 2), list(range(8)))
+    ref = [oracle.exact(o) if N > 18 else oracle.price_exhaustive(o, 8) for o in opts]
+    for prec in (0, 1):
+        _check(ctx.price_exact(opts, prec)["value"], ref, opts, prec, "N=%d" % N)
+
+
+def test_call_put_pair_matches_singles(bt, ctx):
+    """A fused call/put pass gives bit-identical values to separate passes."""
+    sets = W.option_sets(3, 3)
+    pair = W.batch(24, sets, (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT))
+    calls = [o for o in pair if o["payoff"] == W.ASIAN_ARITH_CALL]
+    puts = [o for o in pair if o["payoff"] == W.ASIAN_ARITH_PUT]
+    for prec in (0, 1):
+        rp = ctx.price_exact(pair, prec)["value"]
+        rc = ctx.price_exact(calls, prec)["value"]
+        rq = ctx.price_exact(puts, prec)["value"]
+        assert np.array_equal(rp[0::2], rc) and np.array_equal(rp[1::2], rq)
+
+
+def test_deterministic_alone_and_batched(bt, ctx):
+    opts = W.random_options(11, 24, 10, 28)
+    for prec in (0, 1):
+        a = ctx.price_exact(opts, prec)["value"]
+        b = ctx.price_exact(opts, prec)["value"]
+        assert np.array_equal(a, b)
+        for i in (0, 5, 17):
+            assert ctx.price_exact([opts[i]], prec)["value"][0] == a[i]
+
+
+def test_work_item_partials_against_enumeration(bt, ctx, oracle):
+    """Sampled work items of an N=32 pass: each covers a contiguous range of
+    path indices, whose sum the oracle enumerates directly (eq. f14)."""
+    opts = W.batched_exact_workload(32, 0, 2)[:2] + [W.opt(32, 100.0, 95.0, 0.04, 0.3, 1.0, W.LOOKBACK_FIXED_CALL)]
+    for prec in (0, 1):
+        plan = bt.bt_exact_plan_create(ctx.h, opts, prec)
+        try:
+            bt.bt_exact_plan_run(plan)
+            part, job, first = bt.bt_exact_plan_partials(plan)
+            for item in (0, 137, len(job) - 1):
+                jd = bt.bt_exact_plan_job(plan, int(job[item]))
+                L = jd["L"]
+                lo = int(first[item]) << L
+                hi = (int(first[item]) + jd["prefixes_per_item"]) << L
+                for slot, oi in ((0, jd["opt_call"]), (1, jd["opt_put"])):
+                    if oi < 0:
+                        continue
+                    ref = oracle.sum_range(opts[oi], lo, hi)
+                    got = part[item, slot]
+                    assert abs(got - ref) <= TOL[prec] * abs(ref) + 1e-15 * opts[oi]["S0"], (prec, item, slot, got, ref)
+        finally:
+            bt.bt_exact_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("N", [32, 36])
+def test_batched_workload_full_size(bt, ctx, oracle, N):
+    """The batched workload (64 sets, arithmetic Asian call and put) at full
+    size against the exact meet-in-the-middle oracle, FP32_COMP kernel."""
+    opts = W.batched_exact_workload(N, 0, 64)
+    ref = [oracle.asian_mitm(o, N // 2) for o in opts]
+    r = ctx.price_exact(opts, 1)
+    _check(r["value"], ref, opts, 1, "N=%d" % N)
+    rel = np.abs(r["value"] - ref) / np.maximum(np.abs(ref), 1e-300)
+    print("N=%d max rel err %.3g (values > 1e-6): %.3g" % (N, rel.max(), rel[np.abs(ref) > 1e-6].max()))
+
+
+def test_batched_workload_fp64_n32(bt, ctx, oracle):
+    opts = W.batched_exact_workload(32, 0, 64)
+    ref = [oracle.asian_mitm(o, 16) for o in opts]
+    _check(ctx.price_exact(opts, 0)["value"], ref, opts, 0, "fp64 N=32")
+
+
+@pytest.mark.parametrize("N", [30, 36])
+def test_geometric_and_lookback_full_size(bt, ctx, oracle, N):
+    sets = W.option_sets(5, 6)
+    opts = W.batch(N, sets, (W.ASIAN_GEO_CALL, W.ASIAN_GEO_PUT, W.LOOKBACK_FIXED_CALL, W.LOOKBACK_FIXED_PUT))
+    ref = [oracle.exact(o) for o in opts]
+    _check(ctx.price_exact(opts, 1)["value"], ref, opts, 1, "geo/lookback N=%d" % N)
+
+
+def test_shards_add_up(bt, ctx):
+    opts = W.random_options(21, 10, 18, 30)
+    for prec in (0, 1):
+        plan = bt.bt_exact_plan_create(ctx.h, opts, prec)
+        try:
+            bt.bt_exact_plan_run(plan)
+            full = bt.bt_exact_plan_read(plan)["value"]
+            tot = np.zeros(len(opts))
+            for s in range(3):
+                bt.bt_exact_plan_run_shard(plan, s, 3)
+                tot += bt.bt_exact_plan_read(plan)["value"]
+            assert np.allclose(tot, full, rtol=1e-14, atol=0)
+        finally:
+            bt.bt_exact_plan_destroy(plan)
+
+
+def test_invalid_inputs(bt, ctx):
+    good = W.single_asian_n20()
+    with pytest.raises(bt.BtError) as e:
+        ctx.price_exact([good, dict(good, N=41)], 1)
+    assert e.value.status == bt.BT_EUNSUPPORTED
+    with pytest.raises(bt.BtError) as e:
+        ctx.price_exact([good, dict(good, S0=0.0)], 1)
+    assert e.value.status == bt.BT_EINVAL and "option 1" in str(e.value)
+    o = W.opt(10, 100.0, 100.0, 0.0, 0.2, 1.0, W.EURO_CALL, W.TREE_EXPLICIT, u=1.2, d=1 / 1.2, p=0.001)
+    with pytest.raises(bt.BtError) as e:
+        ctx.price_exact([o], 1)
+    assert e.value.status == bt.BT_EUNSUPPORTED
+    assert ctx.price_exact([o], 0)["value"][0] >= 0.0
+
+
+def test_budget_is_enforced(bt):
+    c = bt.Context(0, device_budget_bytes=1 << 20)
+    try:
+        with pytest.raises(bt.BtError) as e:
+            c.price_exact(W.batched_exact_workload(36, 0, 4), 1)
+        assert e.value.status == bt.BT_EBUDGET
+        assert bt.bt_device_bytes(c.h) == 0
+    finally:
+        c.close()
