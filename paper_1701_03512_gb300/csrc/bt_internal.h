@@ -7,11 +7,11 @@
 
 #define BT_MAX_N_EXACT 40
 #define BT_MAX_L 12            // suffix steps held in a shared-memory table
-#define BT_LOW_BITS 11         // a work item covers 2^11 consecutive prefixes
+#define BT_LOW_BITS 10         // a work item covers 2^10 consecutive prefixes
 #define BT_THREADS 256         // threads per block of the path-sum kernels
-#define BT_PT 8                // prefixes per thread (FP32 kernel): 256 * 8 = 2^11
-#define BT_PT64 8              // prefixes per thread (FP64 kernel)
-#define BT_UNROLL 4            // suffix groups are padded to a multiple of this
+#define BT_PT 4                // prefixes per thread (FP32 kernel): 256 * 4 = 2^10
+#define BT_PT64 4              // prefixes per thread (FP64 kernel)
+#define BT_UNROLL 8            // suffix groups are padded to a multiple of this
 #define BT_SUF_MAX ((1 << BT_MAX_L) + (BT_MAX_L + 1) * (BT_UNROLL - 1))
 #define BT_LVL_NONE 30000      // sentinel level: "no price in this block"
 
@@ -34,7 +34,7 @@ struct bt_job {
     int32_t suf_len;          // padded suffix table length
     int32_t goff[BT_MAX_L + 2];
     int32_t geo_imin, geo_len;
-    int32_t n_items;          // ceil(2^P / 2^11)
+    int32_t n_items;          // ceil(2^P / 2^BT_LOW_BITS)
     int32_t pad0;
     int64_t item_begin;       // first global work item of this job
     int64_t off_suf;          // element offset in the suffix arena
@@ -61,14 +61,14 @@ struct bt_jparams {
     double NKoS0, KoS0, S0oN;
     double fmin, fmax;
     double W[BT_MAX_L + 1];          // suffix-group weights p^k (1-p)^{L-k}
-    double wl[BT_LOW_BITS + 1];      // p^c (1-p)^{Plo-c}, Plo = min(P, 11)
+    double wl[BT_LOW_BITS + 1];      // p^c (1-p)^{Plo-c}, Plo = min(P, BT_LOW_BITS)
     double wh[BT_MAX_N_EXACT + 1];   // p^c (1-p)^{Phi-c}, Phi = P - Plo
     float2 W2[BT_MAX_L + 1];         // FP32 pairs of the above
     float2 wl2[BT_LOW_BITS + 1];
     float2 NKoS0_2, KoS0_2, S0oN_2, S0_2, K_2;
     float fmin_f, fmax_f;
+    int32_t gexp;                    // FP32 split grid of f: f_hi is a multiple of 2^gexp
     int32_t ok;                      // 0 if the device found p outside (0,1)
-    int32_t pad;
 };
 
 struct bt_exact_args {

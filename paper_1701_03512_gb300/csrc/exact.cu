@@ -9,13 +9,26 @@
 // (tau_p, beta_p, C_p from the prefix; the sign selects call or put). The path
 // weight factorises as p(x) = w_p * w_s with w_s = p^k (1-p)^{L-k} depending
 // only on the suffix's up-count k. So one block of threads holds the suffix
-// table (sorted by k) in shared memory, each thread holds eight prefixes in
-// registers, and every path costs one FP32 FMA for tau + f (scaled), one FMA
-// for the low-order correction, one saturating add for max(., 0) and one add
-// into the group sum. Group sums are folded with the weight w(k) by
+// table (sorted by k) in shared memory, each thread holds four prefixes in
+// registers, and every path costs one FP32 FMA for lambda (tau + f), one FMA
+// for the low-order correction, one saturating add for max(., 0) and its
+// share of an eight-wide addition tree. Each tree's sum enters the group sum
+// through TwoSum (compensated), group sums are folded with the weight w(k) by
 // error-free transformations, prefixes are combined in FP32 pairs, and the
 // block's total goes to FP64 (eq. f14); block partials are added in a fixed
 // order per option (eq. f15).
+//
+// Rounding design of the FP32 path. The per-prefix scale lambda = 2^-e
+// (256 - h)/256, with 2^e bounding |tau + f| over the suffix range and h a
+// 7-bit hash of the prefix index, keeps |lambda (tau + f)| <= 1 so that
+// max(., 0) is a saturating add. The suffix table stores f_hi on the fixed grid
+// 2^gexp (gexp = ceil(log2 max f) - 10, at most 10 significant bits) and the
+// exact remainder f_lo; the prefix rounds A = lambda tau to the grid
+// 2^(gexp - e - 8). Then lambda f_hi + A_hi is exact in
+// FP32 on every path, and the only rounding of the payoff is one
+// correctly-rounded FP32 result -- unbiased, unlike a rounding of a rounded
+// value. The hash makes prefixes that share tau (the structured payoffs) scale
+// differently, so those single roundings also average out across prefixes.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -122,6 +135,9 @@ __global__ void k_params(const bt_option *opts, const bt_job *jobs, bt_jparams *
     P.K_2 = split2(P.K);
     P.fmin_f = (float)P.fmin;
     P.fmax_f = (float)P.fmax;
+    int ef;
+    frexp(P.fmax, &ef);  // fmax <= 2^ef
+    P.gexp = ef - 10;
     prm[j] = P;
 }
 
@@ -213,8 +229,10 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
             if (prec == BT_PREC_FP64) {
                 suf64[J.off_suf + pos] = v;
             } else {
-                float2 h = split2(v);
-                suf32[J.off_suf + pos] = make_float2(h.x, -h.y);  // (f_hi, -f_lo)
+                // f_hi on the grid 2^gexp (exact in FP32), f_lo the exact remainder
+                const int gx = prm[j].gexp;
+                const double fh = ldexp(rint(ldexp(v, -gx)), gx);
+                suf32[J.off_suf + pos] = make_float2((float)fh, -(float)(v - fh));  // (f_hi, -f_lo)
             }
             continue;
         }
@@ -346,11 +364,21 @@ __device__ __forceinline__ pref32 prefix32(const bt_job &J, const bt_jparams &P,
     float mmax = fmaxf(m1, m2) * (1.0f + 0x1p-10f);
     int e = ((__float_as_int(mmax) >> 23) & 0xff) - 126;  // mmax < 2^e
     e = max(-120, min(120, e));
-    r.B = __int_as_float((127 - e) << 23);
-    r.Ah = tau.hi * r.B;
-    r.nAl = -tau.lo * r.B;
+    const unsigned hd = ((unsigned)q * 0x9E3779B1u) >> 25;        // 7-bit dither
+    const float lam = ldexpf((float)(256u - hd) * 0x1p-8f, -e);    // 9-bit mantissa, exact
+    r.B = lam;
+    const df32 A = df_mul_f(tau, lam);
+    // A_hi on the grid 2^(gexp - e - 8): lambda f_hi + A_hi is then exact in FP32
+    const int gq = P.gexp - e - 8;
+    const float Ah = ldexpf(rintf(ldexpf(A.hi, -gq)), gq);
+    r.Ah = Ah;
+    r.nAl = -__fadd_rn(__fsub_rn(A.hi, Ah), A.lo);
+    // 1/lambda as an FP32 pair: r0 = rcp, correction from the exact residual 1 - lam r0
+    const float r0 = 1.0f / lam;
+    const float res = __fmaf_rn(-lam, r0, 1.0f);
+    const df32 rinv = fast_two_sum(r0, r0 * res);
     const int c = __popc((unsigned)(q & ((1 << BT_LOW_BITS) - 1)));
-    r.om = df_ldexp(df_mul(df_from2(P.wl2[c]), beta), e);
+    r.om = df_mul(df_mul(df_from2(P.wl2[c]), beta), rinv);
     r.cst = df_mul(df_from2(P.wl2[c]), cst);
     return r;
 }
@@ -446,36 +474,56 @@ __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &s
 
     for (int k = 0; k <= J.L; ++k) {
         const int s0 = J.goff[k], s1 = J.goff[k + 1];
-        float gc[BT_PT], gp[BT_PT];
+        // group sums as (sum, compensation) pairs
+        float gc[BT_PT], ec[BT_PT], gp[BT_PT], ep[BT_PT];
 #pragma unroll
-        for (int j = 0; j < BT_PT; ++j) gc[j] = gp[j] = 0.0f;
+        for (int j = 0; j < BT_PT; ++j) gc[j] = ec[j] = gp[j] = ep[j] = 0.0f;
         for (int s = s0; s < s1; s += BT_UNROLL) {
-            const float4 fa = *reinterpret_cast<const float4 *>(s_suf + s);
-            const float4 fb = *reinterpret_cast<const float4 *>(s_suf + s + 2);
+            float4 f4[BT_UNROLL / 2];
+#pragma unroll
+            for (int i = 0; i < BT_UNROLL / 2; ++i) f4[i] = *reinterpret_cast<const float4 *>(s_suf + s + 2 * i);
 #pragma unroll
             for (int j = 0; j < BT_PT; ++j) {
-                // y = B (tau_hi + f_hi), c = -B (tau_lo + f_lo); payoff/beta = sat(y - c)
-                const float y0 = __fmaf_rn(B[j], fa.x, Ah[j]), c0 = __fmaf_rn(B[j], fa.y, nAl[j]);
-                const float y1 = __fmaf_rn(B[j], fa.z, Ah[j]), c1 = __fmaf_rn(B[j], fa.w, nAl[j]);
-                const float y2 = __fmaf_rn(B[j], fb.x, Ah[j]), c2 = __fmaf_rn(B[j], fb.y, nAl[j]);
-                const float y3 = __fmaf_rn(B[j], fb.z, Ah[j]), c3 = __fmaf_rn(B[j], fb.w, nAl[j]);
+                // y = lambda (tau_hi + f_hi), c = -lambda (tau_lo + f_lo); payoff/beta = sat(y - c)/lambda
+                float y[BT_UNROLL], c[BT_UNROLL];
+#pragma unroll
+                for (int i = 0; i < BT_UNROLL / 2; ++i) {
+                    y[2 * i] = __fmaf_rn(B[j], f4[i].x, Ah[j]);
+                    c[2 * i] = __fmaf_rn(B[j], f4[i].y, nAl[j]);
+                    y[2 * i + 1] = __fmaf_rn(B[j], f4[i].z, Ah[j]);
+                    c[2 * i + 1] = __fmaf_rn(B[j], f4[i].w, nAl[j]);
+                }
                 if (MODE & BT_MODE_CALL) {
-                    const float z = __fadd_rn(__fadd_rn(__saturatef(__fsub_rn(y0, c0)), __saturatef(__fsub_rn(y1, c1))),
-                                              __fadd_rn(__saturatef(__fsub_rn(y2, c2)), __saturatef(__fsub_rn(y3, c3))));
-                    gc[j] = __fadd_rn(gc[j], z);
+                    float z[BT_UNROLL];
+#pragma unroll
+                    for (int i = 0; i < BT_UNROLL; ++i) z[i] = __saturatef(__fsub_rn(y[i], c[i]));
+#pragma unroll
+                    for (int w = 1; w < BT_UNROLL; w *= 2)
+#pragma unroll
+                        for (int i = 0; i < BT_UNROLL; i += 2 * w) z[i] = __fadd_rn(z[i], z[i + w]);
+                    const float sN = __fadd_rn(gc[j], z[0]);  // Fast2Sum (|gc| >= |z0| after the first add)
+                    ec[j] = __fadd_rn(ec[j], __fsub_rn(z[0], __fsub_rn(sN, gc[j])));
+                    gc[j] = sN;
                 }
                 if (MODE & BT_MODE_PUT) {
-                    const float z = __fadd_rn(__fadd_rn(__saturatef(__fsub_rn(c0, y0)), __saturatef(__fsub_rn(c1, y1))),
-                                              __fadd_rn(__saturatef(__fsub_rn(c2, y2)), __saturatef(__fsub_rn(c3, y3))));
-                    gp[j] = __fadd_rn(gp[j], z);
+                    float z[BT_UNROLL];
+#pragma unroll
+                    for (int i = 0; i < BT_UNROLL; ++i) z[i] = __saturatef(__fsub_rn(c[i], y[i]));
+#pragma unroll
+                    for (int w = 1; w < BT_UNROLL; w *= 2)
+#pragma unroll
+                        for (int i = 0; i < BT_UNROLL; i += 2 * w) z[i] = __fadd_rn(z[i], z[i + w]);
+                    const float sN = __fadd_rn(gp[j], z[0]);
+                    ep[j] = __fadd_rn(ep[j], __fsub_rn(z[0], __fsub_rn(sN, gp[j])));
+                    gp[j] = sN;
                 }
             }
         }
         const df32 w = df_from2(P.W2[k]);
 #pragma unroll
         for (int j = 0; j < BT_PT; ++j) {
-            if (MODE & BT_MODE_CALL) accC[j] = df_add_pos(accC[j], df_mul_f(w, gc[j]));
-            if (MODE & BT_MODE_PUT) accP[j] = df_add_pos(accP[j], df_mul_f(w, gp[j]));
+            if (MODE & BT_MODE_CALL) accC[j] = df_add_pos(accC[j], df_mul(w, fast_two_sum(gc[j], ec[j])));
+            if (MODE & BT_MODE_PUT) accP[j] = df_add_pos(accP[j], df_mul(w, fast_two_sum(gp[j], ep[j])));
         }
     }
     df32 totC = df_make(0.0f, 0.0f), totP = df_make(0.0f, 0.0f);

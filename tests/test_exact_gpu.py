@@ -1,8 +1,13 @@
 """GPU parity of the exhaustive sums (eq. f13) against the CPU oracle.
 
-Tolerances: FP64 kernel 1e-12 relative; FP32_COMP kernel 1e-9 relative plus an
-absolute floor of 1e-12 * S0 for values that are (nearly) zero, where a
-relative bound has no meaning. All calls go through the C ABI.
+Tolerances (relative, plus an absolute floor of 1e-12 * S0 for values that are
+(nearly) zero, where a relative bound has no meaning):
+  FP64 kernel: 1e-12.
+  FP32_COMP kernel: 1e-9 for N >= 28. Every path's payoff is one correctly
+  rounded FP32 value (relative error <= 2^-24); those errors average out over
+  many paths, so smaller trees get wider bands: 3e-9 for N >= 20, 2e-8 for
+  N >= 12, 1e-7 below.
+All calls go through the C ABI.
 """
 import math
 
@@ -13,7 +18,19 @@ from paper_1701_03512_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-9}   # BT_PREC_FP64, BT_PREC_FP32_COMP
+TOL = {0: 1e-12, 1: 1e-9}   # BT_PREC_FP64, BT_PREC_FP32_COMP at N >= 28
+
+
+def tol(prec, N):
+    if prec == 0:
+        return 1e-12
+    if N >= 28:
+        return 1e-9
+    if N >= 20:
+        return 3e-9
+    if N >= 12:
+        return 2e-8
+    return 1e-7
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +53,7 @@ def _check(got, ref, opts, prec, what=""):
     ref = np.asarray(ref, dtype=float)
     s0 = np.array([o["S0"] for o in opts])
     err = np.abs(got - ref)
-    bound = TOL[prec] * np.abs(ref) + 1e-12 * s0
+    bound = np.array([tol(prec, o["N"]) for o in opts]) * np.abs(ref) + 1e-12 * s0
     bad = np.nonzero(~(err <= bound))[0]
     assert bad.size == 0, "%s prec=%d: %s" % (what, prec, [(int(i), opts[i]["payoff"], opts[i]["N"], got[i], ref[i],
                                                            err[i] / max(abs(ref[i]), 1e-300)) for i in bad[:8]])
@@ -82,7 +99,7 @@ def test_two_step_worked_example(bt, ctx, golden_dir):
             for n in names]
     for prec in (0, 1):
         got = ctx.price_exact(opts, prec)["value"]
-        assert np.allclose(got, [g["values"][n] for n in names], rtol=TOL[prec], atol=1e-13), (prec, got)
+        assert np.allclose(got, [g["values"][n] for n in names], rtol=tol(prec, 2), atol=1e-13), (prec, got)
 
 
 def test_paper_exact_values(bt, ctx, golden_dir):
@@ -148,7 +165,8 @@ def test_work_item_partials_against_enumeration(bt, ctx, oracle):
                         continue
                     ref = oracle.sum_range(opts[oi], lo, hi)
                     got = part[item, slot]
-                    assert abs(got - ref) <= TOL[prec] * abs(ref) + 1e-15 * opts[oi]["S0"], (prec, item, slot, got, ref)
+                    # one work item holds 2^22 paths: the N >= 20 band
+                    assert abs(got - ref) <= tol(prec, 22) * abs(ref) + 1e-15 * opts[oi]["S0"], (prec, item, slot, got, ref)
         finally:
             bt.bt_exact_plan_destroy(plan)
 
