@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the exhaustive expected value over all 2^N Bernoulli paths.
+
+Workload (one step): the batched exhaustive pass at N=36 -- 64 option sets
+drawn from numpy default_rng(0) (S0, K ~ U[80,120], sigma ~ U[0.1,0.5],
+rate ~ U[0,0.08], T ~ U[0.25,2]), CRR trees, arithmetic-average Asian call
+and put for each set: 128 option-payoffs, each summed over all 2^36 paths,
+FP32 path arithmetic with compensation and FP64 reduction. A step runs every
+step of the path on the device: tree parameters, suffix and prefix tables,
+the path sums and the per-option reduction.
+
+  value  -- payoff-paths per second (128 * 2^36 per step) with the option
+            array already in device memory, CUDA events on the launching
+            stream, L2 flushed (256 MiB write) between steps;
+  e2e    -- the same through bt_price_exact with host arrays (plan creation,
+            host-to-device copies, all kernels, device-to-host copy, sync);
+  roofline -- the path-sum kernel against the FP32 issue peak
+            (n_SM x 128 lanes x max SM clock), counting the algorithmic
+            3 ops per payoff-path;
+  cpu_baseline -- the CPU oracle (plain enumeration, all host cores) on a
+            bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank prices its own copy of the batch (weak
+scaling, independent problems, no collective on the data path); the value is
+all ranks' paths over the slowest rank's time.
+
+--impl reference times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact paths/s at N=36"
+UNIT = "paths/s"
+N_DEFAULT = 36
+SETS_DEFAULT = 64
+OPS_PER_PATH = 3            # algorithmic: FMA (affine), max(.,0), accumulate
+OPS_EXECUTED_PAIR = 6.75    # per payoff-path in the fused call+put pass (54 ops / 8)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--sets", type=int, default=SETS_DEFAULT)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_config(args, extra=None):
+    c = {"workload": "batched exhaustive arithmetic-Asian call+put, N=%d, %d option sets (seed 0), CRR tree"
+                     % (args.N, args.sets),
+         "N": args.N, "option_sets": args.sets, "payoffs_per_set": 2, "paths_per_payoff": 2 ** args.N,
+         "precision": "FP32_COMP (FP32 path math, FP32-pair folds, FP64 reduction)",
+         "l2": "flushed between timed steps (256 MiB device write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(opts, seconds, threads):
+    """Times the oracle's plain enumeration (eq. f14 partition over threads)
+    on the first paths of the first call/put pair; returns (paths/s, sample)."""
+    from oracle import py_oracle as O
+    O.lib()
+    n = 1 << 20
+    pair = opts[:2]
+    while True:
+        t0 = time.perf_counter()
+        for o in pair:
+            O.sum_range_mt(o, 0, n, threads)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 8 or n >= (1 << 34):
+            break
+        n *= 2
+    reps = max(1, int(seconds / max(dt, 1e-3)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for o in pair:
+            O.sum_range_mt(o, 0, n, threads)
+    dt = time.perf_counter() - t0
+    paths = reps * len(pair) * n
+    sample = "%d x %d paths (path indices [0, 2^%d)) of the set-0 call and put, %d threads" % (
+        reps, n, n.bit_length() - 1, threads)
+    return paths / dt, sample
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def physical_gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [x.strip() for x in vis.split(",") if x.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+# ---------------------------------------------------------------------------
+# Roofline inputs
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("exact.cu", "df.cuh", "bt_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1701_03512_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(N):
+    """DRAM bytes per launch of the path-sum kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_exact32_batched_asian.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for ln in txt.splitlines():
+        if ":" in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    key = "dram_bytes_per_launch_N%d" % N
+    try:
+        return float(vals[key])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from paper_1701_03512_gb300 import workloads as W
+    opts = W.batched_exact_workload(args.N, 0, args.sets)
+    threads = cpu_threads()
+    per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(opts, per_step / 4, threads)
+    vals, sample = [], ""
+    for _ in range(args.steps):
+        v, sample = cpu_oracle_sample(opts, per_step, threads)
+        vals.append(v)
+    value = statistics.median(vals)
+    step_paths = float(len(opts)) * 2.0 ** args.N
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_paths / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, {"engine": "CPU oracle (plain C, FP64)",
+                                                                   "precision": "FP64 (oracle)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+    from paper_1701_03512_gb300 import btree as bt
+    from paper_1701_03512_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx = bt.Context(local_rank)
+    opts = W.batched_exact_workload(args.N, 0, args.sets)
+    plan = bt.bt_exact_plan_create(ctx.h, opts, bt.BT_PREC_FP32_COMP)
+    info = bt.bt_exact_plan_info_get(plan)
+    step_paths = info["payoff_paths"]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        bt.bt_exact_plan_run(plan, stream)
+    stream.synchronize()
+
+    sampler = ClockSampler(physical_gpu_index(local_rank))
+    sampler.start()
+    barrier()
+    t_wall0 = time.perf_counter()
+    step_ms, kern_ms = [], []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.bt_exact_plan_run(plan, stream)
+        e1.record(stream)
+        kern_ms.append(bt.bt_exact_plan_kernel_ms(plan))
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    res = bt.bt_exact_plan_read(plan, stream)
+    assert np.all(np.isfinite(res["value"])) and np.all(res["value"] >= 0.0)
+
+    tot_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([tot_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_s = float(t.item())
+    value = world * step_paths * args.steps / tot_s
+
+    # end to end through the public API with host arrays
+    e2e = None
+    if not args.no_e2e:
+        host_opts = bt.options_array(opts)
+        bt.bt_price_exact(ctx.h, host_opts, bt.BT_PREC_FP32_COMP, stream)  # warm
+        barrier()
+        ts = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            out = bt.bt_price_exact(ctx.h, host_opts, bt.BT_PREC_FP32_COMP, stream)
+            ts.append(time.perf_counter() - t0)
+            assert np.all(np.isfinite(out["value"]))
+        barrier()
+        e2e_s = sum(ts)
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * step_paths * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(info["h2d_bytes"]), "d2h_bytes_per_step": int(info["d2h_bytes"]),
+               "ms_per_step": 1e3 * e2e_s / args.steps}
+
+    if rank != 0:
+        bt.bt_exact_plan_destroy(plan)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    fmax = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_gops = sms * 128 * fmax * 1e6 / 1e9
+    kernel_s = statistics.mean(kern_ms) / 1e3
+    achieved = OPS_PER_PATH * step_paths / kernel_s / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s", "frac": achieved / peak_gops,
+            "traffic": profiled_traffic(args.N),
+            "kernel": "k_exact32", "kernel_ms": 1e3 * kernel_s,
+            "ops_per_payoff_path": OPS_PER_PATH, "ops_executed_per_payoff_path": OPS_EXECUTED_PAIR,
+            "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock, MEASURED_PEAKS.json)" % (sms, fmax)}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e9)
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        threads = cpu_threads()
+        v, sample = cpu_oracle_sample(opts, args.cpu_seconds, threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args, {"parallelism": "replicas" if world > 1 else "single GPU",
+                                             "wall_s_timed": t_wall}),
+            "fp32_peak_frac": roof["frac"], "clocks": clocks, "e2e": e2e,
+            "gpu_launches": 4 * args.steps, "roofline": roof, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    bt.bt_exact_plan_destroy(plan)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

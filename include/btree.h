@@ -141,6 +141,8 @@ typedef struct {
     int64_t payoff_paths;     /* sum over options of 2^N                         */
     int64_t path_evaluations; /* sum over jobs of 2^N                            */
     size_t device_bytes;      /* device memory held by the plan                  */
+    size_t h2d_bytes;         /* host-to-device bytes bt_price_exact copies per call */
+    size_t d2h_bytes;         /* device-to-host bytes of the results             */
 } bt_exact_plan_info;
 
 bt_status bt_exact_plan_create(bt_ctx *ctx, const bt_option *opts, int32_t n, bt_precision prec,
@@ -165,6 +167,11 @@ bt_status bt_exact_plan_partials(bt_exact_plan *plan, double *partials, int32_t 
 bt_status bt_exact_plan_job(const bt_exact_plan *plan, int32_t j, int32_t *opt_call, int32_t *opt_put,
                             int32_t *P, int32_t *L, int32_t *prefixes_per_item);
 bt_status bt_exact_plan_info_get(const bt_exact_plan *plan, bt_exact_plan_info *info);
+/* Duration in milliseconds of the path-sum kernel of the most recent run,
+ * measured with CUDA events recorded on that run's stream just before and
+ * after the kernel launch. Synchronises on the end event. BT_EINVAL before
+ * the first run. */
+bt_status bt_exact_plan_kernel_ms(bt_exact_plan *plan, float *ms);
 void bt_exact_plan_destroy(bt_exact_plan *plan);
 
 #ifdef __cplusplus

@@ -48,7 +48,8 @@ class bt_result(C.Structure):
 
 class bt_exact_plan_info(C.Structure):
     _fields_ = [("n_options", C.c_int32), ("n_jobs", C.c_int32), ("n_items", C.c_int64),
-                ("payoff_paths", C.c_int64), ("path_evaluations", C.c_int64), ("device_bytes", C.c_size_t)]
+                ("payoff_paths", C.c_int64), ("path_evaluations", C.c_int64), ("device_bytes", C.c_size_t),
+                ("h2d_bytes", C.c_size_t), ("d2h_bytes", C.c_size_t)]
 
 
 OPTION_DTYPE = np.dtype([("N", "<i4"), ("tree_kind", "<i4"), ("payoff", "<i4"), ("pad", "<i4"),
@@ -94,6 +95,7 @@ def lib():
                                         C.POINTER(_i32), C.POINTER(_i32)])
         _proto(L, "bt_exact_plan_info_get", [_vp, C.POINTER(bt_exact_plan_info)])
         _proto(L, "bt_exact_plan_destroy", [_vp], None)
+        _proto(L, "bt_exact_plan_kernel_ms", [_vp, C.POINTER(C.c_float)])
         _lib = L
     return _lib
 
@@ -200,6 +202,12 @@ def bt_exact_plan_job(plan, j):
     _check(lib().bt_exact_plan_job(plan, j, *[C.byref(v) for v in vals]))
     keys = ("opt_call", "opt_put", "P", "L", "prefixes_per_item")
     return {k: v.value for k, v in zip(keys, vals)}
+
+
+def bt_exact_plan_kernel_ms(plan) -> float:
+    ms = C.c_float()
+    _check(lib().bt_exact_plan_kernel_ms(plan, C.byref(ms)))
+    return ms.value
 
 
 def bt_exact_plan_destroy(plan):

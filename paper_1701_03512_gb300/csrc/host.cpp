@@ -167,7 +167,11 @@ bt_status validate_option(const bt_option *o, int idx, int max_n) {
     }
     double u, d, p;
     bt_status s = host_tree(o, &u, &d, &p);
-    if (s != BT_OK) return bt_fail(s, "option %d: %s", idx, g_err);
+    if (s != BT_OK) {
+        char why[sizeof(g_err)];
+        memcpy(why, g_err, sizeof(why));
+        return bt_fail(s, "option %d: %s", idx, why);
+    }
     return BT_OK;
 }
 
@@ -258,6 +262,8 @@ struct bt_exact_plan {
     double2 *d_partials;
     bt_result *d_out;
     unsigned long long *d_counter;
+    cudaEvent_t ev0, ev1;
+    bool timed;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -420,8 +426,15 @@ static bt_status plan_enqueue(bt_exact_plan *pl, int shard, int n_shards, void *
     a.pw = pl->d_pw;
     a.partials = pl->d_partials;
     a.counter = pl->d_counter;
+    if (!pl->ev0) {
+        if (cudaEventCreate(&pl->ev0) != cudaSuccess || cudaEventCreate(&pl->ev1) != cudaSuccess)
+            return bt_cuda_fail((int)cudaGetLastError(), "cudaEventCreate");
+    }
+    cudaEventRecord(pl->ev0, st);
     e = bt_launch_exact(&a, pl->prec, pl->prec == BT_PREC_FP64 ? c->grid64 : c->grid32, st);
     if (e) return bt_cuda_fail(e, "path-sum kernel");
+    cudaEventRecord(pl->ev1, st);
+    pl->timed = true;
     e = bt_launch_finalize(pl->d_jobs, pl->d_prm, nj, pl->d_partials, shard, n_shards, pl->prec, pl->d_out, st);
     if (e) return bt_cuda_fail(e, "finalize kernel");
     return BT_OK;
@@ -486,16 +499,29 @@ extern "C" bt_status bt_exact_plan_info_get(const bt_exact_plan *pl, bt_exact_pl
     info->payoff_paths = pl->payoff_paths;
     info->path_evaluations = pl->path_evals;
     info->device_bytes = pl->arena_bytes;
+    info->h2d_bytes = sizeof(bt_option) * (size_t)pl->n_opts + sizeof(bt_job) * pl->jobs.size();
+    info->d2h_bytes = sizeof(bt_result) * (size_t)pl->n_opts;
+    return BT_OK;
+}
+
+extern "C" bt_status bt_exact_plan_kernel_ms(bt_exact_plan *pl, float *ms) {
+    if (!pl || !ms || !pl->timed) return bt_fail(BT_EINVAL, "bt_exact_plan_kernel_ms: no timed run");
+    cudaSetDevice(pl->ctx->device);
+    cudaError_t e = cudaEventSynchronize(pl->ev1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, pl->ev0, pl->ev1);
+    if (e != cudaSuccess) return bt_cuda_fail(e, "bt_exact_plan_kernel_ms");
     return BT_OK;
 }
 
 extern "C" void bt_exact_plan_destroy(bt_exact_plan *pl) {
     if (!pl) return;
+    cudaSetDevice(pl->ctx->device);
     if (pl->arena) {
-        cudaSetDevice(pl->ctx->device);
         cudaStreamSynchronize(pl->ctx->stream);
         ctx_free(pl->ctx, pl->arena, pl->arena_bytes);
     }
+    if (pl->ev0) cudaEventDestroy(pl->ev0);
+    if (pl->ev1) cudaEventDestroy(pl->ev1);
     delete pl;
 }
 
