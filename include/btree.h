@@ -174,6 +174,37 @@ bt_status bt_exact_plan_info_get(const bt_exact_plan *plan, bt_exact_plan_info *
 bt_status bt_exact_plan_kernel_ms(bt_exact_plan *plan, float *ms);
 void bt_exact_plan_destroy(bt_exact_plan *plan);
 
+/* Allocation-free exhaustive pricing --------------------------------------- */
+/* The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory while they run -- for example an application whose own
+ * allocator owns the device, or a latency-sensitive loop that cannot afford
+ * cudaMalloc/cudaFree (cudaFree synchronises the whole device).
+ *
+ * Same computation and results as bt_price_exact (host arrays opts[0..n) in,
+ * out[0..n) out, synchronous on `stream`, NULL = the legacy default stream),
+ * but every intermediate buffer lives in one fixed device array of
+ * BT_NOALLOC_SCRATCH_BYTES that the library defines statically: no context is
+ * needed and nothing is allocated (no cudaMalloc, cudaFree, or any allocating
+ * library routine). Every GPU that loads the library holds that array until
+ * the process exits.
+ *
+ * The first call on a device (with that device current) looks up the array's
+ * device address; make that first call before any stream capture.
+ *
+ * All calls on a device share the array, and two calls whose GPU work
+ * overlapped would race on it. The function prevents that: it holds a
+ * process-wide lock from its first copy until its stream has drained, and it
+ * clears the parts that must start at zero on every call.
+ *
+ * Limits: n <= BT_NOALLOC_MAX_OPTIONS, and the batch's tables and per-item
+ * partials must fit in the array (for example 64 options with N <= 30, or a
+ * single option up to N = 40); beyond either, BT_EUNSUPPORTED with a message
+ * giving the bytes needed. Other errors as bt_price_exact. */
+#define BT_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define BT_NOALLOC_MAX_OPTIONS 64
+bt_status bt_price_exact_noalloc(const bt_option *opts, int32_t n, bt_precision prec, bt_result *out,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,7 @@ def lib():
         _proto(L, "bt_exact_plan_info_get", [_vp, C.POINTER(bt_exact_plan_info)])
         _proto(L, "bt_exact_plan_destroy", [_vp], None)
         _proto(L, "bt_exact_plan_kernel_ms", [_vp, C.POINTER(C.c_float)])
+        _proto(L, "bt_price_exact_noalloc", [_vp, _i32, C.c_int, _vp, _vp])
         _lib = L
     return _lib
 
@@ -212,6 +213,20 @@ def bt_exact_plan_kernel_ms(plan) -> float:
 
 def bt_exact_plan_destroy(plan):
     lib().bt_exact_plan_destroy(plan)
+
+
+BT_NOALLOC_SCRATCH_BYTES = 8 << 20
+BT_NOALLOC_MAX_OPTIONS = 64
+
+
+def bt_price_exact_noalloc(opts, prec=BT_PREC_FP32_COMP, stream=None) -> np.ndarray:
+    """Exhaustive pricing without any device allocation: for callers that
+    cannot allocate device memory while they run (see the C header). Uses a
+    fixed library-owned device array; needs no context."""
+    a = options_array(opts)
+    out = np.zeros(len(a), dtype=RESULT_DTYPE)
+    _check(lib().bt_price_exact_noalloc(a.ctypes.data, len(a), prec, out.ctypes.data, _stream(stream)))
+    return out
 
 
 class Context:

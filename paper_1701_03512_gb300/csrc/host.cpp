@@ -241,6 +241,29 @@ void fill_job_shape(bt_job &J, int N, int field, int mode) {
     J.n_items = (int32_t)std::max<int64_t>(1, (nP + (1 << BT_LOW_BITS) - 1) >> BT_LOW_BITS);
 }
 
+// Plans the pass that starts at option i (used by the allocation-free entry
+// point, which keeps its job list on the stack): the same pairing and split
+// rules as plan_jobs. Sets *step to the number of options the pass covers.
+void plan_one_job(const bt_option *opts, int n, int i, bt_job *J, int *step) {
+    int field, mode;
+    payoff_field(opts[i].payoff, &field, &mode);
+    J->opt = i;
+    J->out_call = mode == BT_MODE_CALL ? i : -1;
+    J->out_put = mode == BT_MODE_PUT ? i : -1;
+    *step = 1;
+    if (i + 1 < n && field != BT_F_LOOKMAX && field != BT_F_LOOKMIN && same_params(opts[i], opts[i + 1])) {
+        int f2, m2;
+        payoff_field(opts[i + 1].payoff, &f2, &m2);
+        if (f2 == field && m2 != mode) {
+            mode = BT_MODE_BOTH;
+            if (J->out_call < 0) J->out_call = i + 1;
+            else J->out_put = i + 1;
+            *step = 2;
+        }
+    }
+    fill_job_shape(*J, opts[i].N, field, mode);
+}
+
 struct bt_exact_plan {
     bt_ctx *ctx;
     int prec;

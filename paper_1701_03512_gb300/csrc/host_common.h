@@ -27,3 +27,4 @@ int exact_split_L(int N);
 void fill_job_shape(bt_job &J, int N, int field, int mode);
 bt_status plan_jobs(const bt_option *opts, int n, int prec, std::vector<bt_job> &jobs, int64_t *n_items,
                     int64_t *payoff_paths, int64_t *path_evals, int max_n);
+void plan_one_job(const bt_option *opts, int n, int i, bt_job *J, int *step);
