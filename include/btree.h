@@ -174,6 +174,41 @@ bt_status bt_exact_plan_info_get(const bt_exact_plan *plan, bt_exact_plan_info *
 bt_status bt_exact_plan_kernel_ms(bt_exact_plan *plan, float *ms);
 void bt_exact_plan_destroy(bt_exact_plan *plan);
 
+/* Monte Carlo (Section 4) -------------------------------------------------- */
+typedef enum {
+    BT_MC_PARTITIONED = 0,  /* eq. mc12: R suffix draws inside each stratum          */
+    BT_MC_SHARED = 1        /* eq. mc16 (Remark of Section 4): the same R suffix
+                               draws reused under every stratum's prefix            */
+} bt_mc_kind;
+
+/* Partitioned Monte Carlo with equal allocation. Stratum m in [0, 2^strata_bits)
+ * fixes the first strata_bits steps to m's bits, most significant first (the
+ * rank bits of Section 3); each stratum draws samples_per_stratum suffixes of
+ * N - strata_bits steps. Step t of sample i in stratum m goes up iff word
+ * (t - strata_bits - 1) % 4 of Philox-4x32-10 with counter
+ * ((t - strata_bits - 1) / 4, i, m, option index) and key (seed low 32 bits,
+ * seed high 32 bits) is below round(p 2^32) (clamped to [1, 2^32 - 1]).
+ * value = e^{-qT} sum_m P(D_m) mean_m (eq. mc12); stderr_mc =
+ * e^{-qT} sqrt(sum_m P(D_m)^2 s_m^2 / R) with the unbiased s_m^2; var_plain
+ * = the implied variance of one undiscounted draw, sum_m P(D_m) Var_m +
+ * Var_D E[V|D] (eq. mc14), for comparison with plain MC; paths = samples.
+ * strata_bits = 0 is plain MC. Limits: N <= 4096, strata_bits <= min(N, 24),
+ * 1 <= samples_per_stratum <= 2^32. Synchronous on `stream`. */
+bt_status bt_price_mc(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t strata_bits,
+                      int64_t samples_per_stratum, uint64_t seed, bt_result *out, void *stream);
+/* As bt_price_mc, with the estimator kind (BT_MC_SHARED: counter word 2 is 0
+ * for every stratum, strata_bits <= 10, stderr from the sample variance of
+ * h_i = sum_m P(D_m) V(z_m, y_i), var_plain = 0) and, if strata_stats is not
+ * NULL, per-stratum (mean, unbiased variance, P(D_m)) triples for every
+ * option, options concatenated (2^strata_bits triples per option; one triple
+ * for BT_MC_SHARED). */
+bt_status bt_price_mc_ex(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t strata_bits,
+                         int64_t samples_per_stratum, uint64_t seed, int32_t kind, bt_result *out,
+                         double *strata_stats, void *stream);
+/* The device Philox-4x32-10 used above, evaluated for n counters and keys
+ * (host arrays ctr[n][4], key[n][2], out[n][4]); for verification. */
+bt_status bt_philox4x32_10(bt_ctx *ctx, const uint32_t *ctr, const uint32_t *key, uint32_t *out, int32_t n);
+
 /* Allocation-free exhaustive pricing --------------------------------------- */
 /* The paper has no counterpart: this exists for callers that cannot allocate
  * device memory while they run -- for example an application whose own

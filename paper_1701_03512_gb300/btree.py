@@ -97,6 +97,9 @@ def lib():
         _proto(L, "bt_exact_plan_destroy", [_vp], None)
         _proto(L, "bt_exact_plan_kernel_ms", [_vp, C.POINTER(C.c_float)])
         _proto(L, "bt_price_exact_noalloc", [_vp, _i32, C.c_int, _vp, _vp])
+        _proto(L, "bt_price_mc", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _vp, _vp])
+        _proto(L, "bt_price_mc_ex", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _i32, _vp, _vp, _vp])
+        _proto(L, "bt_philox4x32_10", [_vp, _vp, _vp, _vp, _i32])
         _lib = L
     return _lib
 
@@ -213,6 +216,36 @@ def bt_exact_plan_kernel_ms(plan) -> float:
 
 def bt_exact_plan_destroy(plan):
     lib().bt_exact_plan_destroy(plan)
+
+
+BT_MC_PARTITIONED, BT_MC_SHARED = 0, 1
+
+
+def bt_price_mc(ctx, opts, strata_bits, samples_per_stratum, seed, stream=None) -> np.ndarray:
+    a = options_array(opts)
+    out = np.zeros(len(a), dtype=RESULT_DTYPE)
+    _check(lib().bt_price_mc(ctx, a.ctypes.data, len(a), strata_bits, samples_per_stratum, seed,
+                             out.ctypes.data, _stream(stream)))
+    return out
+
+
+def bt_price_mc_ex(ctx, opts, strata_bits, samples_per_stratum, seed, kind=BT_MC_PARTITIONED,
+                   with_strata=False, stream=None):
+    a = options_array(opts)
+    out = np.zeros(len(a), dtype=RESULT_DTYPE)
+    per = 1 if kind == BT_MC_SHARED else (1 << strata_bits)
+    strata = np.zeros((len(a), per, 3)) if with_strata else None
+    _check(lib().bt_price_mc_ex(ctx, a.ctypes.data, len(a), strata_bits, samples_per_stratum, seed, kind,
+                                out.ctypes.data, strata.ctypes.data if with_strata else None, _stream(stream)))
+    return (out, strata) if with_strata else out
+
+
+def bt_philox4x32_10(ctx, ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
+    out = np.zeros_like(c)
+    _check(lib().bt_philox4x32_10(ctx, c.ctypes.data, k.ctypes.data, out.ctypes.data, len(c)))
+    return out
 
 
 BT_NOALLOC_SCRATCH_BYTES = 8 << 20

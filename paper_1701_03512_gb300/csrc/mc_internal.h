@@ -1,0 +1,46 @@
+// Internal layout of the Monte Carlo kernels (mc.cu) and their host runtime.
+#pragma once
+#include <stdint.h>
+
+#include "bt_internal.h"
+
+#define BT_MC_ITEM 1024            // samples per work item (256 threads x 4)
+#define BT_MC_SHARED_MAX_BITS 10   // Shared-Sample strata live in shared memory
+#define BT_MC_MAX_N 4096
+#define BT_MC_MAX_BITS 24
+
+struct bt_mc_job {
+    int32_t N, mb;                 // tree depth, strata bits (prefix length)
+    int64_t R;                     // samples per stratum (Shared-Sample: per prefix set)
+    int32_t field, sign;           // suffix quantity (bt_field) and +1 call / -1 put
+    int32_t shared;                // 1: Shared-Sample estimator
+    uint32_t stream;               // Philox counter word 3 (the option's index in the call)
+    uint32_t key_lo, key_hi;       // Philox key (the seed)
+    uint32_t thr;                  // up iff the 32-bit word < thr = round(p 2^32)
+    int32_t out;                   // result slot
+    double u, d, p, S0, K, disc;
+    float uf, df, lnu_f;
+    int32_t pad;
+    int64_t item_begin, n_items, strata_off;
+};
+
+struct bt_mc_args {
+    const bt_mc_job *jobs;
+    int32_t n_jobs;
+    int32_t pad;
+    int64_t n_items;
+    double4 *item_stats;           // per item: (count, mean, M2, stratum)
+    unsigned long long *counter;
+};
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+int bt_launch_mc(const bt_mc_args *a, int grid, void *stream);
+int bt_launch_mc_finalize(const bt_mc_job *jobs, int n_jobs, const double4 *item_stats, int64_t n_strata,
+                          double4 *strata_nmq, bt_result *out, double *strata, void *stream);
+int bt_launch_philox_selftest(const uint4 *ctr, const uint2 *key, uint4 *out, int n, void *stream);
+int bt_mc_grid_size(int device);
+#ifdef __cplusplus
+}
+#endif

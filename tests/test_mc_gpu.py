@@ -1,0 +1,145 @@
+"""GPU parity of the Monte Carlo estimators (Section 4) against the oracle.
+
+The device draws the same Bernoulli bits as the oracle (same Philox counters,
+key and threshold), so with equal seeds the estimates agree up to FP32
+per-sample rounding (relative 2e-5 here); statistical properties are checked
+against exact values from the exhaustive oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_1701_03512_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bt():
+    from paper_1701_03512_gb300 import build as b
+    b.build()
+    from paper_1701_03512_gb300 import btree
+    return btree
+
+
+@pytest.fixture(scope="module")
+def ctx(bt):
+    c = bt.Context(0)
+    yield c
+    c.close()
+
+
+def test_device_philox_matches_oracle(bt, ctx, oracle):
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 2 ** 32, (257, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, (257, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    key[0] = 0
+    got = bt.bt_philox4x32_10(ctx.h, ctr, key)
+    for i in range(len(ctr)):
+        assert got[i].tolist() == oracle.philox(ctr[i].tolist(), key[i].tolist()), i
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("mb,R", [(0, 700), (3, 100), (4, 1500)])
+def test_same_draws_as_oracle(bt, ctx, oracle, kind, mb, R):
+    opts = [W.opt(12, 100.0, 101.0, 0.04, 0.3, 1.0, pay, W.TREE_SEYDEL if pay % 3 == 0 else W.TREE_CRR)
+            for pay in range(8)]
+    seed = 0x1234_5678_9ABC
+    got = bt.bt_price_mc_ex(ctx.h, opts, mb, R, seed, kind)
+    for i, o in enumerate(opts):
+        th, var = oracle.mc(o, mb, R, seed, stream=i, shared=bool(kind))
+        disc = oracle.discount(o)
+        assert got["value"][i] == pytest.approx(disc * th, rel=2e-5, abs=1e-9), (i, kind, mb)
+        assert got["stderr_mc"][i] == pytest.approx(disc * math.sqrt(var), rel=2e-4, abs=1e-9), (i, kind, mb)
+        assert got["paths"][i] == (1 if kind else 2 ** mb) * R
+
+
+def test_per_stratum_statistics_match_oracle(bt, ctx, oracle):
+    o = W.opt(11, 97.0, 100.0, 0.05, 0.25, 1.0, W.ASIAN_ARITH_CALL)
+    out, strata = bt.bt_price_mc_ex(ctx.h, [o], 5, 300, 99, 0, with_strata=True)
+    th, var, mean, sv, pr = oracle.mc(o, 5, 300, 99, stream=0, with_strata=True)
+    np.testing.assert_allclose(strata[0, :, 0], mean, rtol=2e-5, atol=1e-9)
+    np.testing.assert_allclose(strata[0, :, 1], sv, rtol=5e-4, atol=1e-9)
+    np.testing.assert_allclose(strata[0, :, 2], pr, rtol=1e-13)
+
+
+def test_all_strata_is_exact(bt, ctx, oracle):
+    """2^N strata: every stratum is one full path, the estimator is the exact sum."""
+    opts = [W.opt(10, 100.0, 100.0, 0.05, 0.3, 1.0, pay) for pay in range(8)]
+    got = bt.bt_price_mc(ctx.h, opts, 10, 2, 7)
+    for i, o in enumerate(opts):
+        assert got["value"][i] == pytest.approx(oracle.price_exhaustive(o, 1), rel=1e-6, abs=1e-9)
+        assert got["stderr_mc"][i] == 0.0
+
+
+def test_unbiased_at_n30_and_stderr_calibrated(bt, ctx, oracle):
+    """N=30, 2^10 strata x 2^10 samples: within 3 SE of the exact value; the
+    spread over seeds matches the reported standard error."""
+    o = W.opt(30, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
+    exact = oracle.asian_mitm(o, 15)
+    vals, ses = [], []
+    for seed in range(24):
+        r = bt.bt_price_mc(ctx.h, [o], 10, 1024, 1000 + seed)
+        vals.append(r["value"][0])
+        ses.append(r["stderr_mc"][0])
+    vals, ses = np.array(vals), np.array(ses)
+    assert np.all(np.abs(vals - exact) <= 4 * ses)
+    assert abs(vals.mean() - exact) <= 3 * ses.mean() / math.sqrt(len(vals))
+    ratio = vals.var(ddof=1) / np.mean(ses ** 2)
+    lo, hi = stats.chi2.ppf([1e-3, 1 - 1e-3], len(vals) - 1) / (len(vals) - 1)
+    assert lo < ratio < hi
+
+
+def test_stratification_reduces_variance(bt, ctx):
+    """eq. mc15: at equal total samples the Partitioned estimator's variance is
+    Var(plain) - Var_D E[V|D]/R, i.e. strictly below plain MC's; the reported
+    var_plain (law of total variance) agrees with the plain estimate."""
+    o = W.opt(64, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
+    strat = bt.bt_price_mc(ctx.h, [o], 10, 1024, 3)[0]
+    plain = bt.bt_price_mc(ctx.h, [o], 0, 1024 * 1024, 4)[0]
+    assert strat["stderr_mc"] < 0.95 * plain["stderr_mc"]
+    assert abs(strat["value"] - plain["value"]) < 4 * math.hypot(strat["stderr_mc"], plain["stderr_mc"])
+    disc = math.exp(-0.05)
+    sd_plain_from_strat = disc * math.sqrt(strat["var_plain"] / (1024 * 1024))
+    assert sd_plain_from_strat == pytest.approx(plain["stderr_mc"], rel=0.05)
+
+
+@pytest.mark.parametrize("N,mb,R", [(64, 12, 1024), (252, 10, 1024), (252, 16, 64)])
+def test_put_call_parity_deep_trees(bt, ctx, N, mb, R):
+    """Per draw, max(A-K,0) - max(K-A,0) = A - K, and E[A] = (S0/N) sum_t e^{q t dt}:
+    the call and put estimates from the same draws differ by that forward."""
+    S0, K, r, T = 100.0, 103.0, 0.05, 1.0
+    opts = [W.opt(N, S0, K, r, 0.2, T, W.ASIAN_ARITH_CALL), W.opt(N, S0, K, r, 0.2, T, W.ASIAN_ARITH_PUT)]
+    out = bt.bt_price_mc(ctx.h, opts, mb, R, 11)
+    # same seed and counters: both options draw identical paths only if their stream ids
+    # match, so price them one at a time
+    c = bt.bt_price_mc(ctx.h, opts[:1], mb, R, 11)[0]
+    p = bt.bt_price_mc(ctx.h, opts[1:], mb, R, 11)[0]
+    dt = T / N
+    fwd = math.exp(-r * T) * (S0 / N * sum(math.exp(r * t * dt) for t in range(1, N + 1)) - K)
+    assert abs((c["value"] - p["value"]) - fwd) <= 4 * (c["stderr_mc"] + p["stderr_mc"])
+    assert np.all(np.isfinite(out["value"])) and np.all(out["stderr_mc"] > 0)
+
+
+def test_theorem1_on_gpu(bt, ctx, oracle):
+    """Var(partitioned) <= Var(shared) <= Var(plain) with R_m = R (Theorem 1),
+    Asian put as in Table 5, from the spread over seeds."""
+    o = W.opt(16, 100.0, 100.0, 0.05, 0.4, 1.0, W.ASIAN_ARITH_PUT)
+    part = [bt.bt_price_mc_ex(ctx.h, [o], 4, 256, s, 0)["value"][0] for s in range(60)]
+    shar = [bt.bt_price_mc_ex(ctx.h, [o], 4, 256, s, 1)["value"][0] for s in range(60)]
+    basic = [bt.bt_price_mc_ex(ctx.h, [o], 0, 256, s, 0)["value"][0] for s in range(60)]
+    assert np.var(part) < np.var(shar) < np.var(basic)
+
+
+def test_mc_invalid(bt, ctx):
+    o = W.single_asian_n20()
+    with pytest.raises(bt.BtError):
+        bt.bt_price_mc(ctx.h, [o], 21, 10, 1)
+    with pytest.raises(bt.BtError) as e:
+        bt.bt_price_mc_ex(ctx.h, [o], 11, 10, 1, 1)
+    assert e.value.status == bt.BT_EUNSUPPORTED
+    with pytest.raises(bt.BtError):
+        bt.bt_price_mc(ctx.h, [dict(o, N=5000)], 2, 10, 1)
