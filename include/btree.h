@@ -174,6 +174,19 @@ bt_status bt_exact_plan_info_get(const bt_exact_plan *plan, bt_exact_plan_info *
 bt_status bt_exact_plan_kernel_ms(bt_exact_plan *plan, float *ms);
 void bt_exact_plan_destroy(bt_exact_plan *plan);
 
+/* Greeks of the exhaustive value ------------------------------------------- */
+/* Not in the paper: derivatives of eq. f13 for opts[0..n): value[i] = V and
+ * grad[4 i + 0..3] = dV/dS0, dV/dsigma, dV/drate, dV/dK. One derivative pass
+ * over every path accumulates, next to the value, the in-the-money weight,
+ * the path-weight derivative sum_x w(x) payoff(x) k(x) (k = up-count, for
+ * dV/dp) and the pathwise dV/du at fixed p; the host applies the chain rule
+ * through u(sigma, rate) and p(u, rate) of the option's tree (CRR, Seydel; an
+ * explicit tree has dV/dsigma = 0 and dV/drate = -T V) and Euler's identity
+ * S0 dV/dS0 + K dV/dK = V (the payoffs are homogeneous of degree one in
+ * (S0, K)). Only BT_PREC_FP32_COMP (BT_EUNSUPPORTED otherwise). Synchronous. */
+bt_status bt_greeks_exact(bt_ctx *ctx, const bt_option *opts, int32_t n, bt_precision prec, double *value,
+                          double *grad, void *stream);
+
 /* Monte Carlo (Section 4) -------------------------------------------------- */
 typedef enum {
     BT_MC_PARTITIONED = 0,  /* eq. mc12: R suffix draws inside each stratum          */

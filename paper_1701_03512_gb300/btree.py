@@ -100,6 +100,7 @@ def lib():
         _proto(L, "bt_price_mc", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _vp, _vp])
         _proto(L, "bt_price_mc_ex", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _i32, _vp, _vp, _vp])
         _proto(L, "bt_philox4x32_10", [_vp, _vp, _vp, _vp, _i32])
+        _proto(L, "bt_greeks_exact", [_vp, _vp, _i32, C.c_int, _vp, _vp, _vp])
         _lib = L
     return _lib
 
@@ -246,6 +247,16 @@ def bt_philox4x32_10(ctx, ctr, key) -> np.ndarray:
     out = np.zeros_like(c)
     _check(lib().bt_philox4x32_10(ctx, c.ctypes.data, k.ctypes.data, out.ctypes.data, len(c)))
     return out
+
+
+def bt_greeks_exact(ctx, opts, prec=BT_PREC_FP32_COMP, stream=None):
+    """(values[n], grads[n, 4]) with grads = dV/d(S0, sigma, rate, K)."""
+    a = options_array(opts)
+    val = np.zeros(len(a))
+    grad = np.zeros((len(a), 4))
+    _check(lib().bt_greeks_exact(ctx, a.ctypes.data, len(a), prec, val.ctypes.data, grad.ctypes.data,
+                                 _stream(stream)))
+    return val, grad
 
 
 BT_NOALLOC_SCRATCH_BYTES = 8 << 20

@@ -13,6 +13,7 @@
 #define BT_PT64 4              // prefixes per thread (FP64 kernel)
 #define BT_UNROLL 8            // suffix groups are padded to a multiple of this
 #define BT_SUF_MAX ((1 << BT_MAX_L) + (BT_MAX_L + 1) * (BT_UNROLL - 1))
+#define BT_SUF_MAX_EVEN ((BT_SUF_MAX + 1) & ~1)   // float2 count keeping what follows 16-byte aligned
 #define BT_LVL_NONE 30000      // sentinel level: "no price in this block"
 
 // What the suffix table of a job holds (one field per job).
@@ -43,10 +44,11 @@ struct bt_job {
 };
 
 struct bt_pentry {            // one entry of a two-level prefix table
-    double R64;               // backward-relative partial sum (see tables.cu)
+    double R64;               // backward-relative partial sum sum_t u^{l_t - l_end}
     float R_hi, R_lo;
     int16_t lvl, mx, mn, D;   // end level, max level, min level, level sum
-    int32_t pad[2];
+    float Q;                  // level-weighted backward sum sum_t l_t u^{l_t - l_end}
+    int32_t pad;
 };
 
 struct bt_pow {               // u^e for some exponent e, in FP64 and as an FP32 pair
@@ -86,6 +88,8 @@ struct bt_exact_args {
     const bt_pow *pw;
     double2 *partials;        // per global work item: (call slot, put slot)
     unsigned long long *counter;
+    const float *sufd;        // derivative pass: df_s/du table
+    double4 *partials4;       // derivative pass: per item (V, sum w pay k, dV/du part, ITM weight)
 };
 
 #ifdef __cplusplus
@@ -96,10 +100,17 @@ int bt_launch_params(const bt_option *d_opts, const bt_job *d_jobs, bt_jparams *
                      void *stream);
 int bt_launch_tables(const bt_job *d_jobs, const bt_jparams *d_prm, int n_jobs, int max_len, int prec,
                      float2 *suf32, double *suf64, bt_pentry *ph, bt_pentry *pm, bt_pow *pw, void *stream);
+// As bt_launch_tables, also writing the suffix derivative table df_s/du (FP32,
+// same positions as the suffix table, 0 in the padding).
+int bt_launch_tables_d(const bt_job *d_jobs, const bt_jparams *d_prm, int n_jobs, int max_len, float2 *suf32,
+                       float *sufd, bt_pentry *ph, bt_pentry *pm, bt_pow *pw, void *stream);
 int bt_launch_exact(const bt_exact_args *a, int prec, int grid, void *stream);
 int bt_launch_finalize(const bt_job *d_jobs, const bt_jparams *d_prm, int n_jobs, const double2 *partials,
                        int shard, int n_shards, int prec, bt_result *d_out, void *stream);
 int bt_exact_grid_size(int prec, int device);
+int bt_launch_greeks(const bt_exact_args *a, int grid, void *stream);
+int bt_launch_greeks_finalize(const bt_job *d_jobs, int n_jobs, const double4 *partials, double4 *sums,
+                              void *stream);
 #ifdef __cplusplus
 }
 #endif

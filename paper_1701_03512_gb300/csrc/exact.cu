@@ -166,16 +166,18 @@ __device__ static int colex_rank(unsigned s) {
 }
 
 // Walk `bits` steps of `x` (MSB first) from level 0 and return the block's
-// summary: end level, max/min level, level sum and the backward-relative
-// partial sum R = sum_t u^{l_t - l_end} (R_t = R_{t-1} * u^{-(l_t - l_{t-1})} + 1).
+// summary: end level, max/min level, level sum, the backward-relative
+// partial sum R = sum_t u^{l_t - l_end} (R_t = R_{t-1} * u^{-(l_t - l_{t-1})} + 1)
+// and its level-weighted form Q = sum_t l_t u^{l_t - l_end}.
 __device__ static bt_pentry walk_block(uint64_t x, int bits, double u, double d) {
     bt_pentry e;
     int lvl = 0, mx = -BT_LVL_NONE, mn = BT_LVL_NONE, D = 0;
-    double R = 0.0;
+    double R = 0.0, Q = 0.0;
     for (int t = 1; t <= bits; ++t) {
         int up = (int)((x >> (bits - t)) & 1u);
         lvl += up ? 1 : -1;
         R = R * (up ? d : u) + 1.0;
+        Q = Q * (up ? d : u) + (double)lvl;
         mx = lvl > mx ? lvl : mx;
         mn = lvl < mn ? lvl : mn;
         D += lvl;
@@ -188,12 +190,13 @@ __device__ static bt_pentry walk_block(uint64_t x, int bits, double u, double d)
     e.mx = (int16_t)mx;
     e.mn = (int16_t)mn;
     e.D = (int16_t)D;
-    e.pad[0] = e.pad[1] = 0;
+    e.Q = (float)Q;
+    e.pad = 0;
     return e;
 }
 
 __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, float2 *suf32, double *suf64,
-                         bt_pentry *ph, bt_pentry *pm, bt_pow *pw) {
+                         bt_pentry *ph, bt_pentry *pm, bt_pow *pw, float *sufd) {
     const int j = blockIdx.y;
     const bt_job J = jobs[j];
     const double u = prm[j].u, d = prm[j].d, lnu = prm[j].lnu;
@@ -207,12 +210,13 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
             unsigned s = (unsigned)i;
             int k = __popc(s);
             int lvl = 0, mx = -BT_LVL_NONE, mn = BT_LVL_NONE, D = 0;
-            double r = 1.0, f = 0.0;
+            double r = 1.0, f = 0.0, fl = 0.0;
             for (int t = 1; t <= J.L; ++t) {
                 int up = (int)((s >> (J.L - t)) & 1u);
                 lvl += up ? 1 : -1;
                 r *= up ? u : d;
                 f += r;
+                fl += (double)lvl * r;
                 D += lvl;
                 mx = lvl > mx ? lvl : mx;
                 mn = lvl < mn ? lvl : mn;
@@ -226,6 +230,17 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
             default: v = exp((double)mn * lnu); break;
             }
             int pos = J.goff[k] + colex_rank(s);
+            if (sufd) {  // df_s/du
+                double dv;
+                switch (J.field) {
+                case BT_F_ARITH: dv = fl / u; break;
+                case BT_F_GEO: dv = v * (double)D / ((double)J.N * u); break;
+                case BT_F_EURO: dv = v * (double)lvl / u; break;
+                case BT_F_LOOKMAX: dv = v * (double)mx / u; break;
+                default: dv = v * (double)mn / u; break;
+                }
+                sufd[J.off_suf + pos] = (float)dv;
+            }
             if (prec == BT_PREC_FP64) {
                 suf64[J.off_suf + pos] = v;
             } else {
@@ -243,6 +258,7 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
             if (pos - J.goff[k] >= binom_small(J.L, k)) {
                 if (prec == BT_PREC_FP64) suf64[J.off_suf + pos] = nan("");
                 else suf32[J.off_suf + pos] = make_float2(__int_as_float(0x7fc00000), 0.0f);
+                if (sufd) sufd[J.off_suf + pos] = 0.0f;
             }
             continue;
         }
@@ -281,6 +297,16 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
 __device__ __forceinline__ df32 pw2(const bt_pow *t, int e) {
     bt_pow v = t[e];
     return df_make(v.hi, v.lo);
+}
+
+struct neu_fwd {
+    double s, c;
+};
+__device__ __forceinline__ void neu_fwd_add(neu_fwd &a, double x) {
+    const double t = a.s + x;
+    if (fabs(a.s) >= fabs(x)) a.c += (a.s - t) + x;
+    else a.c += (x - t) + a.s;
+    a.s = t;
 }
 
 struct pref32 {
@@ -701,6 +727,251 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_exact64(bt_exact_args a) {
 }
 
 // ---------------------------------------------------------------------------
+// Pathwise derivatives of eq. f13 (the adjoint pass behind the Greeks)
+//
+// With payoff = C + beta * max(s (tau + f), 0) = C + max(s (a + b f), 0)
+// (a = beta tau, b = beta, s = +1 call / -1 put), for one prefix and all its
+// suffixes (sum_s w_s = 1):
+//   sum_s w_s d payoff/du = C' + s (a' N_w + b' F_w + b F'_w),
+//   N_w = sum_ITM w_s, F_w = sum_ITM w_s f_s, F'_w = sum_ITM w_s df_s/du;
+//   sum_s w_s 1[payoff > 0] = 1 if C > 0 else N_w;
+//   sum_s w_s k_s payoff = (beta/lambda) sum_k k W(k) G_k + C L p.
+// The kernel accumulates these per prefix next to the value; the host turns
+// them into dV/dS0, dV/dsigma, dV/drate, dV/dK by the chain rule through u, p.
+// ---------------------------------------------------------------------------
+struct prefd {
+    float b, bp, ap, Cp, C;
+};
+
+__device__ __forceinline__ prefd prefix_deriv(const bt_job &J, const bt_jparams &P, const bt_exact_args &a,
+                                              int64_t q) {
+    prefd r;
+    const int64_t h = q >> J.M;
+    const int m = (int)(q & ((1ll << J.M) - 1));
+    const bt_pentry eh = a.ph[J.off_ph + h];
+    const bt_pentry em = a.pm[J.off_pm + m];
+    const int lvl = eh.lvl + em.lvl;
+    const bt_pow *pw = a.pw + J.off_pow + J.N + 1;
+    const float u = (float)P.u, S0 = (float)P.S0, K = (float)P.K, N = (float)J.N;
+    const float SP = S0 * pw[lvl].hi;
+    r.b = SP;
+    r.bp = (float)lvl * SP / u;
+    r.ap = 0.0f;
+    r.Cp = 0.0f;
+    r.C = 0.0f;
+    switch (J.field) {
+    case BT_F_ARITH: {
+        // a = Sigma_P/N - K, a' = S_P Q_P / (N u), Q_P = u^{-Delta_m} Q_h + l_H R_m + Q_m
+        const float QP = pw[-em.lvl].hi * eh.Q + (float)eh.lvl * em.R_hi + em.Q;
+        r.b = SP / N;
+        r.bp = (float)lvl * SP / (N * u);
+        r.ap = SP * QP / (N * u);
+        break;
+    }
+    case BT_F_GEO: {
+        const int I = (int)eh.D + J.M * (int)eh.lvl + (int)em.D + J.L * lvl;
+        const bt_pow *g = a.pw + J.off_geo - J.geo_imin;
+        const float c = S0 * g[I].hi;
+        r.b = c;
+        r.bp = c * (float)I / (N * u);
+        break;
+    }
+    case BT_F_EURO:
+        break;
+    case BT_F_LOOKMAX: {
+        const int lam = max((int)eh.mx, (int)eh.lvl + (int)em.mx);
+        if (lam > -BT_LVL_NONE / 2) {
+            const float M = S0 * pw[lam].hi;
+            if (M > K) {
+                r.ap = -(float)lam * M / u;
+                r.Cp = (float)lam * M / u;
+                r.C = M - K;
+            }
+        }
+        break;
+    }
+    default: {
+        const int lam = min((int)eh.mn, (int)eh.lvl + (int)em.mn);
+        if (lam < BT_LVL_NONE / 2) {
+            const float M = S0 * pw[lam].hi;
+            if (M < K) {
+                r.ap = -(float)lam * M / u;
+                r.Cp = -(float)lam * M / u;
+                r.C = K - M;
+            }
+        }
+        break;
+    }
+    }
+    return r;
+}
+
+template <int MODE>
+__device__ __forceinline__ void item_greeks(const bt_exact_args &a, const smem_job &sj, const float2 *s_suf,
+                                            const float *s_sufd, double *red4) {
+    const bt_job &J = sj.J;
+    const bt_jparams &P = sj.P;
+    const int64_t item_local = sj.item - J.item_begin;
+    const int64_t qbase = item_local << BT_LOW_BITS;
+    const int64_t nP = 1ll << J.P;
+    float B[BT_PT], Ah[BT_PT], nAl[BT_PT];
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) {
+        const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
+        pref32 pr = prefix32(J, P, a, q, q < nP);
+        B[j] = pr.B;
+        Ah[j] = pr.Ah;
+        nAl[j] = pr.nAl;
+    }
+    df32 accV[BT_PT], accK[BT_PT], Fw[BT_PT], Dw[BT_PT];
+    float Nw[BT_PT];
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) {
+        accV[j] = accK[j] = Fw[j] = Dw[j] = df_make(0.0f, 0.0f);
+        Nw[j] = 0.0f;
+    }
+    for (int k = 0; k <= J.L; ++k) {
+        const int s0 = J.goff[k], s1 = J.goff[k + 1];
+        // group sums as (sum, compensation) pairs; the count is exact in FP32
+        float g[BT_PT], e[BT_PT], cn[BT_PT], cf[BT_PT], ef[BT_PT], cd[BT_PT], ed[BT_PT];
+#pragma unroll
+        for (int j = 0; j < BT_PT; ++j) g[j] = e[j] = cn[j] = cf[j] = ef[j] = cd[j] = ed[j] = 0.0f;
+        for (int s = s0; s < s1; s += BT_UNROLL) {
+            float4 f4[BT_UNROLL / 2], d4[BT_UNROLL / 4];
+#pragma unroll
+            for (int i = 0; i < BT_UNROLL / 2; ++i) f4[i] = *reinterpret_cast<const float4 *>(s_suf + s + 2 * i);
+#pragma unroll
+            for (int i = 0; i < BT_UNROLL / 4; ++i) d4[i] = *reinterpret_cast<const float4 *>(s_sufd + s + 4 * i);
+            const float fh[BT_UNROLL] = {f4[0].x, f4[0].z, f4[1].x, f4[1].z, f4[2].x, f4[2].z, f4[3].x, f4[3].z};
+            const float fl[BT_UNROLL] = {f4[0].y, f4[0].w, f4[1].y, f4[1].w, f4[2].y, f4[2].w, f4[3].y, f4[3].w};
+            const float fd[BT_UNROLL] = {d4[0].x, d4[0].y, d4[0].z, d4[0].w, d4[1].x, d4[1].y, d4[1].z, d4[1].w};
+            float ff[BT_UNROLL];
+#pragma unroll
+            for (int i = 0; i < BT_UNROLL; ++i) ff[i] = __fsub_rn(fh[i], fl[i]);  // f = f_hi - (-f_lo)
+#pragma unroll
+            for (int j = 0; j < BT_PT; ++j) {
+                float z[BT_UNROLL], tf[BT_UNROLL], td[BT_UNROLL];
+#pragma unroll
+                for (int i = 0; i < BT_UNROLL; ++i) {
+                    const float y = __fmaf_rn(B[j], fh[i], Ah[j]);
+                    const float c = __fmaf_rn(B[j], fl[i], nAl[j]);
+                    z[i] = (MODE & BT_MODE_CALL) ? __saturatef(__fsub_rn(y, c)) : __saturatef(__fsub_rn(c, y));
+                    // in the money (the NaN padding saturates to 0 and is never selected)
+                    const bool itm = z[i] > 0.0f;
+                    cn[j] += itm ? 1.0f : 0.0f;
+                    tf[i] = itm ? ff[i] : 0.0f;
+                    td[i] = itm ? fd[i] : 0.0f;
+                }
+#pragma unroll
+                for (int w = 1; w < BT_UNROLL; w *= 2)
+#pragma unroll
+                    for (int i = 0; i < BT_UNROLL; i += 2 * w) {
+                        z[i] = __fadd_rn(z[i], z[i + w]);
+                        tf[i] = __fadd_rn(tf[i], tf[i + w]);
+                        td[i] = __fadd_rn(td[i], td[i + w]);
+                    }
+                float sN = __fadd_rn(g[j], z[0]);
+                e[j] = __fadd_rn(e[j], __fsub_rn(z[0], __fsub_rn(sN, g[j])));
+                g[j] = sN;
+                const df32 tsf = two_sum(cf[j], tf[0]);
+                cf[j] = tsf.hi;
+                ef[j] = __fadd_rn(ef[j], tsf.lo);
+                const df32 tsd = two_sum(cd[j], td[0]);
+                cd[j] = tsd.hi;
+                ed[j] = __fadd_rn(ed[j], tsd.lo);
+            }
+        }
+        const df32 w = df_from2(P.W2[k]);
+        const float wf = (float)P.W[k];
+#pragma unroll
+        for (int j = 0; j < BT_PT; ++j) {
+            const df32 wg = df_mul(w, fast_two_sum(g[j], e[j]));
+            accV[j] = df_add_pos(accV[j], wg);
+            accK[j] = df_add_pos(accK[j], df_mul_f(wg, (float)k));
+            Nw[j] = __fmaf_rn(wf, cn[j], Nw[j]);
+            Fw[j] = df_add(Fw[j], df_mul(w, two_sum(cf[j], ef[j])));
+            Dw[j] = df_add(Dw[j], df_mul(w, two_sum(cd[j], ed[j])));
+        }
+    }
+    const double sgn = (MODE & BT_MODE_CALL) ? 1.0 : -1.0;
+    double tV = 0.0, tK = 0.0, tD = 0.0, tP = 0.0;
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) {
+        const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
+        if (q >= nP) continue;
+        const pref32 pr = prefix32(J, P, a, q, true);
+        const prefd dv = prefix_deriv(J, P, a, q);
+        const double wl = P.wl[__popc((unsigned)(q & ((1 << BT_LOW_BITS) - 1)))];
+        const double kq = (double)__popcll((unsigned long long)q);
+        const double cq = df_to_double(pr.cst);  // w_low * C as an FP32 pair, as in the value kernel
+        const double Vq = df_to_double(df_mul(pr.om, accV[j])) + cq;
+        tV += Vq;
+        tK += kq * Vq + df_to_double(df_mul(pr.om, accK[j])) + cq * (double)J.L * P.p;
+        tD += wl * ((double)dv.Cp +
+                    sgn * ((double)dv.ap * Nw[j] + (double)dv.bp * df_to_double(Fw[j]) + (double)dv.b * df_to_double(Dw[j])));
+        tP += wl * (dv.C > 0.0f ? 1.0 : (double)Nw[j]);
+    }
+    // deterministic block sum of four doubles
+    for (int o = 16; o > 0; o >>= 1) {
+        tV += __shfl_down_sync(0xffffffffu, tV, o);
+        tK += __shfl_down_sync(0xffffffffu, tK, o);
+        tD += __shfl_down_sync(0xffffffffu, tD, o);
+        tP += __shfl_down_sync(0xffffffffu, tP, o);
+    }
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red4[4 * wid + 0] = tV;
+        red4[4 * wid + 1] = tK;
+        red4[4 * wid + 2] = tD;
+        red4[4 * wid + 3] = tP;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < BT_THREADS / 32; ++i)
+            for (int c = 0; c < 4; ++c) r[c] += red4[4 * i + c];
+        const double wh = P.wh[__popcll((unsigned long long)item_local)];
+        a.partials4[sj.item] = make_double4(r[0] * wh, r[1] * wh, r[2] * wh, r[3] * wh);
+    }
+}
+
+__global__ void __launch_bounds__(BT_THREADS, 1) k_greeks32(bt_exact_args a) {
+    extern __shared__ float4 smem_raw[];
+    float2 *s_suf = reinterpret_cast<float2 *>(smem_raw);
+    float *s_sufd = reinterpret_cast<float *>(s_suf + BT_SUF_MAX_EVEN);  // 16-byte aligned for float4 loads
+    __shared__ smem_job sj;
+    __shared__ double red4[4 * (BT_THREADS / 32)];
+    int cur_job = -1;
+    for (;;) {
+        const int prev = cur_job;
+        if (!next_item<float2>(a, sj, s_suf, a.suf32, cur_job)) break;
+        if (cur_job != prev) {
+            const float *src = a.sufd + sj.J.off_suf;
+            for (int i = threadIdx.x; i < sj.J.suf_len; i += BT_THREADS) s_sufd[i] = src[i];
+            __syncthreads();
+        }
+        if (sj.J.mode == BT_MODE_CALL) item_greeks<BT_MODE_CALL>(a, sj, s_suf, s_sufd, red4);
+        else item_greeks<BT_MODE_PUT>(a, sj, s_suf, s_sufd, red4);
+    }
+}
+
+// Fixed-order per-job sums of the four partials.
+__global__ void k_greeks_finalize(const bt_job *jobs, int n_jobs, const double4 *partials, double4 *sums) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_jobs) return;
+    const bt_job J = jobs[j];
+    neu_fwd v = {0, 0}, k = {0, 0}, d = {0, 0}, p = {0, 0};
+    for (int i = 0; i < J.n_items; ++i) {
+        const double4 x = partials[J.item_begin + i];
+        neu_fwd_add(v, x.x);
+        neu_fwd_add(k, x.y);
+        neu_fwd_add(d, x.z);
+        neu_fwd_add(p, x.w);
+    }
+    sums[j] = make_double4(v.s + v.c, k.s + k.c, d.s + d.c, p.s + p.c);
+}
+
+// ---------------------------------------------------------------------------
 // a5: per-option reduction of the block partials in a fixed order (eq. f15)
 // ---------------------------------------------------------------------------
 struct neu {
@@ -777,7 +1048,20 @@ extern "C" int bt_launch_tables(const bt_job *d_jobs, const bt_jparams *d_prm, i
     if (bx > 64) bx = 64;
     if (bx < 1) bx = 1;
     dim3 grid(bx, n_jobs);
-    k_tables<<<grid, 256, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, prec, suf32, suf64, ph, pm, pw);
+    k_tables<<<grid, 256, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, prec, suf32, suf64, ph, pm, pw, nullptr);
+    return (int)cudaGetLastError();
+}
+
+extern "C" int bt_launch_tables_d(const bt_job *d_jobs, const bt_jparams *d_prm, int n_jobs, int max_len,
+                                  float2 *suf32, float *sufd, bt_pentry *ph, bt_pentry *pm, bt_pow *pw,
+                                  void *stream) {
+    if (n_jobs <= 0) return 0;
+    int bx = (max_len + 255) / 256;
+    if (bx > 64) bx = 64;
+    if (bx < 1) bx = 1;
+    dim3 grid(bx, n_jobs);
+    k_tables<<<grid, 256, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, BT_PREC_FP32_COMP, suf32, nullptr, ph, pm, pw,
+                                                     sufd);
     return (int)cudaGetLastError();
 }
 
@@ -812,6 +1096,29 @@ extern "C" int bt_launch_exact(const bt_exact_args *a, int prec, int grid, void 
         cudaFuncSetAttribute(k_exact32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_exact32<<<grid, BT_THREADS, sm, (cudaStream_t)stream>>>(*a);
     }
+    return (int)cudaGetLastError();
+}
+
+extern "C" int bt_launch_greeks(const bt_exact_args *a, int grid, void *stream) {
+    if (a->n_run_items <= 0) return 0;
+    const size_t sm = (size_t)BT_SUF_MAX_EVEN * sizeof(float2) + (size_t)BT_SUF_MAX * sizeof(float);
+    cudaFuncSetAttribute(k_greeks32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    {  // persistent grid: every SM's resident blocks, no more
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_greeks32, BT_THREADS, sm);
+        if (sms > 0 && per > 0) grid = sms * per;
+    }
+    if ((int64_t)grid > a->n_run_items) grid = (int)a->n_run_items;
+    k_greeks32<<<grid, BT_THREADS, sm, (cudaStream_t)stream>>>(*a);
+    return (int)cudaGetLastError();
+}
+
+extern "C" int bt_launch_greeks_finalize(const bt_job *d_jobs, int n_jobs, const double4 *partials, double4 *sums,
+                                         void *stream) {
+    if (n_jobs <= 0) return 0;
+    k_greeks_finalize<<<(n_jobs + 63) / 64, 64, 0, (cudaStream_t)stream>>>(d_jobs, n_jobs, partials, sums);
     return (int)cudaGetLastError();
 }
 
