@@ -222,6 +222,56 @@ bt_status bt_price_mc_ex(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t 
  * (host arrays ctr[n][4], key[n][2], out[n][4]); for verification. */
 bt_status bt_philox4x32_10(bt_ctx *ctx, const uint32_t *ctr, const uint32_t *key, uint32_t *out, int32_t n);
 
+/* Continuous-batching pricing server --------------------------------------- */
+/* Not in the paper (its SPMD scheme prices one problem at a time): a server
+ * that prices a stream of single-option requests of mixed N and payoff. A
+ * scheduler thread admits requests in arrival order while a slot is free and
+ * the device pool has room for the request's tables and per-item partials
+ * (admission by memory), keeps up to n_streams path-sum launches in flight,
+ * each over work items of all admitted requests (smallest remaining work
+ * first), and finalises a request with the same fixed-order reduction as
+ * bt_price_exact, so each result is identical alone and in the mix. */
+typedef struct bt_server bt_server;
+typedef struct {
+    int32_t max_active;            /* requests admitted at once (slots); 0 = 256           */
+    int32_t n_streams;             /* path-sum launches in flight; 0 = 3                    */
+    int32_t max_items_per_launch;  /* 2^10-prefix work items per launch; 0 = 1216           */
+    int32_t use_fp64;              /* 0 = BT_PREC_FP32_COMP, 1 = BT_PREC_FP64               */
+    size_t device_budget_bytes;    /* device memory for slots, tables, partials; 0 = 8 GiB */
+} bt_server_cfg;
+typedef struct {
+    int64_t submitted, completed, launches, items;
+    int32_t active, pending;       /* admitted and waiting requests right now              */
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* latency = completion - submission        */
+    double throughput_rps, paths_per_s;     /* over first submission .. last completion */
+    double busy_s;                 /* scheduler time with GPU work in flight               */
+    int32_t peak_active;           /* most requests admitted at one time                   */
+    int32_t reserved;
+    int64_t pool_bytes;            /* device pool for tables and partials                  */
+} bt_server_stats_t;
+
+/* Starts the scheduler thread; allocates device_budget_bytes from the context
+ * (BT_EBUDGET if that exceeds the context's budget). */
+bt_status bt_server_start(bt_ctx *ctx, const bt_server_cfg *cfg, bt_server **out);
+/* Queues one option; returns at once with a ticket. Validation errors as
+ * bt_price_exact; BT_EBUDGET if one request alone exceeds the pool. */
+bt_status bt_submit(bt_server *srv, const bt_option *opt, uint64_t *ticket);
+/* Waits up to timeout_ms for the ticket's result (BT_ETIMEOUT on expiry; the
+ * request stays queued). A ticket can be collected once. */
+bt_status bt_wait(bt_server *srv, uint64_t ticket, int32_t timeout_ms, bt_result *out);
+/* Non-blocking: *done = 1 and the result if finished (collects the ticket). */
+bt_status bt_poll(bt_server *srv, uint64_t ticket, bt_result *out, int32_t *done);
+bt_status bt_server_stats(bt_server *srv, bt_server_stats_t *out);
+/* Finishes all queued requests, stops the thread, frees its memory. */
+bt_status bt_server_stop(bt_server *srv);
+/* Replays an arrival schedule (seconds from the call) of n single-option
+ * requests: mode 1 through a server started with cfg, mode 0 as plain
+ * pricing -- one bt_price_exact per request in arrival order. results are in
+ * request order; latency_ms[i] = completion of request i minus its
+ * scheduled arrival, on the same clock for both modes; wall_s the span. */
+bt_status bt_serve_replay(bt_ctx *ctx, const bt_server_cfg *cfg, const bt_option *opts, const double *arrival_s,
+                          int32_t n, int32_t mode, bt_result *results, double *latency_ms, double *wall_s);
+
 /* Allocation-free exhaustive pricing --------------------------------------- */
 /* The paper has no counterpart: this exists for callers that cannot allocate
  * device memory while they run -- for example an application whose own

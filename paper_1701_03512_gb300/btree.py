@@ -52,6 +52,19 @@ class bt_exact_plan_info(C.Structure):
                 ("h2d_bytes", C.c_size_t), ("d2h_bytes", C.c_size_t)]
 
 
+class bt_server_cfg(C.Structure):
+    _fields_ = [("max_active", C.c_int32), ("n_streams", C.c_int32), ("max_items_per_launch", C.c_int32),
+                ("use_fp64", C.c_int32), ("device_budget_bytes", C.c_size_t)]
+
+
+class bt_server_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("launches", C.c_int64),
+                ("items", C.c_int64), ("active", C.c_int32), ("pending", C.c_int32), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
+                ("throughput_rps", C.c_double), ("paths_per_s", C.c_double), ("busy_s", C.c_double),
+                ("peak_active", C.c_int32), ("reserved", C.c_int32), ("pool_bytes", C.c_int64)]
+
+
 OPTION_DTYPE = np.dtype([("N", "<i4"), ("tree_kind", "<i4"), ("payoff", "<i4"), ("pad", "<i4"),
                          ("S0", "<f8"), ("K", "<f8"), ("rate", "<f8"), ("sigma", "<f8"), ("T", "<f8"),
                          ("u", "<f8"), ("d", "<f8"), ("p", "<f8")])
@@ -101,6 +114,14 @@ def lib():
         _proto(L, "bt_price_mc_ex", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _i32, _vp, _vp, _vp])
         _proto(L, "bt_philox4x32_10", [_vp, _vp, _vp, _vp, _i32])
         _proto(L, "bt_greeks_exact", [_vp, _vp, _i32, C.c_int, _vp, _vp, _vp])
+        _proto(L, "bt_server_start", [_vp, C.POINTER(bt_server_cfg), C.POINTER(_vp)])
+        _proto(L, "bt_submit", [_vp, _vp, C.POINTER(C.c_uint64)])
+        _proto(L, "bt_wait", [_vp, C.c_uint64, _i32, _vp])
+        _proto(L, "bt_poll", [_vp, C.c_uint64, _vp, C.POINTER(_i32)])
+        _proto(L, "bt_server_stats", [_vp, C.POINTER(bt_server_stats_t)])
+        _proto(L, "bt_server_stop", [_vp])
+        _proto(L, "bt_serve_replay", [_vp, C.POINTER(bt_server_cfg), _vp, _vp, _i32, _i32, _vp, _vp,
+                                      C.POINTER(C.c_double)])
         _lib = L
     return _lib
 
@@ -257,6 +278,61 @@ def bt_greeks_exact(ctx, opts, prec=BT_PREC_FP32_COMP, stream=None):
     _check(lib().bt_greeks_exact(ctx, a.ctypes.data, len(a), prec, val.ctypes.data, grad.ctypes.data,
                                  _stream(stream)))
     return val, grad
+
+
+def _cfg(max_active=0, n_streams=0, max_items_per_launch=0, use_fp64=0, device_budget_bytes=0):
+    return bt_server_cfg(max_active, n_streams, max_items_per_launch, use_fp64, device_budget_bytes)
+
+
+def bt_server_start(ctx, **cfg):
+    h = _vp()
+    c = _cfg(**cfg)
+    _check(lib().bt_server_start(ctx, C.byref(c), C.byref(h)))
+    return h
+
+
+def bt_submit(srv, opt) -> int:
+    a = options_array(opt)
+    t = C.c_uint64()
+    _check(lib().bt_submit(srv, a.ctypes.data, C.byref(t)))
+    return t.value
+
+
+def bt_wait(srv, ticket, timeout_ms=60000) -> np.ndarray:
+    out = np.zeros(1, dtype=RESULT_DTYPE)
+    _check(lib().bt_wait(srv, ticket, timeout_ms, out.ctypes.data))
+    return out[0]
+
+
+def bt_poll(srv, ticket):
+    out = np.zeros(1, dtype=RESULT_DTYPE)
+    done = _i32()
+    _check(lib().bt_poll(srv, ticket, out.ctypes.data, C.byref(done)))
+    return (out[0] if done.value else None)
+
+
+def bt_server_stats(srv) -> dict:
+    st = bt_server_stats_t()
+    _check(lib().bt_server_stats(srv, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in bt_server_stats_t._fields_}
+
+
+def bt_server_stop(srv):
+    _check(lib().bt_server_stop(srv))
+
+
+def bt_serve_replay(ctx, opts, arrival_s, mode, **cfg):
+    """mode 1: through a server; mode 0: one bt_price_exact per request (FIFO).
+    Returns (results in request order, latencies in ms, wall seconds)."""
+    a = options_array(opts)
+    arr = np.ascontiguousarray(np.asarray(arrival_s, dtype=np.float64))
+    out = np.zeros(len(a), dtype=RESULT_DTYPE)
+    lat = np.zeros(len(a))
+    wall = C.c_double()
+    c = _cfg(**cfg)
+    _check(lib().bt_serve_replay(ctx, C.byref(c), a.ctypes.data, arr.ctypes.data, len(a), mode, out.ctypes.data,
+                                 lat.ctypes.data, C.byref(wall)))
+    return out, lat, wall.value
 
 
 BT_NOALLOC_SCRATCH_BYTES = 8 << 20

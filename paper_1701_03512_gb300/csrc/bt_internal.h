@@ -37,7 +37,10 @@ struct bt_job {
     int32_t geo_imin, geo_len;
     int32_t n_items;          // ceil(2^P / 2^BT_LOW_BITS)
     int32_t pad0;
-    int64_t item_begin;       // first global work item of this job
+    int64_t item_begin;       // first work item of this job in the launch's numbering
+    int64_t item_offset;      // job-local index of that first item (0 unless a launch covers part of a job)
+    int64_t part_off;         // index of the job's item 0 in the partials array
+    int64_t prm_off;          // index of the job's parameters in the parameter array
     int64_t off_suf;          // element offset in the suffix arena
     int64_t off_ph, off_pm;   // entry offsets in the prefix-table arena
     int64_t off_pow, off_geo; // entry offsets in the power-table arena

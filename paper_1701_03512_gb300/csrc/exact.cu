@@ -138,7 +138,7 @@ __global__ void k_params(const bt_option *opts, const bt_job *jobs, bt_jparams *
     int ef;
     frexp(P.fmax, &ef);  // fmax <= 2^ef
     P.gexp = ef - 10;
-    prm[j] = P;
+    prm[J.prm_off] = P;
 }
 
 // ---------------------------------------------------------------------------
@@ -199,7 +199,8 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
                          bt_pentry *ph, bt_pentry *pm, bt_pow *pw, float *sufd) {
     const int j = blockIdx.y;
     const bt_job J = jobs[j];
-    const double u = prm[j].u, d = prm[j].d, lnu = prm[j].lnu;
+    const bt_jparams &Pj = prm[J.prm_off];
+    const double u = Pj.u, d = Pj.d, lnu = Pj.lnu;
     const int64_t nsuf = 1ll << J.L, nh = 1ll << J.H, nm = 1ll << J.M;
     const int64_t npow = 2 * J.N + 3;
     const int64_t total = nsuf + J.suf_len + nh + nm + npow + J.geo_len;
@@ -245,7 +246,7 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
                 suf64[J.off_suf + pos] = v;
             } else {
                 // f_hi on the grid 2^gexp (exact in FP32), f_lo the exact remainder
-                const int gx = prm[j].gexp;
+                const int gx = Pj.gexp;
                 const double fh = ldexp(rint(ldexp(v, -gx)), gx);
                 suf32[J.off_suf + pos] = make_float2((float)fh, -(float)(v - fh));  // (f_hi, -f_lo)
             }
@@ -462,7 +463,7 @@ __device__ __forceinline__ bool next_item(const bt_exact_args &a, smem_job &sj, 
         cur_job = sj.job;
         if (threadIdx.x == 0) {
             sj.J = a.jobs[cur_job];
-            sj.P = a.prm[cur_job];
+            sj.P = a.prm[sj.J.prm_off];
         }
         __syncthreads();
         const SufT *src = g_suf + sj.J.off_suf;
@@ -477,7 +478,7 @@ __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &s
                                        double2 *red) {
     const bt_job &J = sj.J;
     const bt_jparams &P = sj.P;
-    const int64_t item_local = sj.item - J.item_begin;
+    const int64_t item_local = sj.item - J.item_begin + J.item_offset;
     const int64_t qbase = item_local << BT_LOW_BITS;
     const int64_t nP = 1ll << J.P;
 
@@ -564,7 +565,7 @@ __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &s
     double2 s = block_sum2(vc, vp, red);
     if (threadIdx.x == 0) {
         const double wh = P.wh[__popcll((unsigned long long)item_local)];
-        a.partials[sj.item] = make_double2(s.x * wh, s.y * wh);
+        a.partials[J.part_off + item_local] = make_double2(s.x * wh, s.y * wh);
     }
 }
 
@@ -660,7 +661,7 @@ __device__ __forceinline__ void item64(const bt_exact_args &a, const smem_job &s
                                        double2 *red) {
     const bt_job &J = sj.J;
     const bt_jparams &P = sj.P;
-    const int64_t item_local = sj.item - J.item_begin;
+    const int64_t item_local = sj.item - J.item_begin + J.item_offset;
     const int64_t qbase = item_local << BT_LOW_BITS;
     const int64_t nP = 1ll << J.P;
     double tau[BT_PT64], om[BT_PT64], cst = 0.0;
@@ -708,7 +709,7 @@ __device__ __forceinline__ void item64(const bt_exact_args &a, const smem_job &s
     double2 s = block_sum2(vc, vp, red);
     if (threadIdx.x == 0) {
         const double wh = P.wh[__popcll((unsigned long long)item_local)];
-        a.partials[sj.item] = make_double2(s.x * wh, s.y * wh);
+        a.partials[J.part_off + item_local] = make_double2(s.x * wh, s.y * wh);
     }
 }
 
@@ -811,7 +812,7 @@ __device__ __forceinline__ void item_greeks(const bt_exact_args &a, const smem_j
                                             const float *s_sufd, double *red4) {
     const bt_job &J = sj.J;
     const bt_jparams &P = sj.P;
-    const int64_t item_local = sj.item - J.item_begin;
+    const int64_t item_local = sj.item - J.item_begin + J.item_offset;
     const int64_t qbase = item_local << BT_LOW_BITS;
     const int64_t nP = 1ll << J.P;
     float B[BT_PT], Ah[BT_PT], nAl[BT_PT];
@@ -931,7 +932,7 @@ __device__ __forceinline__ void item_greeks(const bt_exact_args &a, const smem_j
         for (int i = 0; i < BT_THREADS / 32; ++i)
             for (int c = 0; c < 4; ++c) r[c] += red4[4 * i + c];
         const double wh = P.wh[__popcll((unsigned long long)item_local)];
-        a.partials4[sj.item] = make_double4(r[0] * wh, r[1] * wh, r[2] * wh, r[3] * wh);
+        a.partials4[J.part_off + item_local] = make_double4(r[0] * wh, r[1] * wh, r[2] * wh, r[3] * wh);
     }
 }
 
@@ -962,7 +963,7 @@ __global__ void k_greeks_finalize(const bt_job *jobs, int n_jobs, const double4 
     const bt_job J = jobs[j];
     neu_fwd v = {0, 0}, k = {0, 0}, d = {0, 0}, p = {0, 0};
     for (int i = 0; i < J.n_items; ++i) {
-        const double4 x = partials[J.item_begin + i];
+        const double4 x = partials[J.part_off + i];
         neu_fwd_add(v, x.x);
         neu_fwd_add(k, x.y);
         neu_fwd_add(d, x.z);
@@ -992,7 +993,7 @@ __global__ void k_finalize(const bt_job *jobs, const bt_jparams *prm, int n_jobs
     const bt_job J = jobs[j];
     neu c = {0.0, 0.0}, p = {0.0, 0.0};
     for (int i = lane; i < J.n_items; i += 32) {
-        double2 v = partials[J.item_begin + i];
+        double2 v = partials[J.part_off + i];
         neu_add(c, v.x);
         neu_add(p, v.y);
     }
@@ -1006,7 +1007,7 @@ __global__ void k_finalize(const bt_job *jobs, const bt_jparams *prm, int n_jobs
         p.c += pc;
     }
     if (lane == 0) {
-        const double disc = prm[j].disc;
+        const double disc = prm[J.prm_off].disc;
         const double rel = prec == BT_PREC_FP64 ? 1e-13 : 1e-9;
         const int64_t paths = 1ll << J.N;
         if (J.out_call >= 0) {

@@ -59,6 +59,9 @@ extern "C" bt_status bt_greeks_exact(bt_ctx *ctx, const bt_option *opts, int32_t
         J.out_call = J.out_call >= 0 ? i : -1;
         J.out_put = J.out_put >= 0 ? i : -1;
         J.item_begin = items;
+        J.item_offset = 0;
+        J.part_off = items;
+        J.prm_off = i;
         J.off_suf = suf;
         J.off_ph = ph;
         J.off_pm = pm;

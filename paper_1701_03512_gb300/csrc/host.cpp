@@ -83,6 +83,7 @@ extern "C" void bt_destroy(bt_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->cache) ctx_free(c, c->cache, c->cache_bytes);
     cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -287,6 +288,7 @@ struct bt_exact_plan {
     unsigned long long *d_counter;
     cudaEvent_t ev0, ev1;
     bool timed;
+    bool cached;  // arena borrowed from the context's scratch (not freed by destroy)
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -331,6 +333,9 @@ bt_status plan_jobs(const bt_option *opts, int n, int prec, std::vector<bt_job> 
         }
         fill_job_shape(J, opts[i].N, field, mode);
         J.item_begin = items;
+        J.item_offset = 0;
+        J.part_off = items;
+        J.prm_off = (int64_t)jobs.size();
         J.off_suf = suf;
         J.off_ph = ph;
         J.off_pm = pm;
@@ -349,8 +354,17 @@ bt_status plan_jobs(const bt_option *opts, int n, int prec, std::vector<bt_job> 
     return BT_OK;
 }
 
+static bt_status plan_create(bt_ctx *ctx, const bt_option *opts, int32_t n, bt_precision prec, bool cached,
+                             bt_exact_plan **out);
+
 extern "C" bt_status bt_exact_plan_create(bt_ctx *ctx, const bt_option *opts, int32_t n, bt_precision prec,
                                           bt_exact_plan **out) {
+    return plan_create(ctx, opts, n, prec, false, out);
+}
+
+// cached = true borrows the context's scratch (the caller holds cache_mu).
+static bt_status plan_create(bt_ctx *ctx, const bt_option *opts, int32_t n, bt_precision prec, bool cached,
+                             bt_exact_plan **out) {
     if (!ctx || !opts || !out || n < 1) return bt_fail(BT_EINVAL, "bt_exact_plan_create: bad arguments");
     if (prec != BT_PREC_FP64 && prec != BT_PREC_FP32_COMP) return bt_fail(BT_EINVAL, "bad precision %d", (int)prec);
     *out = nullptr;
@@ -389,10 +403,29 @@ extern "C" bt_status bt_exact_plan_create(bt_ctx *ctx, const bt_option *opts, in
     size_t o_cnt = off; off = align256(off + sizeof(unsigned long long));
     cudaSetDevice(ctx->device);
     void *arena = nullptr;
-    s = ctx_alloc(ctx, off, &arena);
-    if (s != BT_OK) {
-        delete pl;
-        return s;
+    if (cached) {
+        if (ctx->cache_bytes < off) {
+            if (ctx->cache) {
+                cudaStreamSynchronize(ctx->stream);
+                ctx_free(ctx, ctx->cache, ctx->cache_bytes);
+                ctx->cache = nullptr;
+                ctx->cache_bytes = 0;
+            }
+            s = ctx_alloc(ctx, off, &ctx->cache);
+            if (s != BT_OK) {
+                delete pl;
+                return s;
+            }
+            ctx->cache_bytes = off;
+        }
+        arena = ctx->cache;
+        pl->cached = true;
+    } else {
+        s = ctx_alloc(ctx, off, &arena);
+        if (s != BT_OK) {
+            delete pl;
+            return s;
+        }
     }
     pl->arena = (char *)arena;
     pl->arena_bytes = off;
@@ -539,7 +572,7 @@ extern "C" bt_status bt_exact_plan_kernel_ms(bt_exact_plan *pl, float *ms) {
 extern "C" void bt_exact_plan_destroy(bt_exact_plan *pl) {
     if (!pl) return;
     cudaSetDevice(pl->ctx->device);
-    if (pl->arena) {
+    if (pl->arena && !pl->cached) {
         cudaStreamSynchronize(pl->ctx->stream);
         ctx_free(pl->ctx, pl->arena, pl->arena_bytes);
     }
@@ -551,8 +584,9 @@ extern "C" void bt_exact_plan_destroy(bt_exact_plan *pl) {
 extern "C" bt_status bt_price_exact(bt_ctx *ctx, const bt_option *opts, int32_t n, bt_precision prec,
                                     bt_result *out, void *stream) {
     if (!ctx || !opts || !out || n < 1) return bt_fail(BT_EINVAL, "bt_price_exact: bad arguments");
+    std::lock_guard<std::mutex> lock(ctx->cache_mu);
     bt_exact_plan *pl = nullptr;
-    bt_status s = bt_exact_plan_create(ctx, opts, n, prec, &pl);
+    bt_status s = plan_create(ctx, opts, n, prec, true, &pl);
     if (s != BT_OK) return s;
     s = bt_exact_plan_run(pl, stream);
     if (s == BT_OK) s = bt_exact_plan_read(pl, out, stream);

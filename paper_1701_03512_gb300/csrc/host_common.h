@@ -7,6 +7,8 @@
 
 #include "bt_internal.h"
 
+#include <mutex>
+
 struct bt_ctx {
     int device;
     size_t budget;
@@ -14,6 +16,10 @@ struct bt_ctx {
     cudaStream_t stream;
     int n_sm;
     int grid32, grid64;
+    // scratch reused by bt_price_exact (grown on demand, freed with the context)
+    std::mutex cache_mu;
+    void *cache;
+    size_t cache_bytes;
 };
 
 bt_status bt_fail(bt_status s, const char *fmt, ...);

@@ -56,6 +56,9 @@ extern "C" bt_status bt_price_exact_noalloc(const bt_option *opts, int32_t n, bt
         int step = 1;
         plan_one_job(opts, n, i, &J, &step);
         J.item_begin = items;
+        J.item_offset = 0;
+        J.part_off = items;
+        J.prm_off = nj;
         J.off_suf = suf;
         J.off_ph = ph;
         J.off_pm = pm;
