@@ -20,6 +20,19 @@ the path sums and the per-option reduction.
   cpu_baseline -- the CPU oracle (plain enumeration, all host cores) on a
             bounded sample of the same workload.
 
+Two further measurements ride on the same line (rank 0, N=1 only):
+  serving -- a Poisson stream of single-option requests (N ~ U{16..34},
+            payoff from {arith call, arith put, geo call, lookback call},
+            parameters as above, seed 2) replayed through the
+            continuous-batching server and as plain one-call-per-request
+            pricing; first both capacities (all requests at t=0), then
+            p50/p99 latency and throughput at offered loads of 0.5/0.8/0.95
+            x the plain capacity, with a check that both modes return
+            bit-identical values;
+  mc      -- Partitioned Monte Carlo, arithmetic Asian call, N=252,
+            2^16 strata x 2^14 Philox samples: samples/s and steps/s against
+            the integer/FP32 issue peak.
+
 Multi-GPU (torchrun): every rank prices its own copy of the batch (weak
 scaling, independent problems, no collective on the data path); the value is
 all ranks' paths over the slowest rank's time.
@@ -41,7 +54,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "exact paths/s at N=36"
+METRIC = "exact paths/s at N=36, % FP32 peak; batched-serving p50/p99 ms vs plain"
 UNIT = "paths/s"
 N_DEFAULT = 36
 SETS_DEFAULT = 64
@@ -60,6 +73,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=10000)
+    ap.add_argument("--serving-loads", default="0.5,0.8,0.95")
+    ap.add_argument("--no-mc", action="store_true")
     return ap.parse_args()
 
 
@@ -216,6 +233,85 @@ def profiled_traffic(N):
 
 
 # ---------------------------------------------------------------------------
+# Serving: continuous batching vs plain pricing on one arrival stream
+# ---------------------------------------------------------------------------
+SERVING_CFG = dict(max_active=256, n_streams=3, max_items_per_launch=1216, device_budget_bytes=8 << 30)
+
+
+def _lat(lat):
+    import numpy as np
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(np.mean(lat)), "max_ms": float(np.max(lat))}
+
+
+def serving_bench(bt, W, ctx, n_req, loads):
+    import numpy as np
+    arr1, opts = W.serving_stream(2, n_req, 1.0)     # arrivals at rate 1/s; scaled per load
+    paths = float(sum(2.0 ** o["N"] for o in opts))
+    zero = np.zeros(n_req)
+    bt.bt_serve_replay(ctx.h, opts[:64], zero[:64], 0)          # warm both paths
+    bt.bt_serve_replay(ctx.h, opts[:64], zero[:64], 1, **SERVING_CFG)
+    rp, _, wall_p = bt.bt_serve_replay(ctx.h, opts, zero, 0)
+    rb, _, wall_b = bt.bt_serve_replay(ctx.h, opts, zero, 1, **SERVING_CFG)
+    cap_p, cap_b = n_req / wall_p, n_req / wall_b
+    out = {"workload": "Poisson stream of %d single-option requests, N~U{16..34}, payoff uniform over "
+                       "{arith Asian call, arith Asian put, geometric Asian call, fixed-strike lookback call}, "
+                       "parameters drawn as the batched sets (seed 2), FP32_COMP" % n_req,
+           "server": dict(SERVING_CFG),
+           "plain": "one synchronous bt_price_exact per request, arrival order, same GPU and precision",
+           "capacity_rps": {"plain": cap_p, "batched": cap_b},
+           "capacity_paths_per_s": {"plain": paths / wall_p, "batched": paths / wall_b},
+           "identical_values": bool(np.array_equal(rp["value"], rb["value"])), "loads": []}
+    for f in loads:
+        lam = f * cap_p
+        arr = arr1 / lam
+        rp, lp, wp = bt.bt_serve_replay(ctx.h, opts, arr, 0)
+        rb, lb, wb = bt.bt_serve_replay(ctx.h, opts, arr, 1, **SERVING_CFG)
+        out["identical_values"] &= bool(np.array_equal(rp["value"], rb["value"]))
+        out["loads"].append({"load_vs_plain_capacity": f, "arrival_rps": lam,
+                             "plain": dict(_lat(lp), throughput_rps=n_req / wp),
+                             "batched": dict(_lat(lb), throughput_rps=n_req / wb)})
+    main = next((x for x in out["loads"] if abs(x["load_vs_plain_capacity"] - 0.8) < 1e-9), None)
+    if main:
+        out["at_0.8"] = {"p50_ms": {"plain": main["plain"]["p50_ms"], "batched": main["batched"]["p50_ms"]},
+                         "p99_ms": {"plain": main["plain"]["p99_ms"], "batched": main["batched"]["p99_ms"]}}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Monte Carlo: Partitioned estimator throughput
+# ---------------------------------------------------------------------------
+MC_OPS_PER_STEP = 19   # Philox-4x32-10 per 4 steps: 10 x (2 wide mul + 2 xor + 2 key adds) = 60; + compare,
+                       # select, multiply, add per step
+
+
+def mc_bench(bt, W, ctx, sms, fmax, reps=3):
+    import torch
+    N, mb, R = 252, 16, 1 << 14
+    o = W.opt(N, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
+    stream = torch.cuda.Stream()
+    bt.bt_price_mc(ctx.h, [o], mb, R, 1, stream)
+    ts = []
+    for i in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = bt.bt_price_mc(ctx.h, [o], mb, R, 2 + i, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.median(ts)
+    samples = float(R) * (1 << mb)
+    steps = samples * (N - mb)
+    peak = sms * 128 * fmax * 1e6
+    return {"workload": "Partitioned MC, arithmetic Asian call, N=%d, S0=K=100, rate 0.05, sigma 0.2, T=1, "
+                        "2^%d strata x %d samples" % (N, mb, R),
+            "samples_per_s": samples / t, "steps_per_s": steps / t, "ms": 1e3 * t,
+            "value": float(r[0]["value"]), "stderr": float(r[0]["stderr_mc"]),
+            "ops_per_step": MC_OPS_PER_STEP, "frac_of_issue_peak": MC_OPS_PER_STEP * steps / t / peak}
+
+
+# ---------------------------------------------------------------------------
 # Reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
 def run_reference(args, rank):
@@ -360,13 +456,21 @@ def main():
         v, sample = cpu_oracle_sample(opts, args.cpu_seconds, threads)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
 
+    serving = mc = None
+    if world == 1 and not args.no_mc:
+        mc = mc_bench(bt, W, ctx, sms, fmax)
+    if world == 1 and not args.no_serving:
+        loads = [float(x) for x in args.serving_loads.split(",") if x]
+        serving = serving_bench(bt, W, ctx, args.serving_requests, loads)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args, {"parallelism": "replicas" if world > 1 else "single GPU",
                                              "wall_s_timed": t_wall}),
             "fp32_peak_frac": roof["frac"], "clocks": clocks, "e2e": e2e,
-            "gpu_launches": 4 * args.steps, "roofline": roof, "cpu_baseline": cpu}
+            "gpu_launches": 4 * args.steps, "roofline": roof, "cpu_baseline": cpu,
+            "serving": serving, "mc": mc}
     print(json.dumps(line), flush=True)
     bt.bt_exact_plan_destroy(plan)
     ctx.close()

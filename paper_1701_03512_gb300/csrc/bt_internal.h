@@ -15,6 +15,8 @@
 #define BT_SUF_MAX ((1 << BT_MAX_L) + (BT_MAX_L + 1) * (BT_UNROLL - 1))
 #define BT_SUF_MAX_EVEN ((BT_SUF_MAX + 1) & ~1)   // float2 count keeping what follows 16-byte aligned
 #define BT_LVL_NONE 30000      // sentinel level: "no price in this block"
+#define BT_CLS_UNROLL 4        // class groups are padded to a multiple of this
+#define BT_KEY_SPAN (BT_MAX_L * (BT_MAX_L + 1) / 2)   // |class key| <= this (level sum of the suffix)
 
 // What the suffix table of a job holds (one field per job).
 enum bt_field {
@@ -36,7 +38,7 @@ struct bt_job {
     int32_t goff[BT_MAX_L + 2];
     int32_t geo_imin, geo_len;
     int32_t n_items;          // ceil(2^P / 2^BT_LOW_BITS)
-    int32_t pad0;
+    int32_t cls;              // 1: suffix table of recombined classes (goff in class units)
     int64_t item_begin;       // first work item of this job in the launch's numbering
     int64_t item_offset;      // job-local index of that first item (0 unless a launch covers part of a job)
     int64_t part_off;         // index of the job's item 0 in the partials array

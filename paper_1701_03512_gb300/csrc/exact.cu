@@ -201,9 +201,11 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
     const bt_job J = jobs[j];
     const bt_jparams &Pj = prm[J.prm_off];
     const double u = Pj.u, d = Pj.d, lnu = Pj.lnu;
-    const int64_t nsuf = 1ll << J.L, nh = 1ll << J.H, nm = 1ll << J.M;
+    // class jobs get their suffix table from k_class_tables
+    const int64_t nsuf = J.cls ? 0 : 1ll << J.L, nsl = J.cls ? 0 : J.suf_len;
+    const int64_t nh = 1ll << J.H, nm = 1ll << J.M;
     const int64_t npow = 2 * J.N + 3;
-    const int64_t total = nsuf + J.suf_len + nh + nm + npow + J.geo_len;
+    const int64_t total = nsuf + nsl + nh + nm + npow + J.geo_len;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = idx;
@@ -253,7 +255,7 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
             continue;
         }
         i -= nsuf;
-        if (i < J.suf_len) {  // padding slots of each up-count group
+        if (i < nsl) {  // padding slots of each up-count group
             int pos = (int)i, k = 0;
             while (k < J.L && pos >= J.goff[k + 1]) ++k;
             if (pos - J.goff[k] >= binom_small(J.L, k)) {
@@ -263,7 +265,7 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
             }
             continue;
         }
-        i -= J.suf_len;
+        i -= nsl;
         if (i < nh) {
             ph[J.off_ph + i] = walk_block((uint64_t)i, J.H, u, d);
             continue;
@@ -292,6 +294,65 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
     }
 }
 
+// Suffix table of recombined classes (the FP32 geometric, European and
+// lookback passes). Within an up-count group every suffix with the same key
+// -- level sum D (f = u^{D/N}), end level (u^{l'_L}), max or min level
+// (u^{max l'}, u^{min l'}) -- has the same f_s and the same weight, so the
+// group's sum over suffixes is a sum over its distinct keys times their
+// multiplicities. One block per job counts the keys of all 2^L suffixes in
+// shared memory and writes, per group in ascending key order, two float2
+// slots per class: (f_hi, f_lo) and (multiplicity, 0); with sufd, the pair
+// (df/du hi, lo). Groups are padded with zero-multiplicity classes. The
+// host plans the same class counts (same keys, same order) for goff.
+#define BT_KEY_RANGE (2 * BT_KEY_SPAN + 1)
+__global__ void k_class_tables(const bt_job *jobs, const bt_jparams *prm, float2 *suf32, float *sufd) {
+    const bt_job J = jobs[blockIdx.x];
+    if (!J.cls) return;
+    __shared__ int hist[(BT_MAX_L + 1) * BT_KEY_RANGE];
+    for (int i = threadIdx.x; i < (J.L + 1) * BT_KEY_RANGE; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (unsigned s = threadIdx.x; s < (1u << J.L); s += blockDim.x) {
+        int lvl = 0, mx = -BT_LVL_NONE, mn = BT_LVL_NONE, D = 0;
+        for (int t = 1; t <= J.L; ++t) {
+            lvl += ((s >> (J.L - t)) & 1u) ? 1 : -1;
+            mx = max(mx, lvl);
+            mn = min(mn, lvl);
+            D += lvl;
+        }
+        const int key = J.field == BT_F_GEO ? D : J.field == BT_F_EURO ? lvl : J.field == BT_F_LOOKMAX ? mx : mn;
+        atomicAdd(&hist[__popc(s) * BT_KEY_RANGE + key + BT_KEY_SPAN], 1);
+    }
+    __syncthreads();
+    const bt_jparams &P = prm[J.prm_off];
+    const double lnu = P.lnu, u = P.u, N = (double)J.N;
+    for (int k = threadIdx.x; k <= J.L; k += blockDim.x) {
+        int pos = J.goff[k];
+        const int end = J.goff[k + 1];
+        for (int key = -BT_KEY_SPAN; key <= BT_KEY_SPAN && pos < end; ++key) {
+            const int c = hist[k * BT_KEY_RANGE + key + BT_KEY_SPAN];
+            if (!c) continue;
+            const double x = J.field == BT_F_GEO ? (double)key / N : (double)key;
+            const double v = exp(x * lnu);
+            suf32[J.off_suf + 2 * pos] = split2(v);
+            suf32[J.off_suf + 2 * pos + 1] = make_float2((float)c, 0.0f);
+            if (sufd) {
+                const float2 dv = split2(v * x / u);
+                sufd[J.off_suf + 2 * pos] = dv.x;
+                sufd[J.off_suf + 2 * pos + 1] = dv.y;
+            }
+            ++pos;
+        }
+        for (; pos < end; ++pos) {
+            suf32[J.off_suf + 2 * pos] = make_float2(0.0f, 0.0f);
+            suf32[J.off_suf + 2 * pos + 1] = make_float2(0.0f, 0.0f);
+            if (sufd) {
+                sufd[J.off_suf + 2 * pos] = 0.0f;
+                sufd[J.off_suf + 2 * pos + 1] = 0.0f;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a3 (per prefix) and a4: the path sums
 // ---------------------------------------------------------------------------
@@ -316,19 +377,13 @@ struct pref32 {
     df32 cst;  // w_low * C (lookback)
 };
 
-// Per-prefix affine coefficients: y = B * (tau + f) with B = 2^-e chosen so that
-// |y| <= 1 over the whole suffix range, so that max(y, 0) is a saturating add.
-__device__ __forceinline__ pref32 prefix32(const bt_job &J, const bt_jparams &P, const bt_exact_args &a,
-                                           int64_t q, bool valid) {
-    pref32 r;
-    if (!valid) {
-        r.B = 0.0f;
-        r.Ah = __int_as_float(0x7fc00000);
-        r.nAl = r.Ah;
-        r.om = df_make(0.0f, 0.0f);
-        r.cst = df_make(0.0f, 0.0f);
-        return r;
-    }
+// Per-prefix affine form of the payoff in the suffix factor f:
+// payoff = beta * max(+-(tau + f), 0) + C, with tau, beta, C as FP32 pairs.
+struct pstate {
+    df32 tau, beta, cst;
+};
+__device__ __forceinline__ pstate prefix_state(const bt_job &J, const bt_jparams &P, const bt_exact_args &a,
+                                               int64_t q) {
     const int64_t h = q >> J.M;
     const int m = (int)(q & ((1ll << J.M) - 1));
     const bt_pentry eh = a.ph[J.off_ph + h];
@@ -387,6 +442,28 @@ __device__ __forceinline__ pref32 prefix32(const bt_job &J, const bt_jparams &P,
         break;
     }
     }
+    pstate st;
+    st.tau = tau;
+    st.beta = beta;
+    st.cst = cst;
+    return st;
+}
+
+// Per-prefix affine coefficients: y = B * (tau + f) with B = 2^-e chosen so that
+// |y| <= 1 over the whole suffix range, so that max(y, 0) is a saturating add.
+__device__ __forceinline__ pref32 prefix32(const bt_job &J, const bt_jparams &P, const bt_exact_args &a,
+                                           int64_t q, bool valid) {
+    pref32 r;
+    if (!valid) {
+        r.B = 0.0f;
+        r.Ah = __int_as_float(0x7fc00000);
+        r.nAl = r.Ah;
+        r.om = df_make(0.0f, 0.0f);
+        r.cst = df_make(0.0f, 0.0f);
+        return r;
+    }
+    const pstate st = prefix_state(J, P, a, q);
+    const df32 tau = st.tau, beta = st.beta, cst = st.cst;
     float m1 = fabsf(__fadd_rn(tau.hi, P.fmin_f)), m2 = fabsf(__fadd_rn(tau.hi, P.fmax_f));
     float mmax = fmaxf(m1, m2) * (1.0f + 0x1p-10f);
     int e = ((__float_as_int(mmax) >> 23) & 0xff) - 126;  // mmax < 2^e
@@ -569,6 +646,103 @@ __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &s
     }
 }
 
+// g += m * (th + tl) for an unnormalised pair (th, tl): exact product of the
+// high part (TwoProd), then TwoSum into g; m is a small integer (or 0).
+__device__ __forceinline__ void acc_pair(df32 &g, float m, float th, float tl) {
+    const df32 p = two_prod(m, th);
+    const float lo = __fmaf_rn(m, tl, p.lo);
+    const df32 t = two_sum(g.hi, p.hi);
+    g.hi = t.hi;
+    g.lo = __fadd_rn(g.lo, __fadd_rn(t.lo, lo));
+}
+
+// Per-prefix pair coefficients of the class pass: tau, w_low * beta and
+// w_low * C (zero for a prefix past the end of the job).
+__device__ __forceinline__ void prefix_cls(const bt_job &J, const bt_jparams &P, const bt_exact_args &a, int64_t q,
+                                           bool valid, df32 &tau, df32 &om, df32 &cst) {
+    if (!valid) {
+        tau = om = cst = df_make(0.0f, 0.0f);
+        return;
+    }
+    const pstate st = prefix_state(J, P, a, q);
+    const df32 wl = df_from2(P.wl2[__popc((unsigned)(q & ((1 << BT_LOW_BITS) - 1)))]);
+    tau = st.tau;
+    om = df_mul(wl, st.beta);
+    cst = df_mul(wl, st.cst);
+}
+
+// One work item over a class table (J.cls): for each prefix and up-count
+// group, sum multiplicity * max(+-(tau + f), 0) over the group's classes with
+// tau + f, the product and the sum all in FP32 pairs, then fold with W(k) as
+// in item32. Identical classes are evaluated once, so there is no repeated
+// FP32 rounding to correlate across the suffixes of a group.
+template <int MODE>
+__device__ __forceinline__ void item32_cls(const bt_exact_args &a, const smem_job &sj, const float2 *s_suf,
+                                           double2 *red) {
+    const bt_job &J = sj.J;
+    const bt_jparams &P = sj.P;
+    const int64_t item_local = sj.item - J.item_begin + J.item_offset;
+    const int64_t qbase = item_local << BT_LOW_BITS;
+    const int64_t nP = 1ll << J.P;
+    const float4 *s_cls = reinterpret_cast<const float4 *>(s_suf);
+
+    df32 tau[BT_PT], om[BT_PT];
+    df32 cst = df_make(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) {
+        const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
+        df32 c;
+        prefix_cls(J, P, a, q, q < nP, tau[j], om[j], c);
+        cst = df_add_pos(cst, c);
+    }
+    df32 accC[BT_PT], accP[BT_PT];
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) accC[j] = accP[j] = df_make(0.0f, 0.0f);
+
+    for (int k = 0; k <= J.L; ++k) {
+        df32 gc[BT_PT], gp[BT_PT];
+#pragma unroll
+        for (int j = 0; j < BT_PT; ++j) gc[j] = gp[j] = df_make(0.0f, 0.0f);
+        for (int s = J.goff[k]; s < J.goff[k + 1]; s += BT_CLS_UNROLL) {
+            float4 e[BT_CLS_UNROLL];
+#pragma unroll
+            for (int i = 0; i < BT_CLS_UNROLL; ++i) e[i] = s_cls[s + i];
+#pragma unroll
+            for (int j = 0; j < BT_PT; ++j) {
+#pragma unroll
+                for (int i = 0; i < BT_CLS_UNROLL; ++i) {
+                    // tau + f as an unnormalised pair; its sign from the rounded sum
+                    const df32 t0 = two_sum(tau[j].hi, e[i].x);
+                    const float tl = __fadd_rn(t0.lo, __fadd_rn(tau[j].lo, e[i].y));
+                    const float ts = __fadd_rn(t0.hi, tl);
+                    if (MODE & BT_MODE_CALL) acc_pair(gc[j], ts > 0.0f ? e[i].z : 0.0f, t0.hi, tl);
+                    if (MODE & BT_MODE_PUT) acc_pair(gp[j], ts < 0.0f ? -e[i].z : 0.0f, t0.hi, tl);
+                }
+            }
+        }
+        const df32 w = df_from2(P.W2[k]);
+#pragma unroll
+        for (int j = 0; j < BT_PT; ++j) {
+            if (MODE & BT_MODE_CALL) accC[j] = df_add_pos(accC[j], df_mul(w, fast_two_sum(gc[j].hi, gc[j].lo)));
+            if (MODE & BT_MODE_PUT) accP[j] = df_add_pos(accP[j], df_mul(w, fast_two_sum(gp[j].hi, gp[j].lo)));
+        }
+    }
+    df32 totC = df_make(0.0f, 0.0f), totP = df_make(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) {
+        if (MODE & BT_MODE_CALL) totC = df_add_pos(totC, df_mul(om[j], accC[j]));
+        if (MODE & BT_MODE_PUT) totP = df_add_pos(totP, df_mul(om[j], accP[j]));
+    }
+    double vc = df_to_double(totC), vp = df_to_double(totP);
+    if (J.field == BT_F_LOOKMAX) vc += df_to_double(cst);
+    if (J.field == BT_F_LOOKMIN) vp += df_to_double(cst);
+    double2 sum = block_sum2(vc, vp, red);
+    if (threadIdx.x == 0) {
+        const double wh = P.wh[__popcll((unsigned long long)item_local)];
+        a.partials[J.part_off + item_local] = make_double2(sum.x * wh, sum.y * wh);
+    }
+}
+
 __global__ void __launch_bounds__(BT_THREADS, 2) k_exact32(bt_exact_args a) {
     extern __shared__ float4 smem_raw[];
     float2 *s_suf = reinterpret_cast<float2 *>(smem_raw);
@@ -576,6 +750,14 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_exact32(bt_exact_args a) {
     __shared__ double2 red[BT_THREADS / 32];
     int cur_job = -1;
     while (next_item<float2>(a, sj, s_suf, a.suf32, cur_job)) {
+        if (sj.J.cls) {
+            switch (sj.J.mode) {
+            case BT_MODE_CALL: item32_cls<BT_MODE_CALL>(a, sj, s_suf, red); break;
+            case BT_MODE_PUT: item32_cls<BT_MODE_PUT>(a, sj, s_suf, red); break;
+            default: item32_cls<BT_MODE_BOTH>(a, sj, s_suf, red); break;
+            }
+            continue;
+        }
         switch (sj.J.mode) {
         case BT_MODE_CALL: item32<BT_MODE_CALL>(a, sj, s_suf, red); break;
         case BT_MODE_PUT: item32<BT_MODE_PUT>(a, sj, s_suf, red); break;
@@ -807,6 +989,66 @@ __device__ __forceinline__ prefd prefix_deriv(const bt_job &J, const bt_jparams 
     return r;
 }
 
+// Per-prefix combination and block sum of the derivative pass: value, the
+// up-count moment (for dV/dp), the u-derivative and the in-the-money mass.
+template <int MODE, bool CLS>
+__device__ __forceinline__ void greeks_tail(const bt_exact_args &a, const smem_job &sj, int64_t item_local,
+                                            const df32 *accV, const df32 *accK, const float *Nw, const df32 *Fw,
+                                            const df32 *Dw, double *red4) {
+    const bt_job &J = sj.J;
+    const bt_jparams &P = sj.P;
+    const int64_t qbase = item_local << BT_LOW_BITS;
+    const int64_t nP = 1ll << J.P;
+    const double sgn = (MODE & BT_MODE_CALL) ? 1.0 : -1.0;
+    double tV = 0.0, tK = 0.0, tD = 0.0, tP = 0.0;
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) {
+        const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
+        if (q >= nP) continue;
+        df32 om, cw;  // w_low * beta (/ lambda in the per-path pass) and w_low * C
+        if (CLS) {
+            df32 tq;
+            prefix_cls(J, P, a, q, true, tq, om, cw);
+        } else {
+            const pref32 pr = prefix32(J, P, a, q, true);
+            om = pr.om;
+            cw = pr.cst;
+        }
+        const prefd dv = prefix_deriv(J, P, a, q);
+        const double wl = P.wl[__popc((unsigned)(q & ((1 << BT_LOW_BITS) - 1)))];
+        const double kq = (double)__popcll((unsigned long long)q);
+        const double cq = df_to_double(cw);  // w_low * C as an FP32 pair, as in the value kernel
+        const double Vq = df_to_double(df_mul(om, accV[j])) + cq;
+        tV += Vq;
+        tK += kq * Vq + df_to_double(df_mul(om, accK[j])) + cq * (double)J.L * P.p;
+        tD += wl * ((double)dv.Cp +
+                    sgn * ((double)dv.ap * Nw[j] + (double)dv.bp * df_to_double(Fw[j]) + (double)dv.b * df_to_double(Dw[j])));
+        tP += wl * (dv.C > 0.0f ? 1.0 : (double)Nw[j]);
+    }
+    // deterministic block sum of four doubles
+    for (int o = 16; o > 0; o >>= 1) {
+        tV += __shfl_down_sync(0xffffffffu, tV, o);
+        tK += __shfl_down_sync(0xffffffffu, tK, o);
+        tD += __shfl_down_sync(0xffffffffu, tD, o);
+        tP += __shfl_down_sync(0xffffffffu, tP, o);
+    }
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red4[4 * wid + 0] = tV;
+        red4[4 * wid + 1] = tK;
+        red4[4 * wid + 2] = tD;
+        red4[4 * wid + 3] = tP;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < BT_THREADS / 32; ++i)
+            for (int c = 0; c < 4; ++c) r[c] += red4[4 * i + c];
+        const double wh = P.wh[__popcll((unsigned long long)item_local)];
+        a.partials4[J.part_off + item_local] = make_double4(r[0] * wh, r[1] * wh, r[2] * wh, r[3] * wh);
+    }
+}
+
 template <int MODE>
 __device__ __forceinline__ void item_greeks(const bt_exact_args &a, const smem_job &sj, const float2 *s_suf,
                                             const float *s_sufd, double *red4) {
@@ -894,46 +1136,72 @@ __device__ __forceinline__ void item_greeks(const bt_exact_args &a, const smem_j
             Dw[j] = df_add(Dw[j], df_mul(w, two_sum(cd[j], ed[j])));
         }
     }
-    const double sgn = (MODE & BT_MODE_CALL) ? 1.0 : -1.0;
-    double tV = 0.0, tK = 0.0, tD = 0.0, tP = 0.0;
+    greeks_tail<MODE, false>(a, sj, item_local, accV, accK, Nw, Fw, Dw, red4);
+}
+
+// Derivative pass over a class table: per class the in-the-money test and
+// the sums of multiplicity x (payoff, 1, f, df/du) in FP32 pairs.
+template <int MODE>
+__device__ __forceinline__ void item_greeks_cls(const bt_exact_args &a, const smem_job &sj, const float2 *s_suf,
+                                                const float *s_sufd, double *red4) {
+    const bt_job &J = sj.J;
+    const bt_jparams &P = sj.P;
+    const int64_t item_local = sj.item - J.item_begin + J.item_offset;
+    const int64_t qbase = item_local << BT_LOW_BITS;
+    const int64_t nP = 1ll << J.P;
+    const float4 *s_cls = reinterpret_cast<const float4 *>(s_suf);
+    const float2 *s_cd = reinterpret_cast<const float2 *>(s_sufd);
+    df32 tau[BT_PT];
 #pragma unroll
     for (int j = 0; j < BT_PT; ++j) {
         const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
-        if (q >= nP) continue;
-        const pref32 pr = prefix32(J, P, a, q, true);
-        const prefd dv = prefix_deriv(J, P, a, q);
-        const double wl = P.wl[__popc((unsigned)(q & ((1 << BT_LOW_BITS) - 1)))];
-        const double kq = (double)__popcll((unsigned long long)q);
-        const double cq = df_to_double(pr.cst);  // w_low * C as an FP32 pair, as in the value kernel
-        const double Vq = df_to_double(df_mul(pr.om, accV[j])) + cq;
-        tV += Vq;
-        tK += kq * Vq + df_to_double(df_mul(pr.om, accK[j])) + cq * (double)J.L * P.p;
-        tD += wl * ((double)dv.Cp +
-                    sgn * ((double)dv.ap * Nw[j] + (double)dv.bp * df_to_double(Fw[j]) + (double)dv.b * df_to_double(Dw[j])));
-        tP += wl * (dv.C > 0.0f ? 1.0 : (double)Nw[j]);
+        df32 om, cw;
+        prefix_cls(J, P, a, q, q < nP, tau[j], om, cw);
     }
-    // deterministic block sum of four doubles
-    for (int o = 16; o > 0; o >>= 1) {
-        tV += __shfl_down_sync(0xffffffffu, tV, o);
-        tK += __shfl_down_sync(0xffffffffu, tK, o);
-        tD += __shfl_down_sync(0xffffffffu, tD, o);
-        tP += __shfl_down_sync(0xffffffffu, tP, o);
+    df32 accV[BT_PT], accK[BT_PT], Fw[BT_PT], Dw[BT_PT];
+    float Nw[BT_PT];
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) {
+        accV[j] = accK[j] = Fw[j] = Dw[j] = df_make(0.0f, 0.0f);
+        Nw[j] = 0.0f;
     }
-    const int wid = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        red4[4 * wid + 0] = tV;
-        red4[4 * wid + 1] = tK;
-        red4[4 * wid + 2] = tD;
-        red4[4 * wid + 3] = tP;
+    for (int k = 0; k <= J.L; ++k) {
+        df32 g[BT_PT], cf[BT_PT], cd[BT_PT];
+        float cn[BT_PT];
+#pragma unroll
+        for (int j = 0; j < BT_PT; ++j) {
+            g[j] = cf[j] = cd[j] = df_make(0.0f, 0.0f);
+            cn[j] = 0.0f;
+        }
+        for (int s = J.goff[k]; s < J.goff[k + 1]; ++s) {
+            const float4 e = s_cls[s];
+            const float2 fd = s_cd[s];
+#pragma unroll
+            for (int j = 0; j < BT_PT; ++j) {
+                const df32 t0 = two_sum(tau[j].hi, e.x);
+                const float tl = __fadd_rn(t0.lo, __fadd_rn(tau[j].lo, e.y));
+                const float ts = __fadd_rn(t0.hi, tl);
+                const bool itm = (MODE & BT_MODE_CALL) ? ts > 0.0f : ts < 0.0f;
+                const float m = itm ? e.z : 0.0f;
+                acc_pair(g[j], (MODE & BT_MODE_CALL) ? m : -m, t0.hi, tl);
+                cn[j] += m;
+                acc_pair(cf[j], m, e.x, e.y);
+                acc_pair(cd[j], m, fd.x, fd.y);
+            }
+        }
+        const df32 w = df_from2(P.W2[k]);
+        const float wf = (float)P.W[k];
+#pragma unroll
+        for (int j = 0; j < BT_PT; ++j) {
+            const df32 wg = df_mul(w, fast_two_sum(g[j].hi, g[j].lo));
+            accV[j] = df_add_pos(accV[j], wg);
+            accK[j] = df_add_pos(accK[j], df_mul_f(wg, (float)k));
+            Nw[j] = __fmaf_rn(wf, cn[j], Nw[j]);
+            Fw[j] = df_add(Fw[j], df_mul(w, fast_two_sum(cf[j].hi, cf[j].lo)));
+            Dw[j] = df_add(Dw[j], df_mul(w, two_sum(cd[j].hi, cd[j].lo)));
+        }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double r[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int i = 0; i < BT_THREADS / 32; ++i)
-            for (int c = 0; c < 4; ++c) r[c] += red4[4 * i + c];
-        const double wh = P.wh[__popcll((unsigned long long)item_local)];
-        a.partials4[J.part_off + item_local] = make_double4(r[0] * wh, r[1] * wh, r[2] * wh, r[3] * wh);
-    }
+    greeks_tail<MODE, true>(a, sj, item_local, accV, accK, Nw, Fw, Dw, red4);
 }
 
 __global__ void __launch_bounds__(BT_THREADS, 1) k_greeks32(bt_exact_args a) {
@@ -951,8 +1219,14 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_greeks32(bt_exact_args a) {
             for (int i = threadIdx.x; i < sj.J.suf_len; i += BT_THREADS) s_sufd[i] = src[i];
             __syncthreads();
         }
-        if (sj.J.mode == BT_MODE_CALL) item_greeks<BT_MODE_CALL>(a, sj, s_suf, s_sufd, red4);
-        else item_greeks<BT_MODE_PUT>(a, sj, s_suf, s_sufd, red4);
+        if (sj.J.cls) {
+            if (sj.J.mode == BT_MODE_CALL) item_greeks_cls<BT_MODE_CALL>(a, sj, s_suf, s_sufd, red4);
+            else item_greeks_cls<BT_MODE_PUT>(a, sj, s_suf, s_sufd, red4);
+        } else if (sj.J.mode == BT_MODE_CALL) {
+            item_greeks<BT_MODE_CALL>(a, sj, s_suf, s_sufd, red4);
+        } else {
+            item_greeks<BT_MODE_PUT>(a, sj, s_suf, s_sufd, red4);
+        }
     }
 }
 
@@ -1050,6 +1324,8 @@ extern "C" int bt_launch_tables(const bt_job *d_jobs, const bt_jparams *d_prm, i
     if (bx < 1) bx = 1;
     dim3 grid(bx, n_jobs);
     k_tables<<<grid, 256, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, prec, suf32, suf64, ph, pm, pw, nullptr);
+    if (prec == BT_PREC_FP32_COMP)
+        k_class_tables<<<n_jobs, 256, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, suf32, nullptr);
     return (int)cudaGetLastError();
 }
 
@@ -1063,6 +1339,7 @@ extern "C" int bt_launch_tables_d(const bt_job *d_jobs, const bt_jparams *d_prm,
     dim3 grid(bx, n_jobs);
     k_tables<<<grid, 256, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, BT_PREC_FP32_COMP, suf32, nullptr, ph, pm, pw,
                                                      sufd);
+    k_class_tables<<<n_jobs, 256, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, suf32, sufd);
     return (int)cudaGetLastError();
 }
 

@@ -214,7 +214,55 @@ static void payoff_field(int payoff, int *field, int *mode) {
 
 int exact_split_L(int N) { return std::max(1, std::min(BT_MAX_L, N - BT_LOW_BITS)); }
 
-void fill_job_shape(bt_job &J, int N, int field, int mode) {
+// Recombined suffix classes. For the geometric, European and lookback
+// payoffs the suffix factor f_s depends on the suffix only through one
+// integer key (level sum, end level, max or min level), so within an up-count
+// group (same weight) the suffixes fall into a few classes of equal f_s: at
+// L = 12, 13 (European), <= 91 (lookback) or 299 (geometric) classes instead
+// of 4096 suffixes. The FP32 pass then sums multiplicity x payoff over the
+// classes in pair arithmetic. The key, its definition and the ordering
+// (groups by up-count, keys ascending) are shared with k_class_tables.
+static int suffix_key(int field, unsigned s, int L) {
+    int lvl = 0, mx = -BT_LVL_NONE, mn = BT_LVL_NONE, D = 0;
+    for (int t = 1; t <= L; ++t) {
+        lvl += ((s >> (L - t)) & 1u) ? 1 : -1;
+        mx = std::max(mx, lvl);
+        mn = std::min(mn, lvl);
+        D += lvl;
+    }
+    switch (field) {
+    case BT_F_GEO: return D;
+    case BT_F_EURO: return lvl;
+    case BT_F_LOOKMAX: return mx;
+    default: return mn;
+    }
+}
+
+static bool field_has_classes(int field) { return field != BT_F_ARITH; }
+
+// Number of distinct keys per up-count group, for every field and L (cached).
+static const int *class_counts(int field, int L) {
+    static int table[5][BT_MAX_L + 1][BT_MAX_L + 1];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (int f = 0; f < 5; ++f) {
+            if (!field_has_classes(f)) continue;
+            for (int l = 1; l <= BT_MAX_L; ++l) {
+                std::vector<std::vector<char>> seen(l + 1, std::vector<char>(2 * BT_KEY_SPAN + 1, 0));
+                for (unsigned s = 0; s < (1u << l); ++s)
+                    seen[__builtin_popcount(s)][suffix_key(f, s, l) + BT_KEY_SPAN] = 1;
+                for (int k = 0; k <= l; ++k) {
+                    int c = 0;
+                    for (char x : seen[k]) c += x;
+                    table[f][l][k] = c;
+                }
+            }
+        }
+    });
+    return table[field][L];
+}
+
+void fill_job_shape(bt_job &J, int N, int field, int mode, int prec) {
     J.N = N;
     J.L = exact_split_L(N);
     J.P = N - J.L;
@@ -230,6 +278,19 @@ void fill_job_shape(bt_job &J, int N, int field, int mode) {
     }
     for (int k = J.L + 1; k < BT_MAX_L + 2; ++k) J.goff[k] = off;
     J.suf_len = off;
+    J.cls = 0;
+    if (prec == BT_PREC_FP32_COMP && field_has_classes(field)) {
+        // class table: goff in class units, two float2 slots per class
+        const int *cnt = class_counts(field, J.L);
+        off = 0;
+        for (int k = 0; k <= J.L; ++k) {
+            J.goff[k] = off;
+            off += (cnt[k] + BT_CLS_UNROLL - 1) / BT_CLS_UNROLL * BT_CLS_UNROLL;
+        }
+        for (int k = J.L + 1; k < BT_MAX_L + 2; ++k) J.goff[k] = off;
+        J.suf_len = 2 * off;
+        J.cls = 1;
+    }
     if (field == BT_F_GEO) {
         int span = J.P * (J.P + 1) / 2 + J.L * J.P + 1;
         J.geo_imin = -span;
@@ -245,7 +306,7 @@ void fill_job_shape(bt_job &J, int N, int field, int mode) {
 // Plans the pass that starts at option i (used by the allocation-free entry
 // point, which keeps its job list on the stack): the same pairing and split
 // rules as plan_jobs. Sets *step to the number of options the pass covers.
-void plan_one_job(const bt_option *opts, int n, int i, bt_job *J, int *step) {
+void plan_one_job(const bt_option *opts, int n, int i, bt_job *J, int *step, int prec) {
     int field, mode;
     payoff_field(opts[i].payoff, &field, &mode);
     J->opt = i;
@@ -262,7 +323,7 @@ void plan_one_job(const bt_option *opts, int n, int i, bt_job *J, int *step) {
             *step = 2;
         }
     }
-    fill_job_shape(*J, opts[i].N, field, mode);
+    fill_job_shape(*J, opts[i].N, field, mode, prec);
 }
 
 struct bt_exact_plan {
@@ -331,7 +392,7 @@ bt_status plan_jobs(const bt_option *opts, int n, int prec, std::vector<bt_job> 
                 step = 2;
             }
         }
-        fill_job_shape(J, opts[i].N, field, mode);
+        fill_job_shape(J, opts[i].N, field, mode, prec);
         J.item_begin = items;
         J.item_offset = 0;
         J.part_off = items;

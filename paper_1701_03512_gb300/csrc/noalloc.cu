@@ -54,7 +54,7 @@ extern "C" bt_status bt_price_exact_noalloc(const bt_option *opts, int32_t n, bt
         bt_job &J = jobs[nj];
         memset(&J, 0, sizeof(J));
         int step = 1;
-        plan_one_job(opts, n, i, &J, &step);
+        plan_one_job(opts, n, i, &J, &step, prec);
         J.item_begin = items;
         J.item_offset = 0;
         J.part_off = items;

@@ -250,7 +250,7 @@ extern "C" bt_status bt_submit(bt_server *S, const bt_option *opt, uint64_t *tic
     request r;
     memset(&r.job, 0, sizeof(r.job));
     int step = 1;
-    plan_one_job(opt, 1, 0, &r.job, &step);
+    plan_one_job(opt, 1, 0, &r.job, &step, S_PREC(S));
     size_t a, b, c, d, e;
     r.mem_bytes = request_bytes(r.job, S_PREC(S), &a, &b, &c, &d, &e);
     if (r.mem_bytes > S->pool_bytes)
