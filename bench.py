@@ -461,7 +461,9 @@ def main():
         mc = mc_bench(bt, W, ctx, sms, fmax)
     if world == 1 and not args.no_serving:
         loads = [float(x) for x in args.serving_loads.split(",") if x]
-        serving = serving_bench(bt, W, ctx, args.serving_requests, loads)
+        sctx = bt.Context(local_rank, device_budget_bytes=12 << 30)   # 8 GiB server pool + plain scratch
+        serving = serving_bench(bt, W, sctx, args.serving_requests, loads)
+        sctx.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
