@@ -7,9 +7,12 @@
 //  - keeps up to n_streams path-sum launches in flight, each over work items
 //    drawn from every admitted request (smallest remaining work first), so
 //    requests that arrive while others run are admitted and share the GPU;
-//  - when all items of a request are done, sums its partials in a fixed
-//    order (the same reduction as bt_price_exact, so a result does not depend
-//    on the mix it ran in), copies the result back and frees its memory.
+//  - enqueues the fixed-order reduction of a request's partials (the same
+//    reduction as bt_price_exact, so a result does not depend on the mix it
+//    ran in) and the copy of its result to the host on the stream of the
+//    launch that holds its last items, after that stream has waited for the
+//    other launches holding its items; one event per launch then completes
+//    the request, and its memory and slot are freed.
 // Every wait in the server is bounded (BT_ETIMEOUT).
 #include <cuda_runtime.h>
 
@@ -83,6 +86,7 @@ struct request {
     int slot = -1;
     size_t mem_off = 0, mem_bytes = 0;
     int64_t next_item = 0, done_items = 0;
+    uint32_t inflight = 0;  // launch slots whose launch in flight holds items of this request
     req_state state = RQ_PENDING;
     bt_result result;
     bt_status status = BT_OK;
@@ -97,6 +101,9 @@ struct launch_slot {
     bt_job *d_jobs = nullptr;
     unsigned long long *d_counter = nullptr;
     std::vector<std::pair<uint64_t, int64_t>> parts;  // (ticket, items in this launch)
+    bt_job *h_fin_jobs = nullptr, *d_fin_jobs = nullptr;  // reductions enqueued after the launch
+    bt_result *h_out = nullptr, *d_out = nullptr;
+    std::vector<uint64_t> fin;                         // requests completed by this launch
 };
 
 }  // namespace
@@ -110,14 +117,10 @@ struct bt_server {
     bt_option *d_opts = nullptr;   // slot-indexed
     bt_jparams *d_prm = nullptr;   // slot-indexed
     std::vector<int> free_slots;
-    cudaStream_t setup_stream = nullptr, fin_stream = nullptr;
-    cudaEvent_t setup_done = nullptr, fin_done = nullptr;
+    cudaStream_t setup_stream = nullptr;
+    cudaEvent_t setup_done = nullptr;
     bt_job *h_setup_jobs = nullptr, *d_setup_jobs = nullptr;
     bt_option *h_setup_opts = nullptr;
-    bt_job *h_fin_jobs = nullptr, *d_fin_jobs = nullptr;
-    bt_result *h_fin_out = nullptr, *d_fin_out = nullptr;
-    std::vector<uint64_t> fin_tickets;
-    bool fin_busy = false;
     std::vector<launch_slot> slots;
     int grid = 0;
 
@@ -172,9 +175,8 @@ extern "C" bt_status bt_server_start(bt_ctx *ctx, const bt_server_cfg *cfg_in, b
     cudaSetDevice(ctx->device);
     const int A = cfg.max_active;
     // fixed device arrays (slots) followed by the pool for tables and partials
-    S->fixed_bytes = up256(sizeof(bt_option) * A) + up256(sizeof(bt_jparams) * A) +
-                     up256(sizeof(bt_job) * A) * 2 + up256(sizeof(bt_result) * A) +
-                     (size_t)cfg.n_streams * (up256(sizeof(bt_job) * A) + 256);
+    S->fixed_bytes = up256(sizeof(bt_option) * A) + up256(sizeof(bt_jparams) * A) + up256(sizeof(bt_job) * A) +
+                     (size_t)cfg.n_streams * (2 * up256(sizeof(bt_job) * A) + up256(sizeof(bt_result) * A) + 256);
     if (S->fixed_bytes >= cfg.device_budget_bytes) {
         delete S;
         return bt_fail(BT_EBUDGET, "bt_server_start: budget below the fixed arrays");
@@ -190,27 +192,25 @@ extern "C" bt_status bt_server_start(bt_ctx *ctx, const bt_server_cfg *cfg_in, b
     S->d_opts = (bt_option *)p; p += up256(sizeof(bt_option) * A);
     S->d_prm = (bt_jparams *)p; p += up256(sizeof(bt_jparams) * A);
     S->d_setup_jobs = (bt_job *)p; p += up256(sizeof(bt_job) * A);
-    S->d_fin_jobs = (bt_job *)p; p += up256(sizeof(bt_job) * A);
-    S->d_fin_out = (bt_result *)p; p += up256(sizeof(bt_result) * A);
     S->slots.resize(cfg.n_streams);
     cudaError_t e = cudaSuccess;
     for (auto &L : S->slots) {
         L.d_jobs = (bt_job *)p; p += up256(sizeof(bt_job) * A);
+        L.d_fin_jobs = (bt_job *)p; p += up256(sizeof(bt_job) * A);
+        L.d_out = (bt_result *)p; p += up256(sizeof(bt_result) * A);
         L.d_counter = (unsigned long long *)p; p += 256;
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost((void **)&L.h_jobs, sizeof(bt_job) * A);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&L.h_fin_jobs, sizeof(bt_job) * A);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&L.h_out, sizeof(bt_result) * A);
     }
     S->pool = p;
     S->palloc.init(S->pool_bytes & ~(size_t)255);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->setup_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->fin_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->setup_done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->fin_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_setup_jobs, sizeof(bt_job) * A);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_setup_opts, sizeof(bt_option) * A);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_fin_jobs, sizeof(bt_job) * A);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_fin_out, sizeof(bt_result) * A);
     if (e == cudaSuccess) e = cudaEventRecord(S->setup_done, S->setup_stream);
     if (e != cudaSuccess) {
         bt_status r = bt_cuda_fail(e, "bt_server_start");
@@ -358,21 +358,16 @@ extern "C" bt_status bt_server_stop(bt_server *S) {
         if (L.stream) cudaStreamDestroy(L.stream);
         if (L.done) cudaEventDestroy(L.done);
         if (L.h_jobs) cudaFreeHost(L.h_jobs);
+        if (L.h_fin_jobs) cudaFreeHost(L.h_fin_jobs);
+        if (L.h_out) cudaFreeHost(L.h_out);
     }
     if (S->setup_stream) {
         cudaStreamSynchronize(S->setup_stream);
         cudaStreamDestroy(S->setup_stream);
     }
-    if (S->fin_stream) {
-        cudaStreamSynchronize(S->fin_stream);
-        cudaStreamDestroy(S->fin_stream);
-    }
     if (S->setup_done) cudaEventDestroy(S->setup_done);
-    if (S->fin_done) cudaEventDestroy(S->fin_done);
     if (S->h_setup_jobs) cudaFreeHost(S->h_setup_jobs);
     if (S->h_setup_opts) cudaFreeHost(S->h_setup_opts);
-    if (S->h_fin_jobs) cudaFreeHost(S->h_fin_jobs);
-    if (S->h_fin_out) cudaFreeHost(S->h_fin_out);
     if (S->d_opts) ctx_free(S->ctx, S->d_opts, S->cfg.device_budget_bytes);
     delete S;
     return BT_OK;
@@ -402,7 +397,9 @@ static void admit(bt_server *S) {
         }
     }
     if (admitted.empty()) return;
-    // tables of the new requests on the set-up stream
+    // the pinned staging of the previous admission must have been copied
+    cudaError_t e = cudaEventSynchronize(S->setup_done);
+    // tables of the new requests on the set-up stream; launches wait on its event
     int max_len = 0;
     for (size_t i = 0; i < admitted.size(); ++i) {
         request &r = *rq[i];
@@ -430,7 +427,6 @@ static void admit(bt_server *S) {
     const int na = (int)admitted.size();
     cudaStream_t st = S->setup_stream;
     // options go to their slots; params are written to the slots by k_params (prm_off = slot)
-    cudaError_t e = cudaSuccess;
     for (int i = 0; i < na && e == cudaSuccess; ++i)
         e = cudaMemcpyAsync(S->d_opts + S->h_setup_jobs[i].opt, &S->h_setup_opts[i], sizeof(bt_option),
                             cudaMemcpyHostToDevice, st);
@@ -441,8 +437,6 @@ static void admit(bt_server *S) {
         le = bt_launch_tables(S->d_setup_jobs, S->d_prm, na, max_len, S_PREC(S), (float2 *)S->pool,
                               (double *)S->pool, (bt_pentry *)S->pool, (bt_pentry *)S->pool, (bt_pow *)S->pool, st);
     if (!le) le = (int)cudaEventRecord(S->setup_done, st);
-    // the pinned staging is reused next admission: wait for the copies
-    if (!le) le = (int)cudaStreamSynchronize(st);
     std::lock_guard<std::mutex> lock(S->mu);
     if (le) {
         server_fail(S, BT_ECUDA, cudaGetErrorString((cudaError_t)le));
@@ -452,9 +446,13 @@ static void admit(bt_server *S) {
     S->peak_active = std::max(S->peak_active, (int32_t)S->active.size());
 }
 
-// Build and launch one path-sum launch over items of the active requests.
-static bool launch_work(bt_server *S, launch_slot &L) {
+// Build and launch one path-sum launch over items of the active requests;
+// requests whose last items are in it get their reduction and result copy
+// enqueued behind it on the same stream.
+static bool launch_work(bt_server *S, launch_slot &L, int li) {
     std::vector<std::pair<request *, int64_t>> pick;
+    std::vector<request *> fin;
+    uint32_t wait_mask = 0;
     {
         std::lock_guard<std::mutex> lock(S->mu);
         std::vector<request *> cand;
@@ -475,9 +473,18 @@ static bool launch_work(bt_server *S, launch_slot &L) {
             pick.push_back({r, take});
             budget -= take;
         }
+        for (auto &pr : pick) {
+            request *r = pr.first;
+            if (r->next_item + pr.second == r->job.n_items) {
+                fin.push_back(r);
+                wait_mask |= r->inflight;  // other launches that hold its earlier items
+            }
+            r->inflight |= 1u << li;
+        }
     }
     int64_t cursor = 0;
     L.parts.clear();
+    L.fin.clear();
     for (size_t i = 0; i < pick.size(); ++i) {
         request *r = pick[i].first;
         bt_job J = r->job;
@@ -487,13 +494,22 @@ static bool launch_work(bt_server *S, launch_slot &L) {
         cursor += pick[i].second;
         L.parts.push_back({r->ticket, pick[i].second});
     }
+    for (size_t k = 0; k < fin.size(); ++k) {
+        bt_job J = fin[k]->job;
+        J.out_call = J.out_call >= 0 ? (int)k : -1;
+        J.out_put = J.out_put >= 0 ? (int)k : -1;
+        L.h_fin_jobs[k] = J;
+        L.fin.push_back(fin[k]->ticket);
+    }
     {
         std::lock_guard<std::mutex> lock(S->mu);
         for (auto &pr : pick) pr.first->next_item += pr.second;
     }
-    const int nj = (int)pick.size();
+    const int nj = (int)pick.size(), nf = (int)fin.size();
     cudaError_t e = cudaStreamWaitEvent(L.stream, S->setup_done, 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_jobs, L.h_jobs, sizeof(bt_job) * nj, cudaMemcpyHostToDevice, L.stream);
+    if (e == cudaSuccess && nf)
+        e = cudaMemcpyAsync(L.d_fin_jobs, L.h_fin_jobs, sizeof(bt_job) * nf, cudaMemcpyHostToDevice, L.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(L.d_counter, 0, sizeof(unsigned long long), L.stream);
     int le = (int)e;
     if (!le) {
@@ -515,6 +531,16 @@ static bool launch_work(bt_server *S, launch_slot &L) {
         a.counter = L.d_counter;
         le = bt_launch_exact(&a, S_PREC(S), S->grid, L.stream);
     }
+    if (!le && nf) {
+        // the other launches holding items of these requests are in flight on
+        // their own streams; their events were recorded when they launched
+        for (int o = 0; o < (int)S->slots.size() && !le; ++o)
+            if (o != li && (wait_mask >> o & 1u)) le = (int)cudaStreamWaitEvent(L.stream, S->slots[o].done, 0);
+        if (!le)
+            le = bt_launch_finalize(L.d_fin_jobs, S->d_prm, nf, (const double2 *)S->pool, 0, 1, S_PREC(S), L.d_out,
+                                    L.stream);
+        if (!le) le = (int)cudaMemcpyAsync(L.h_out, L.d_out, sizeof(bt_result) * nf, cudaMemcpyDeviceToHost, L.stream);
+    }
     if (!le) le = (int)cudaEventRecord(L.done, L.stream);
     std::lock_guard<std::mutex> lock(S->mu);
     if (le) {
@@ -526,95 +552,47 @@ static bool launch_work(bt_server *S, launch_slot &L) {
     return true;
 }
 
-// Completed launches: count items; requests with every item done go to finalize.
+// Completed launches: count items, complete the requests they finalised.
 static bool reap_work(bt_server *S) {
     bool any = false;
-    for (auto &L : S->slots) {
+    for (int li = 0; li < (int)S->slots.size(); ++li) {
+        launch_slot &L = S->slots[li];
         if (!L.busy) continue;
         cudaError_t q = cudaEventQuery(L.done);
         if (q == cudaErrorNotReady) continue;
         std::lock_guard<std::mutex> lock(S->mu);
+        L.busy = false;
         if (q != cudaSuccess) {
             server_fail(S, BT_ECUDA, cudaGetErrorString(q));
-            L.busy = false;
             continue;
         }
         for (auto &pt : L.parts) {
-            request &r = S->reqs[pt.first];
-            r.done_items += pt.second;
             S->items_done += pt.second;
+            // a request finalised on another stream may be collected already
+            auto it = S->reqs.find(pt.first);
+            if (it == S->reqs.end()) continue;
+            it->second.done_items += pt.second;
+            it->second.inflight &= ~(1u << li);
         }
-        L.busy = false;
+        const auto now = clk::now();
+        for (size_t k = 0; k < L.fin.size(); ++k) {
+            request &r = S->reqs[L.fin[k]];
+            r.result = L.h_out[k];
+            r.state = RQ_DONE;
+            r.t_done = now;
+            S->palloc.release(r.mem_off, r.mem_bytes);
+            S->free_slots.push_back(r.slot);
+            S->lat_ms.push_back(ms_between(r.t_arrive, now));
+            S->done_log.push_back({r.ticket, now});
+            S->completed++;
+            S->paths_done += (double)r.result.paths;
+            S->t_last = now;
+            S->active.erase(std::find(S->active.begin(), S->active.end(), r.ticket));
+        }
+        if (!L.fin.empty()) S->cv_done.notify_all();
         any = true;
     }
     return any;
-}
-
-static void start_finalize(bt_server *S) {
-    if (S->fin_busy) return;
-    S->fin_tickets.clear();
-    {
-        std::lock_guard<std::mutex> lock(S->mu);
-        for (uint64_t t : S->active) {
-            request &r = S->reqs[t];
-            if (r.state == RQ_ACTIVE && r.done_items == r.job.n_items) {
-                bt_job J = r.job;
-                const int k = (int)S->fin_tickets.size();
-                J.out_call = J.out_call >= 0 ? k : -1;
-                J.out_put = J.out_put >= 0 ? k : -1;
-                S->h_fin_jobs[k] = J;
-                S->fin_tickets.push_back(t);
-                r.state = RQ_FINALIZING;
-            }
-        }
-    }
-    const int n = (int)S->fin_tickets.size();
-    if (!n) return;
-    cudaStream_t st = S->fin_stream;
-    // the partials were written on the compute streams, whose completion the
-    // scheduler has already observed
-    cudaError_t e = cudaMemcpyAsync(S->d_fin_jobs, S->h_fin_jobs, sizeof(bt_job) * n, cudaMemcpyHostToDevice, st);
-    int le = (int)e;
-    if (!le)
-        le = bt_launch_finalize(S->d_fin_jobs, S->d_prm, n, (const double2 *)S->pool, 0, 1, S_PREC(S), S->d_fin_out,
-                                st);
-    if (!le) le = (int)cudaMemcpyAsync(S->h_fin_out, S->d_fin_out, sizeof(bt_result) * n, cudaMemcpyDeviceToHost, st);
-    if (!le) le = (int)cudaEventRecord(S->fin_done, st);
-    if (le) {
-        std::lock_guard<std::mutex> lock(S->mu);
-        server_fail(S, BT_ECUDA, cudaGetErrorString((cudaError_t)le));
-        return;
-    }
-    S->fin_busy = true;
-}
-
-static bool reap_finalize(bt_server *S) {
-    if (!S->fin_busy) return false;
-    cudaError_t q = cudaEventQuery(S->fin_done);
-    if (q == cudaErrorNotReady) return false;
-    std::lock_guard<std::mutex> lock(S->mu);
-    S->fin_busy = false;
-    if (q != cudaSuccess) {
-        server_fail(S, BT_ECUDA, cudaGetErrorString(q));
-        return false;
-    }
-    const auto now = clk::now();
-    for (size_t k = 0; k < S->fin_tickets.size(); ++k) {
-        request &r = S->reqs[S->fin_tickets[k]];
-        r.result = S->h_fin_out[k];
-        r.state = RQ_DONE;
-        r.t_done = now;
-        S->palloc.release(r.mem_off, r.mem_bytes);
-        S->free_slots.push_back(r.slot);
-        S->lat_ms.push_back(ms_between(r.t_arrive, now));
-        S->done_log.push_back({r.ticket, now});
-        S->completed++;
-        S->paths_done += (double)r.result.paths;
-        S->t_last = now;
-        S->active.erase(std::find(S->active.begin(), S->active.end(), r.ticket));
-    }
-    S->cv_done.notify_all();
-    return true;
 }
 
 static void server_loop(bt_server *S) {
@@ -643,18 +621,20 @@ static void server_loop(bt_server *S) {
         }
         const auto t0 = clk::now();
         bool progress = reap_work(S);
-        progress |= reap_finalize(S);
         admit(S);
-        for (auto &L : S->slots)
-            if (!L.busy && launch_work(S, L)) progress = true;
-        start_finalize(S);
-        bool busy = S->fin_busy;
+        for (int li = 0; li < (int)S->slots.size(); ++li)
+            if (!S->slots[li].busy && launch_work(S, S->slots[li], li)) progress = true;
+        bool busy = false;
         for (auto &L : S->slots) busy |= L.busy;
         if (busy) {
             std::lock_guard<std::mutex> lock(S->mu);
             S->busy_s += std::chrono::duration<double>(clk::now() - t0).count();
         }
-        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        // poll the launch events while work is in flight; otherwise back off
+        if (!progress) {
+            if (busy) std::this_thread::yield();
+            else std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
     }
 }
 
