@@ -218,6 +218,20 @@ bt_status bt_price_mc(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t str
 bt_status bt_price_mc_ex(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t strata_bits,
                          int64_t samples_per_stratum, uint64_t seed, int32_t kind, bt_result *out,
                          double *strata_stats, void *stream);
+/* One shard of the Partitioned estimator for splitting strata across GPUs
+ * or processes (the strata of Section 4 are the rank blocks of Section 3):
+ * this call covers strata m = shard + j * n_shards only (1 <= n_shards <=
+ * 2^strata_bits, 0 <= shard < n_shards), with the same Philox streams as the
+ * unsharded call, so the shards' strata are exactly its strata. out[i].value
+ * and out[i].stderr_mc^2 are this shard's terms of eq. mc12 and of its
+ * variance: over all shards, value sums to the unsharded value and
+ * stderr_mc^2 to its square (up to FP64 rounding). var_plain = 0 (it needs
+ * every stratum's mean); paths = samples drawn by this shard. strata_stats
+ * (optional) receives (mean, unbiased variance, P(D_m)) for this shard's
+ * strata in ascending m, options concatenated. */
+bt_status bt_price_mc_shard(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t strata_bits,
+                            int64_t samples_per_stratum, uint64_t seed, int32_t shard, int32_t n_shards,
+                            bt_result *out, double *strata_stats, void *stream);
 /* The device Philox-4x32-10 used above, evaluated for n counters and keys
  * (host arrays ctr[n][4], key[n][2], out[n][4]); for verification. */
 bt_status bt_philox4x32_10(bt_ctx *ctx, const uint32_t *ctr, const uint32_t *key, uint32_t *out, int32_t n);

@@ -112,6 +112,7 @@ def lib():
         _proto(L, "bt_price_exact_noalloc", [_vp, _i32, C.c_int, _vp, _vp])
         _proto(L, "bt_price_mc", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _vp, _vp])
         _proto(L, "bt_price_mc_ex", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _i32, _vp, _vp, _vp])
+        _proto(L, "bt_price_mc_shard", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _i32, _i32, _vp, _vp, _vp])
         _proto(L, "bt_philox4x32_10", [_vp, _vp, _vp, _vp, _i32])
         _proto(L, "bt_greeks_exact", [_vp, _vp, _i32, C.c_int, _vp, _vp, _vp])
         _proto(L, "bt_server_start", [_vp, C.POINTER(bt_server_cfg), C.POINTER(_vp)])
@@ -259,6 +260,19 @@ def bt_price_mc_ex(ctx, opts, strata_bits, samples_per_stratum, seed, kind=BT_MC
     strata = np.zeros((len(a), per, 3)) if with_strata else None
     _check(lib().bt_price_mc_ex(ctx, a.ctypes.data, len(a), strata_bits, samples_per_stratum, seed, kind,
                                 out.ctypes.data, strata.ctypes.data if with_strata else None, _stream(stream)))
+    return (out, strata) if with_strata else out
+
+
+def bt_price_mc_shard(ctx, opts, strata_bits, samples_per_stratum, seed, shard, n_shards, with_strata=False,
+                      stream=None):
+    """Strata m = shard + j * n_shards of the Partitioned estimator."""
+    a = options_array(opts)
+    out = np.zeros(len(a), dtype=RESULT_DTYPE)
+    per = ((1 << strata_bits) - shard + n_shards - 1) // n_shards
+    strata = np.zeros((len(a), per, 3)) if with_strata else None
+    _check(lib().bt_price_mc_shard(ctx, a.ctypes.data, len(a), strata_bits, samples_per_stratum, seed, shard,
+                                   n_shards, out.ctypes.data, strata.ctypes.data if with_strata else None,
+                                   _stream(stream)))
     return (out, strata) if with_strata else out
 
 

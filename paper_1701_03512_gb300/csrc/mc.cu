@@ -189,7 +189,7 @@ __device__ void mc_item(const bt_mc_args &a, const bt_mc_job &J, int64_t item_lo
                         float3 *red) {
     // item -> (stratum, first sample); shared mode has one "stratum" index 0
     const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
-    const int64_t m = item_local / chunks;
+    const int64_t m = J.shard + (item_local / chunks) * J.n_shards;  // global stratum index
     const int64_t i0 = (item_local % chunks) * BT_MC_ITEM;
     float n = 0.0f, mean = 0.0f, M2 = 0.0f;
     float tau = 0.0f, beta = 0.0f, C = 0.0f;
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_mc(bt_mc_args a) {
             }
         } else {
             const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
-            const int64_t m = item_local / chunks;
+            const int64_t m = J.shard + (item_local / chunks) * J.n_shards;
             if (s_job != cur_job || m != cur_stratum) {
                 __syncthreads();
                 if (threadIdx.x == 0) s_str[0] = stratum_state(J, (uint64_t)m);
@@ -322,7 +322,8 @@ __global__ void k_mc_strata(const bt_mc_job *jobs, int n_jobs, const double4 *it
         else hi = mid - 1;
     }
     const bt_mc_job &J = jobs[lo];
-    const int64_t m = g - J.strata_off;
+    const int64_t m = g - J.strata_off;                // stratum of this run
+    const int64_t mg = J.shard + m * J.n_shards;       // its global index
     const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
     double n = 0.0, mu = 0.0, Q = 0.0;
     for (int64_t c = lane; c < chunks; c += 32) {
@@ -335,7 +336,7 @@ __global__ void k_mc_strata(const bt_mc_job *jobs, int n_jobs, const double4 *it
         const double Qb = __shfl_down_sync(0xffffffffu, Q, o);
         chan64(n, mu, Q, nb, mb_, Qb);
     }
-    if (lane == 0) strata_nmq[g] = make_double4(n, mu, Q, J.shared ? 1.0 : stratum_state(J, (uint64_t)m).prob);
+    if (lane == 0) strata_nmq[g] = make_double4(n, mu, Q, J.shared ? 1.0 : stratum_state(J, (uint64_t)mg).prob);
 }
 
 // a8 (second half): across strata, eq. mc12 and Var = sum_m P(D_m)^2 s_m^2 / R_m
@@ -347,7 +348,7 @@ __global__ void k_mc_finalize(const bt_mc_job *jobs, int n_jobs, const double4 *
     if (j >= n_jobs) return;
     const bt_mc_job J = jobs[j];
     __shared__ double sh[3][BT_THREADS];
-    const int64_t M = J.shared ? 1 : (1ll << J.mb);
+    const int64_t M = J.M;
     double th = 0.0, thc = 0.0, var = 0.0, ew = 0.0;
     for (int64_t m = threadIdx.x; m < M; m += BT_THREADS) {
         const double4 s = strata_nmq[J.strata_off + m];
@@ -393,7 +394,8 @@ __global__ void k_mc_finalize(const bt_mc_job *jobs, int n_jobs, const double4 *
         bt_result r;
         r.value = J.disc * theta;
         r.stderr_mc = J.disc * sqrt(var_tot);
-        r.var_plain = J.shared ? 0.0 : ew_tot + sh[0][0];
+        // eq. mc14 needs the mean over all strata: only a run over all of them has it
+        r.var_plain = J.shared || J.n_shards > 1 ? 0.0 : ew_tot + sh[0][0];
         r.err_est = 0.0;
         r.paths = (int64_t)M * J.R;
         out[J.out] = r;

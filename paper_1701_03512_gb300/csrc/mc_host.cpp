@@ -33,9 +33,9 @@ static uint32_t bernoulli_threshold(double p) {
     return (uint32_t)x;
 }
 
-extern "C" bt_status bt_price_mc_ex(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t strata_bits,
-                                    int64_t samples_per_stratum, uint64_t seed, int32_t kind, bt_result *out,
-                                    double *strata_stats, void *stream) {
+static bt_status mc_run(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t strata_bits,
+                        int64_t samples_per_stratum, uint64_t seed, int32_t kind, int32_t shard, int32_t n_shards,
+                        bt_result *out, double *strata_stats, void *stream) {
     if (!ctx || !opts || !out || n < 1) return bt_fail(BT_EINVAL, "bt_price_mc: bad arguments");
     if (kind != BT_MC_PARTITIONED && kind != BT_MC_SHARED) return bt_fail(BT_EINVAL, "bt_price_mc: bad kind %d", kind);
     if (samples_per_stratum < 1 || samples_per_stratum > ((int64_t)1 << 32))
@@ -49,6 +49,8 @@ extern "C" bt_status bt_price_mc_ex(bt_ctx *ctx, const bt_option *opts, int32_t 
         if (strata_bits < 0 || strata_bits > opts[i].N || strata_bits > maxbits)
             return bt_fail(strata_bits > maxbits ? BT_EUNSUPPORTED : BT_EINVAL,
                            "option %d: strata_bits %d outside 0..min(N=%d, %d)", i, strata_bits, opts[i].N, maxbits);
+        if (n_shards > (1 << strata_bits))
+            return bt_fail(BT_EINVAL, "%d shards of %d strata", n_shards, 1 << strata_bits);
         bt_mc_job &J = jobs[i];
         memset(&J, 0, sizeof(J));
         host_tree(&opts[i], &J.u, &J.d, &J.p);
@@ -69,7 +71,10 @@ extern "C" bt_status bt_price_mc_ex(bt_ctx *ctx, const bt_option *opts, int32_t 
         J.df = (float)J.d;
         J.lnu_f = (float)std::log(J.u);
         const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
-        const int64_t M = J.shared ? 1 : ((int64_t)1 << J.mb);
+        J.shard = shard;
+        J.n_shards = n_shards;
+        const int64_t M = J.shared ? 1 : (((int64_t)1 << J.mb) - shard + n_shards - 1) / n_shards;
+        J.M = M;
         J.item_begin = items;
         J.n_items = M * chunks;
         J.strata_off = strata_total;
@@ -125,6 +130,21 @@ extern "C" bt_status bt_price_mc_ex(bt_ctx *ctx, const bt_option *opts, int32_t 
     cudaStreamSynchronize(st);
     ctx_free(ctx, arena, off);
     return rs;
+}
+
+extern "C" bt_status bt_price_mc_ex(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t strata_bits,
+                                    int64_t samples_per_stratum, uint64_t seed, int32_t kind, bt_result *out,
+                                    double *strata_stats, void *stream) {
+    return mc_run(ctx, opts, n, strata_bits, samples_per_stratum, seed, kind, 0, 1, out, strata_stats, stream);
+}
+
+extern "C" bt_status bt_price_mc_shard(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t strata_bits,
+                                       int64_t samples_per_stratum, uint64_t seed, int32_t shard, int32_t n_shards,
+                                       bt_result *out, double *strata_stats, void *stream) {
+    if (n_shards < 1 || shard < 0 || shard >= n_shards)
+        return bt_fail(BT_EINVAL, "bt_price_mc_shard: shard %d of %d", shard, n_shards);
+    return mc_run(ctx, opts, n, strata_bits, samples_per_stratum, seed, BT_MC_PARTITIONED, shard, n_shards, out,
+                  strata_stats, stream);
 }
 
 extern "C" bt_status bt_price_mc(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t strata_bits,

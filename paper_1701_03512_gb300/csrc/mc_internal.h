@@ -21,6 +21,8 @@ struct bt_mc_job {
     double u, d, p, S0, K, disc;
     float uf, df, lnu_f;
     int32_t pad;
+    int32_t shard, n_shards;       // this run covers strata m = shard + j * n_shards
+    int64_t M;                     // strata in this run (1 for Shared-Sample)
     int64_t item_begin, n_items, strata_off;
 };
 

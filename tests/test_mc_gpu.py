@@ -143,3 +143,22 @@ def test_mc_invalid(bt, ctx):
     assert e.value.status == bt.BT_EUNSUPPORTED
     with pytest.raises(bt.BtError):
         bt.bt_price_mc(ctx.h, [dict(o, N=5000)], 2, 10, 1)
+
+
+@pytest.mark.parametrize("n_shards", [1, 3, 16])
+def test_strata_shards_add_up(bt, ctx, n_shards):
+    """bt_price_mc_shard: the shards' strata are the unsharded call's strata
+    (bit for bit), their value terms sum to its value and their variance
+    terms to its squared standard error."""
+    o = W.opt(64, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
+    full, st_full = bt.bt_price_mc_ex(ctx.h, [o], 4, 2000, 11, with_strata=True)
+    v = se2 = paths = 0.0
+    for s in range(n_shards):
+        r, st = bt.bt_price_mc_shard(ctx.h, [o], 4, 2000, 11, s, n_shards, with_strata=True)
+        assert np.array_equal(st[0], st_full[0][s::n_shards])
+        v += r[0]["value"]
+        se2 += r[0]["stderr_mc"] ** 2
+        paths += r[0]["paths"]
+    assert abs(v - full[0]["value"]) <= 1e-13 * full[0]["value"]
+    assert abs(np.sqrt(se2) - full[0]["stderr_mc"]) <= 1e-12 * full[0]["stderr_mc"]
+    assert paths == full[0]["paths"]
