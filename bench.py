@@ -31,7 +31,9 @@ Two further measurements ride on the same line (rank 0, N=1 only):
             bit-identical values;
   mc      -- Partitioned Monte Carlo, arithmetic Asian call, N=252,
             2^16 strata x 2^14 Philox samples: samples/s and steps/s against
-            the integer/FP32 issue peak.
+            the integer/FP32 issue peak;
+  greeks  -- the derivative pass over 512 N=28 options (value and four
+            Greeks each), host arrays in and out.
 
 Multi-GPU (torchrun): every rank prices its own copy of the batch (weak
 scaling, independent problems, no collective on the data path); the value is
@@ -77,6 +79,7 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--serving-loads", default="0.5,0.8,0.95")
     ap.add_argument("--no-mc", action="store_true")
+    ap.add_argument("--no-greeks", action="store_true")
     return ap.parse_args()
 
 
@@ -312,6 +315,26 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3):
 
 
 # ---------------------------------------------------------------------------
+# Greeks: one derivative pass over the N=28 Greeks workload
+# ---------------------------------------------------------------------------
+def greeks_bench(bt, W, ctx, reps=3):
+    import numpy as np
+    opts = W.greeks_workload(28, 1, 256)
+    bt.bt_greeks_exact(ctx.h, opts)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        val, grad = bt.bt_greeks_exact(ctx.h, opts)
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    paths = float(len(opts)) * 2.0 ** 28
+    return {"workload": "value and dV/d(S0, sigma, rate, K), 256 sets (seed 1) x {arithmetic Asian call, "
+                        "fixed-strike lookback call}, N=28, FP32_COMP, host arrays in and out",
+            "ms": 1e3 * t, "options_per_s": len(opts) / t, "payoff_paths_per_s": paths / t,
+            "finite": bool(np.all(np.isfinite(grad)))}
+
+
+# ---------------------------------------------------------------------------
 # Reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
 def run_reference(args, rank):
@@ -456,9 +479,11 @@ def main():
         v, sample = cpu_oracle_sample(opts, args.cpu_seconds, threads)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
 
-    serving = mc = None
+    serving = mc = greeks = None
     if world == 1 and not args.no_mc:
         mc = mc_bench(bt, W, ctx, sms, fmax)
+    if world == 1 and not args.no_greeks:
+        greeks = greeks_bench(bt, W, ctx)
     if world == 1 and not args.no_serving:
         loads = [float(x) for x in args.serving_loads.split(",") if x]
         sctx = bt.Context(local_rank, device_budget_bytes=12 << 30)   # 8 GiB server pool + plain scratch
@@ -472,7 +497,7 @@ def main():
                                              "wall_s_timed": t_wall}),
             "fp32_peak_frac": roof["frac"], "clocks": clocks, "e2e": e2e,
             "gpu_launches": 4 * args.steps, "roofline": roof, "cpu_baseline": cpu,
-            "serving": serving, "mc": mc}
+            "serving": serving, "mc": mc, "greeks": greeks}
     print(json.dumps(line), flush=True)
     bt.bt_exact_plan_destroy(plan)
     ctx.close()
