@@ -284,8 +284,8 @@ def serving_bench(bt, W, ctx, n_req, loads):
 # ---------------------------------------------------------------------------
 # Monte Carlo: Partitioned estimator throughput
 # ---------------------------------------------------------------------------
-MC_OPS_PER_STEP = 19   # Philox-4x32-10 per 4 steps: 10 x (2 wide mul + 2 xor + 2 key adds) = 60; + compare,
-                       # select, multiply, add per step
+MC_OPS_PER_STEP = 14   # Philox-4x32-10 per 4 steps: 10 rounds x (2 wide multiplies + 2 three-input xors) = 40
+                       # (the key schedule is the same for every thread); + compare, select, multiply, add
 
 
 def mc_bench(bt, W, ctx, sms, fmax, reps=3):

@@ -308,6 +308,95 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_mc(bt_mc_args a) {
     }
 }
 
+// The Partitioned estimator, one work item per warp: a warp takes items from
+// the shared counter and runs them to the end on its own -- 32 lanes x 32
+// samples of one stratum, a shuffle-tree Welford combination, one FP64
+// record per item -- so no block-wide barrier ever holds the other warps.
+// Same draws, same item records and the same per-stratum combination
+// (k_mc_strata) as the block kernel.
+template <int FIELD>
+__device__ __forceinline__ void mc_warp_item(const bt_mc_args &a, const bt_mc_job &J, int64_t item_local,
+                                             float tau, float beta, float C, int64_t m) {
+    const int lane = threadIdx.x & 31;
+    const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
+    const int64_t i0 = (item_local % chunks) * BT_MC_ITEM;
+    float n = 0.0f, mean = 0.0f, M2 = 0.0f;
+#pragma unroll 1
+    for (int k = 0; k < BT_MC_ITEM / 32; k += 2) {
+        const int64_t ia = i0 + lane + (int64_t)k * 32;
+        const int64_t ib = ia + 32;
+        if (ia >= J.R) break;
+        float f2[2];
+        simulate_two<FIELD>(J, (unsigned)ia, (unsigned)ib, (unsigned)m, f2[0], f2[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && ib >= J.R) break;
+            const float v = payoff_of(J, tau, beta, C, f2[h]);
+            n += 1.0f;
+            const float delta = v - mean;
+            mean += delta / n;
+            M2 += delta * (v - mean);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float nb = __shfl_down_sync(0xffffffffu, n, o);
+        const float mb_ = __shfl_down_sync(0xffffffffu, mean, o);
+        const float M2b = __shfl_down_sync(0xffffffffu, M2, o);
+        chan(n, mean, M2, nb, mb_, M2b);
+    }
+    if (lane == 0) a.item_stats[J.item_begin + item_local] = make_double4(n, mean, M2, (double)m);
+}
+
+__global__ void __launch_bounds__(BT_THREADS, 2) k_mc_warp(bt_mc_args a) {
+    const int lane = threadIdx.x & 31;
+    int cur_job = -1;
+    int64_t cur_stratum = -1;
+    float tau = 0.0f, beta = 0.0f, C = 0.0f;
+    for (;;) {
+        unsigned long long i = 0;
+        int j = 0;
+        if (lane == 0) {
+            i = atomicAdd(a.counter, 1ull);
+            if (i < (unsigned long long)a.n_items) {
+                int lo = 0, hi = a.n_jobs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (a.jobs[mid].item_begin <= (int64_t)i) lo = mid;
+                    else hi = mid - 1;
+                }
+                j = lo;
+            }
+        }
+        i = __shfl_sync(0xffffffffu, i, 0);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (i >= (unsigned long long)a.n_items) break;
+        const bt_mc_job J = a.jobs[j];
+        const int64_t item_local = (int64_t)i - J.item_begin;
+        const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
+        const int64_t m = J.shard + (item_local / chunks) * J.n_shards;  // global stratum index
+        if (j != cur_job || m != cur_stratum) {
+            if (lane == 0) {
+                const mc_pref st = stratum_state(J, (uint64_t)m);
+                tau = (float)st.tau;
+                beta = (float)st.beta;
+                C = (float)st.C;
+            }
+            tau = __shfl_sync(0xffffffffu, tau, 0);
+            beta = __shfl_sync(0xffffffffu, beta, 0);
+            C = __shfl_sync(0xffffffffu, C, 0);
+            cur_job = j;
+            cur_stratum = m;
+        }
+        switch (J.field) {
+        case BT_F_ARITH: mc_warp_item<BT_F_ARITH>(a, J, item_local, tau, beta, C, m); break;
+        case BT_F_GEO: mc_warp_item<BT_F_GEO>(a, J, item_local, tau, beta, C, m); break;
+        case BT_F_EURO: mc_warp_item<BT_F_EURO>(a, J, item_local, tau, beta, C, m); break;
+        case BT_F_LOOKMAX: mc_warp_item<BT_F_LOOKMAX>(a, J, item_local, tau, beta, C, m); break;
+        default: mc_warp_item<BT_F_LOOKMIN>(a, J, item_local, tau, beta, C, m); break;
+        }
+    }
+}
+
 // a8 (first half): one warp per stratum combines the stratum's work items
 // (Chan et al.'s update, fixed lane order and a fixed shuffle tree).
 __global__ void k_mc_strata(const bt_mc_job *jobs, int n_jobs, const double4 *item_stats, int64_t n_strata,
@@ -402,10 +491,16 @@ __global__ void k_mc_finalize(const bt_mc_job *jobs, int n_jobs, const double4 *
     }
 }
 
-extern "C" int bt_launch_mc(const bt_mc_args *a, int grid, void *stream) {
+extern "C" int bt_launch_mc(const bt_mc_args *a, int shared, int grid, void *stream) {
     if (a->n_items <= 0) return 0;
-    if ((int64_t)grid > a->n_items) grid = (int)a->n_items;
-    k_mc<<<grid, BT_THREADS, 0, (cudaStream_t)stream>>>(*a);
+    if (shared) {
+        if ((int64_t)grid > a->n_items) grid = (int)a->n_items;
+        k_mc<<<grid, BT_THREADS, 0, (cudaStream_t)stream>>>(*a);
+    } else {
+        const int64_t warps = (int64_t)grid * (BT_THREADS / 32);
+        if (warps > a->n_items) grid = (int)((a->n_items + BT_THREADS / 32 - 1) / (BT_THREADS / 32));
+        k_mc_warp<<<grid, BT_THREADS, 0, (cudaStream_t)stream>>>(*a);
+    }
     return (int)cudaGetLastError();
 }
 
@@ -425,10 +520,11 @@ extern "C" int bt_launch_philox_selftest(const uint4 *ctr, const uint2 *key, uin
     return (int)cudaGetLastError();
 }
 
-extern "C" int bt_mc_grid_size(int device) {
+extern "C" int bt_mc_grid_size(int device, int shared) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc, BT_THREADS, 0);
+    if (shared) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc, BT_THREADS, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_warp, BT_THREADS, 0);
     if (per < 1) per = 1;
     return sms * per;
 }

@@ -113,7 +113,7 @@ static bt_status mc_run(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t s
         a.n_items = items;
         a.item_stats = d_stats;
         a.counter = d_cnt;
-        int le = bt_launch_mc(&a, bt_mc_grid_size(ctx->device), st);
+        int le = bt_launch_mc(&a, kind == BT_MC_SHARED, bt_mc_grid_size(ctx->device, kind == BT_MC_SHARED), st);
         if (le) rs = bt_cuda_fail(le, "MC kernel");
     }
     if (rs == BT_OK) {

@@ -38,11 +38,11 @@ struct bt_mc_args {
 #ifdef __cplusplus
 extern "C" {
 #endif
-int bt_launch_mc(const bt_mc_args *a, int grid, void *stream);
+int bt_launch_mc(const bt_mc_args *a, int shared, int grid, void *stream);
 int bt_launch_mc_finalize(const bt_mc_job *jobs, int n_jobs, const double4 *item_stats, int64_t n_strata,
                           double4 *strata_nmq, bt_result *out, double *strata, void *stream);
 int bt_launch_philox_selftest(const uint4 *ctr, const uint2 *key, uint4 *out, int n, void *stream);
-int bt_mc_grid_size(int device);
+int bt_mc_grid_size(int device, int shared);
 #ifdef __cplusplus
 }
 #endif
