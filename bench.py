@@ -496,7 +496,8 @@ def main():
             "config": workload_config(args, {"parallelism": "replicas" if world > 1 else "single GPU",
                                              "wall_s_timed": t_wall}),
             "fp32_peak_frac": roof["frac"], "clocks": clocks, "e2e": e2e,
-            "gpu_launches": 4 * args.steps, "roofline": roof, "cpu_baseline": cpu,
+            # per step: k_params, k_tables, k_class_tables, k_exact32, k_finalize
+            "gpu_launches": 5 * args.steps, "roofline": roof, "cpu_baseline": cpu,
             "serving": serving, "mc": mc, "greeks": greeks}
     print(json.dumps(line), flush=True)
     bt.bt_exact_plan_destroy(plan)
