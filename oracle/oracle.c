@@ -670,3 +670,87 @@ double orc_greeks_crr(int N, int payoff, double S0, double K, double rate, doubl
     grid_free(&g);
     return v;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Time-varying trees: eq. f13 with per-step u_t, d_t, p_t                   */
+/* ------------------------------------------------------------------------ */
+/* The payoff's quantity along path b: S_t = S_{t-1} * (x_t ? u_t : d_t). */
+static double steps_quantity(const orc_steps_model *m, uint64_t b) {
+    int N = m->N;
+    double sum = 0.0, lsum = 0.0, mx = -INFINITY, mn = INFINITY, St = m->S0;
+    for (int t = 1; t <= N; ++t) {
+        int x = (int)((b >> (N - t)) & 1u);
+        St = St * (x ? m->u[t - 1] : m->d[t - 1]);
+        sum += St;
+        lsum += log(St);
+        if (St > mx) mx = St;
+        if (St < mn) mn = St;
+    }
+    switch (m->payoff) {
+    case ORC_EURO_CALL: case ORC_EURO_PUT: return St;
+    case ORC_ARITH_CALL: case ORC_ARITH_PUT: return sum / (double)N;
+    case ORC_GEO_CALL: case ORC_GEO_PUT: return exp(lsum / (double)N);
+    case ORC_LOOK_CALL: return mx;
+    default: return mn;
+    }
+}
+
+double orc_steps_path_payoff(const orc_steps_model *m, uint64_t b) {
+    return payoff_of(m->payoff, m->K, steps_quantity(m, b));
+}
+
+double orc_steps_path_prob(const orc_steps_model *m, uint64_t b) {
+    int N = m->N;
+    double w = 1.0;
+    for (int t = 1; t <= N; ++t) {
+        int x = (int)((b >> (N - t)) & 1u);
+        w *= x ? m->p[t - 1] : 1.0 - m->p[t - 1];
+    }
+    return w;
+}
+
+static void steps_sum(const orc_steps_model *m, uint64_t lo, uint64_t hi, nsum *acc) {
+    for (uint64_t b = lo; b < hi; ++b)
+        nsum_add(acc, orc_steps_path_prob(m, b) * orc_steps_path_payoff(m, b));
+}
+
+void orc_steps_sum_range(const orc_steps_model *m, uint64_t lo, uint64_t hi, double *sum, double *comp) {
+    nsum acc = {0.0, 0.0};
+    if (m->N > 62) { *sum = NAN; *comp = 0.0; return; }
+    steps_sum(m, lo, hi, &acc);
+    *sum = acc.s; *comp = acc.c;
+}
+
+typedef struct { const orc_steps_model *m; uint64_t lo, hi; nsum acc; } steps_worker_t;
+
+static void *steps_worker_run(void *arg) {
+    steps_worker_t *w = (steps_worker_t *)arg;
+    w->acc.s = 0.0; w->acc.c = 0.0;
+    steps_sum(w->m, w->lo, w->hi, &w->acc);
+    return NULL;
+}
+
+double orc_steps_price(const orc_steps_model *m, int nthreads) {
+    if (m->N < 1 || m->N > 62) return NAN;
+    int r = 0;
+    while ((2 << r) <= nthreads && r + 1 <= m->N) ++r;
+    if (nthreads < 2) r = 0;
+    const int M = 1 << r;
+    const uint64_t per = ((uint64_t)1 << m->N) >> r;   /* process m owns B_m^N (Section 3) */
+    steps_worker_t *ws = (steps_worker_t *)calloc((size_t)M, sizeof(steps_worker_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)M, sizeof(pthread_t));
+    int *started = (int *)calloc((size_t)M, sizeof(int));
+    for (int k = 0; k < M; ++k) {
+        ws[k].m = m; ws[k].lo = (uint64_t)k * per; ws[k].hi = (uint64_t)(k + 1) * per;
+        started[k] = (M > 1) && pthread_create(&th[k], NULL, steps_worker_run, &ws[k]) == 0;
+        if (!started[k]) steps_worker_run(&ws[k]);
+    }
+    nsum tot = {0.0, 0.0};
+    for (int k = 0; k < M; ++k) {          /* eq. f15 in rank order */
+        if (started[k]) pthread_join(th[k], NULL);
+        nsum_add(&tot, ws[k].acc.s);
+        nsum_add(&tot, ws[k].acc.c);
+    }
+    free(ws); free(th); free(started);
+    return m->disc * nsum_get(&tot);
+}

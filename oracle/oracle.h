@@ -115,6 +115,27 @@ void orc_mc(const orc_model *m, int mb, int64_t Rm, uint64_t seed, uint32_t stre
  * mean_m = E[V | D_m], var_m = Var[V | D_m], prob_m = P(D_m). */
 void orc_stratum_moments(const orc_model *m, int mb, double *mean, double *var, double *prob);
 
+/* Time-varying trees (eq. f13 with per-step moves and probabilities; the
+ * case Section 2 names where eq. f8 no longer applies): step t multiplies the
+ * price by u[t-1] (up, probability p[t-1]) or by d[t-1]; the tree need not
+ * recombine. p(x) = prod_t p_t^{x_t} (1-p_t)^{1-x_t}. Payoffs as above. */
+typedef struct {
+    int32_t N;
+    int32_t payoff;
+    double S0, K;
+    double disc;                 /* e^{-qT} */
+    const double *u, *d, *p;     /* N entries each, step 1 first */
+} orc_steps_model;
+
+/* Path walk in the shape of Listing 1: rebuild path b step by step. */
+double orc_steps_path_payoff(const orc_steps_model *m, uint64_t b);
+double orc_steps_path_prob(const orc_steps_model *m, uint64_t b);
+/* Undiscounted Neumaier sum of p(x) V_N(x) over path indices [lo, hi). */
+void orc_steps_sum_range(const orc_steps_model *m, uint64_t lo, uint64_t hi, double *sum, double *comp);
+/* Discounted value by the Section 3 partition over nthreads workers (rounded
+ * down to a power of two), partials added in rank order (eq. f14, f15). */
+double orc_steps_price(const orc_steps_model *m, int nthreads);
+
 /* Pathwise Greeks by enumeration for CRR trees: grad = dV/d(S0, sigma, rate, K).
  * Returns the value. */
 double orc_greeks_crr(int N, int payoff, double S0, double K, double rate, double sigma,

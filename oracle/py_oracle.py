@@ -7,6 +7,7 @@ baseline use this module. It compiles ``oracle.c`` with gcc on first use
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -37,6 +38,12 @@ class Model(C.Structure):
                 ("u", C.c_double), ("d", C.c_double), ("p", C.c_double), ("disc", C.c_double)]
 
 
+class StepsModel(C.Structure):
+    _fields_ = [("N", C.c_int32), ("payoff", C.c_int32), ("S0", C.c_double), ("K", C.c_double),
+                ("disc", C.c_double), ("u", C.POINTER(C.c_double)), ("d", C.POINTER(C.c_double)),
+                ("p", C.POINTER(C.c_double))]
+
+
 def lib():
     global _lib
     with _lock:
@@ -65,6 +72,11 @@ def lib():
             L.orc_stratum_moments.argtypes = [pm, C.c_int, pd, pd, pd]
             L.orc_greeks_crr.argtypes = [C.c_int, C.c_int, d, d, d, d, d, pd]
             L.orc_greeks_crr.restype = d
+            ps = C.POINTER(StepsModel)
+            L.orc_steps_path_payoff.argtypes = [ps, u64]; L.orc_steps_path_payoff.restype = d
+            L.orc_steps_path_prob.argtypes = [ps, u64]; L.orc_steps_path_prob.restype = d
+            L.orc_steps_sum_range.argtypes = [ps, u64, u64, pd, pd]
+            L.orc_steps_price.argtypes = [ps, C.c_int]; L.orc_steps_price.restype = d
             _lib = L
     return _lib
 
@@ -199,3 +211,38 @@ def greeks_crr(o: dict):
 
 def discount(o: dict) -> float:
     return model(o).disc
+
+
+# ---------------------------------------------------------------------------
+# Time-varying trees (eq. f13 with per-step u_t, d_t, p_t)
+# ---------------------------------------------------------------------------
+def steps_model(o: dict, steps):
+    """(model, keep-alive arrays) for an option dict and steps[N][3] = (u_t, d_t, p_t)."""
+    st = np.ascontiguousarray(np.asarray(steps, dtype=np.float64).reshape(o["N"], 3))
+    u, d, p = (np.ascontiguousarray(st[:, k]) for k in range(3))
+    pd = C.POINTER(C.c_double)
+    m = StepsModel(o["N"], o["payoff"], o["S0"], o["K"], math.exp(-o["rate"] * o["T"]),
+                   u.ctypes.data_as(pd), d.ctypes.data_as(pd), p.ctypes.data_as(pd))
+    return m, (u, d, p)
+
+
+def steps_price(o: dict, steps, nthreads: int = 8) -> float:
+    m, keep = steps_model(o, steps)
+    return lib().orc_steps_price(C.byref(m), nthreads)
+
+
+def steps_sum_range(o: dict, steps, lo: int, hi: int) -> float:
+    m, keep = steps_model(o, steps)
+    s, c = C.c_double(), C.c_double()
+    lib().orc_steps_sum_range(C.byref(m), lo, hi, C.byref(s), C.byref(c))
+    return s.value + c.value
+
+
+def steps_path_payoff(o: dict, steps, b: int) -> float:
+    m, keep = steps_model(o, steps)
+    return lib().orc_steps_path_payoff(C.byref(m), b)
+
+
+def steps_path_prob(o: dict, steps, b: int) -> float:
+    m, keep = steps_model(o, steps)
+    return lib().orc_steps_path_prob(C.byref(m), b)

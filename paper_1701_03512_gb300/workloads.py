@@ -125,3 +125,14 @@ def serving_stream(seed: int = 2, n: int = 10000, rate_per_s: float = 1000.0, N_
     opts = [opt(Ns[i], sets["S0"][i], sets["K"][i], sets["rate"][i], sets["sigma"][i], sets["T"][i],
                 pays[i]) for i in range(n)]
     return arrivals, opts
+
+
+def step_factors(seed: int, N: int, lo: float = 0.02, hi: float = 0.15, p_lo: float = 0.3, p_hi: float = 0.7):
+    """Per-step moves and probabilities for a time-varying tree: steps[N][3] =
+    (u_t, d_t, p_t) with ln u_t ~ U[lo, hi], ln d_t ~ -U[lo, hi] (drawn
+    independently, so the tree does not recombine) and p_t ~ U[p_lo, p_hi]."""
+    rng = np.random.default_rng(seed)
+    lu = rng.uniform(lo, hi, N)
+    ld = rng.uniform(lo, hi, N)
+    p = rng.uniform(p_lo, p_hi, N)
+    return np.stack([np.exp(lu), np.exp(-ld), p], axis=1)

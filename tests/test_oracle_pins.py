@@ -357,3 +357,71 @@ def test_greeks_euler_identity(oracle):
         o = W.opt(12, 96.0, 104.0, 0.05, 0.3, 0.7, pay)
         v, g = oracle.greeks_crr(o)
         assert 96.0 * g[0] + 104.0 * g[3] == pytest.approx(v, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Time-varying trees (eq. f13 with per-step u_t, d_t, p_t)
+# ---------------------------------------------------------------------------
+def _numpy_steps(o, steps):
+    """Independent brute force: every path at once with numpy."""
+    N = o["N"]
+    b = np.arange(1 << N, dtype=np.int64)
+    x = ((b[:, None] >> (N - 1 - np.arange(N))[None, :]) & 1).astype(bool)
+    u, d, p = steps[:, 0], steps[:, 1], steps[:, 2]
+    S = o["S0"] * np.cumprod(np.where(x, u, d), axis=1)
+    w = np.prod(np.where(x, p, 1.0 - p), axis=1)
+    pay = o["payoff"]
+    X = {0: S[:, -1], 1: S[:, -1], 2: S.mean(axis=1), 3: S.mean(axis=1),
+         4: np.exp(np.log(S).mean(axis=1)), 5: np.exp(np.log(S).mean(axis=1)),
+         6: S.max(axis=1), 7: S.min(axis=1)}[pay]
+    v = np.maximum(X - o["K"], 0.0) if pay % 2 == 0 else np.maximum(o["K"] - X, 0.0)
+    return math.exp(-o["rate"] * o["T"]) * math.fsum(w * v)
+
+
+@pytest.mark.parametrize("payoff", range(8))
+def test_steps_constant_factors_match_the_lattice_oracle(oracle, payoff):
+    """Constant u, d, p reduce the time-varying walk to the recombining tree."""
+    for kind in (W.TREE_CRR, W.TREE_SEYDEL):
+        o = W.opt(12, 100.0, 98.0, 0.05, 0.3, 1.0, payoff, kind)
+        u, d, p = oracle.tree(kind, 12, 0.3, 0.05, 1.0)
+        steps = np.tile([u, d, p], (12, 1))
+        assert oracle.steps_price(o, steps, 4) == pytest.approx(oracle.price_exhaustive(o, 4), rel=1e-13, abs=1e-13)
+
+
+@pytest.mark.parametrize("payoff", range(8))
+def test_steps_match_numpy_brute_force(oracle, payoff):
+    steps = W.step_factors(3, 11)
+    o = W.opt(11, 100.0, 101.0, 0.04, 0.2, 1.0, payoff)
+    assert oracle.steps_price(o, steps, 4) == pytest.approx(_numpy_steps(o, steps), rel=1e-13, abs=1e-13)
+
+
+def test_steps_zero_strike_closed_forms(oracle):
+    """With K = 0 the calls are plain expectations of products of independent
+    steps: E[S_N] = S0 prod g_t, E[A] = (S0/N) sum_t prod_{i<=t} g_i with
+    g_i = p_i u_i + (1 - p_i) d_i, and E[G] = S0 prod_i E[m_i^{(N-i+1)/N}]."""
+    N = 14
+    steps = W.step_factors(5, N)
+    u, d, p = steps[:, 0], steps[:, 1], steps[:, 2]
+    g = p * u + (1 - p) * d
+    disc = math.exp(-0.03 * 1.5)
+    c = (N - np.arange(N)) / N
+    closed = {W.EURO_CALL: 100.0 * np.prod(g),
+              W.ASIAN_ARITH_CALL: 100.0 / N * np.sum(np.cumprod(g)),
+              W.ASIAN_GEO_CALL: 100.0 * np.prod(p * u ** c + (1 - p) * d ** c)}
+    for pay, v in closed.items():
+        o = W.opt(N, 100.0, 0.0, 0.03, 0.2, 1.5, pay)
+        assert oracle.steps_price(o, steps, 4) == pytest.approx(disc * v, rel=1e-13)
+
+
+def test_steps_put_call_parity_and_weights(oracle):
+    N = 13
+    steps = W.step_factors(9, N)
+    u, d, p = steps[:, 0], steps[:, 1], steps[:, 2]
+    g = p * u + (1 - p) * d
+    disc = math.exp(-0.05)
+    EA = 100.0 / N * np.sum(np.cumprod(g))
+    c = oracle.steps_price(W.opt(N, 100.0, 97.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL), steps, 4)
+    q = oracle.steps_price(W.opt(N, 100.0, 97.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_PUT), steps, 4)
+    assert c - q == pytest.approx(disc * (EA - 97.0), rel=1e-12)
+    o = W.opt(N, 100.0, 97.0, 0.05, 0.2, 1.0, W.EURO_CALL)
+    assert math.fsum(oracle.steps_path_prob(o, steps, b) for b in range(1 << N)) == pytest.approx(1.0, abs=1e-14)
