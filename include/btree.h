@@ -174,6 +174,21 @@ bt_status bt_exact_plan_info_get(const bt_exact_plan *plan, bt_exact_plan_info *
 bt_status bt_exact_plan_kernel_ms(bt_exact_plan *plan, float *ms);
 void bt_exact_plan_destroy(bt_exact_plan *plan);
 
+/* Time-varying trees ------------------------------------------------------- */
+/* eq. f13 with per-step moves and probabilities -- the case Section 2 names
+ * where eq. f8 no longer applies. Step t of option i multiplies the price by
+ * u_t (up, with probability p_t) or by d_t, read from the host array steps:
+ * (u_t, d_t, p_t) = steps[3 (o_i + t - 1) + 0, 1, 2] with o_i = N_0 + ... +
+ * N_{i-1} (options' steps concatenated, step 1 first). Of opts[i] the fields
+ * N (<= 40), payoff, S0, K, rate and T (discount e^{-rate T}) are used;
+ * tree_kind, sigma, u, d, p are ignored. The tree need not recombine: every
+ * path is evaluated, with weight prod_t p_t^{x_t} (1 - p_t)^{1 - x_t}.
+ * Requires 0 < d_t < u_t and 0 < p_t < 1 (BT_EINVAL), and for FP32_COMP
+ * min(p_t, 1 - p_t) >= 0.004 (BT_EUNSUPPORTED). Every option is its own pass
+ * (no call/put fusion). Results as bt_price_exact; synchronous on `stream`. */
+bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, int32_t n, const double *steps,
+                               bt_precision prec, bt_result *out, void *stream);
+
 /* Greeks of the exhaustive value ------------------------------------------- */
 /* Not in the paper: derivatives of eq. f13 for opts[0..n): value[i] = V and
  * grad[4 i + 0..3] = dV/dS0, dV/dsigma, dV/drate, dV/dK. One derivative pass

@@ -112,6 +112,7 @@ def lib():
         _proto(L, "bt_price_exact_noalloc", [_vp, _i32, C.c_int, _vp, _vp])
         _proto(L, "bt_price_mc", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _vp, _vp])
         _proto(L, "bt_price_mc_ex", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _i32, _vp, _vp, _vp])
+        _proto(L, "bt_price_exact_steps", [_vp, _vp, _i32, _vp, C.c_int, _vp, _vp])
         _proto(L, "bt_price_mc_shard", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _i32, _i32, _vp, _vp, _vp])
         _proto(L, "bt_philox4x32_10", [_vp, _vp, _vp, _vp, _i32])
         _proto(L, "bt_greeks_exact", [_vp, _vp, _i32, C.c_int, _vp, _vp, _vp])
@@ -261,6 +262,21 @@ def bt_price_mc_ex(ctx, opts, strata_bits, samples_per_stratum, seed, kind=BT_MC
     _check(lib().bt_price_mc_ex(ctx, a.ctypes.data, len(a), strata_bits, samples_per_stratum, seed, kind,
                                 out.ctypes.data, strata.ctypes.data if with_strata else None, _stream(stream)))
     return (out, strata) if with_strata else out
+
+
+def bt_price_exact_steps(ctx, opts, steps, prec=BT_PREC_FP32_COMP, stream=None) -> np.ndarray:
+    """Time-varying trees: steps is a sequence of per-option [N][3] arrays
+    (u_t, d_t, p_t), or one array of all options' steps concatenated."""
+    a = options_array(opts)
+    if isinstance(steps, (list, tuple)):
+        steps = np.concatenate([np.asarray(s, dtype=np.float64).reshape(-1, 3) for s in steps])
+    st = np.ascontiguousarray(np.asarray(steps, dtype=np.float64).reshape(-1, 3))
+    if st.shape[0] != int(a["N"].sum()):
+        raise ValueError("steps holds %d steps, the options need %d" % (st.shape[0], int(a["N"].sum())))
+    out = np.zeros(len(a), dtype=RESULT_DTYPE)
+    _check(lib().bt_price_exact_steps(ctx, a.ctypes.data, len(a), st.ctypes.data, prec, out.ctypes.data,
+                                      _stream(stream)))
+    return out
 
 
 def bt_price_mc_shard(ctx, opts, strata_bits, samples_per_stratum, seed, shard, n_shards, with_strata=False,

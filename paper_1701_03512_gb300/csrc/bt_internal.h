@@ -56,6 +56,11 @@ struct bt_pentry {            // one entry of a two-level prefix table
     int32_t pad;
 };
 
+struct bt_spentry {           // one entry of a time-varying two-level prefix table (steps.cu)
+    double rho, irho, R, mx, mn, e, ie, w;              // FP64
+    float2 rho2, irho2, R2, mx2, mn2, e2, ie2, w2;      // the same as FP32 pairs
+};
+
 struct bt_pow {               // u^e for some exponent e, in FP64 and as an FP32 pair
     double v;
     float hi, lo;
@@ -113,6 +118,11 @@ int bt_launch_exact(const bt_exact_args *a, int prec, int grid, void *stream);
 int bt_launch_finalize(const bt_job *d_jobs, const bt_jparams *d_prm, int n_jobs, const double2 *partials,
                        int shard, int n_shards, int prec, bt_result *d_out, void *stream);
 int bt_exact_grid_size(int prec, int device);
+int bt_launch_steps_params(const bt_option *d_opts, const bt_job *d_jobs, const double *d_steps, bt_jparams *d_prm,
+                           int n_jobs, void *stream);
+int bt_launch_steps_tables(const bt_job *d_jobs, const bt_jparams *d_prm, const double *d_steps, int n_jobs,
+                           int max_len, int prec, float4 *suf32, double2 *suf64, bt_spentry *tab, void *stream);
+int bt_launch_steps(const bt_exact_args *a, const bt_spentry *tab, int prec, int device, void *stream);
 int bt_launch_greeks(const bt_exact_args *a, int grid, void *stream);
 int bt_launch_greeks_finalize(const bt_job *d_jobs, int n_jobs, const double4 *partials, double4 *sums,
                               void *stream);

@@ -199,7 +199,7 @@ static bool same_params(const bt_option &a, const bt_option &b) {
 }
 
 // Payoff -> (suffix field, sign mode) of the affine form in exact.cu.
-static void payoff_field(int payoff, int *field, int *mode) {
+void payoff_field(int payoff, int *field, int *mode) {
     switch (payoff) {
     case BT_EURO_CALL: *field = BT_F_EURO; *mode = BT_MODE_CALL; break;
     case BT_EURO_PUT: *field = BT_F_EURO; *mode = BT_MODE_PUT; break;

@@ -30,6 +30,7 @@ cudaStream_t ctx_stream(bt_ctx *c, void *s);
 bt_status host_tree(const bt_option *o, double *u, double *d, double *p);
 bt_status validate_option(const bt_option *o, int idx, int max_n);
 int exact_split_L(int N);
+void payoff_field(int payoff, int *field, int *mode);
 void fill_job_shape(bt_job &J, int N, int field, int mode, int prec);
 bt_status plan_jobs(const bt_option *opts, int n, int prec, std::vector<bt_job> &jobs, int64_t *n_items,
                     int64_t *payoff_paths, int64_t *path_evals, int max_n);

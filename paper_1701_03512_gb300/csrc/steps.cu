@@ -1,0 +1,428 @@
+// Time-varying trees: eq. f13 with per-step moves and probabilities, sm_103a.
+//
+// Step t multiplies the price by u_t (up, probability p_t) or by d_t; the
+// tree need not recombine, so every path is evaluated. The prefix/suffix
+// split of exact.cu still applies, because the suffix steps sit at the same
+// positions P+1..N under every prefix: with rho_j(s) = S_{P+j}/S_P the
+// suffix's relative prices, each payoff is beta_q max(+-(tau_q + f_s), 0) + C_q
+// with f_s = sum_j rho_j (arithmetic Asian), exp(sum_j ln rho_j / N)
+// (geometric), rho_L (European), max_j or min_j rho_j (lookback). What
+// changes is the weight: w(x) = w_q w_s with w_s the product over the suffix
+// of p_t or 1 - p_t, a different number for every suffix. So each path's
+// payoff is multiplied by its suffix weight (one more multiply-add per path)
+// instead of summing an up-count group before one multiplication.
+//
+// Prefix states come from two-level tables over the steps 1..H and H+1..P
+// (end factor and its inverse, backward-relative partial sum, extreme
+// relative prices, geometric factor and its inverse, weight; FP64 and as FP32
+// pairs), composed per prefix in pair arithmetic. The FP32 path keeps the
+// rounding design of exact.cu (scaled affine form, exact lambda f_hi + A_hi,
+// one rounding per payoff); the weight enters as w_hi z + w_lo z.
+//
+// A job reuses bt_job: off_pow is the index of its first step in the step
+// array (three doubles per step: u, d, p), off_ph and off_pm index the
+// bt_spentry arena, off_suf the suffix arena (4 floats or 2 doubles per
+// entry), suf_len counts entries (2^L, at least 8; padding has weight 0).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bt_internal.h"
+#include "df.cuh"
+#include "exact_common.cuh"
+
+#define BT_SBIG 1.0e30  // the minimum over an empty block
+
+struct sblock {
+    double rho, R, sum, mx, mn, lg, w;
+};
+
+// Walks `bits` steps of x (MSB first) whose moves are st[3 (t-1) + 0/1/2] =
+// (u, d, p): end factor rho = S_end/S_start, backward-relative partial sum
+// R = sum_t S_t/S_end, forward-relative sum sum_t S_t/S_start, extreme
+// relative prices, sum of ln(S_t/S_start) and the block's weight.
+__device__ static sblock walk_steps(uint64_t x, int bits, const double *st) {
+    sblock b;
+    double rel = 1.0, R = 0.0, sum = 0.0, mx = 0.0, mn = BT_SBIG, lg = 0.0, w = 1.0;
+    for (int t = 1; t <= bits; ++t) {
+        const bool up = (x >> (bits - t)) & 1u;
+        const double m = up ? st[3 * (t - 1)] : st[3 * (t - 1) + 1];
+        const double p = st[3 * (t - 1) + 2];
+        rel *= m;
+        R = R / m + 1.0;
+        sum += rel;
+        mx = fmax(mx, rel);
+        mn = fmin(mn, rel);
+        lg += log(rel);
+        w *= up ? p : 1.0 - p;
+    }
+    b.rho = rel;
+    b.R = R;
+    b.sum = sum;
+    b.mx = mx;
+    b.mn = mn;
+    b.lg = lg;
+    b.w = w;
+    return b;
+}
+
+// f_s of a suffix block for the job's field.
+__device__ static double suffix_f(int field, const sblock &b, int N) {
+    switch (field) {
+    case BT_F_ARITH: return b.sum;
+    case BT_F_GEO: return exp(b.lg / (double)N);
+    case BT_F_EURO: return b.rho;
+    case BT_F_LOOKMAX: return b.mx;
+    default: return b.mn;
+    }
+}
+
+// a1 for time-varying jobs: scalars and the suffix f range (every f_s is
+// non-decreasing in each step's move, so all-down and all-up bound it).
+__global__ void k_steps_params(const bt_option *opts, const bt_job *jobs, const double *steps, bt_jparams *prm,
+                               int n_jobs) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_jobs) return;
+    const bt_job J = jobs[j];
+    const bt_option o = opts[J.opt];
+    bt_jparams P;
+    memset(&P, 0, sizeof(P));
+    P.ok = 1;
+    P.disc = exp(-o.rate * o.T);
+    P.S0 = o.S0;
+    P.K = o.K;
+    P.NKoS0 = (double)J.N * o.K / o.S0;
+    P.KoS0 = o.K / o.S0;
+    P.S0oN = o.S0 / (double)J.N;
+    const double *st = steps + 3 * (J.off_pow + J.P);
+    P.fmin = suffix_f(J.field, walk_steps(0, J.L, st), J.N);
+    P.fmax = suffix_f(J.field, walk_steps((1ull << J.L) - 1, J.L, st), J.N);
+    P.NKoS0_2 = split2(P.NKoS0);
+    P.KoS0_2 = split2(P.KoS0);
+    P.S0oN_2 = split2(P.S0oN);
+    P.S0_2 = split2(P.S0);
+    P.K_2 = split2(P.K);
+    P.fmin_f = (float)P.fmin;
+    P.fmax_f = (float)P.fmax;
+    int ef;
+    frexp(P.fmax, &ef);  // fmax <= 2^ef
+    P.gexp = ef - 10;
+    prm[J.prm_off] = P;
+}
+
+__device__ static bt_spentry make_spentry(const sblock &b, double e) {
+    bt_spentry r;
+    r.rho = b.rho;
+    r.irho = 1.0 / b.rho;
+    r.R = b.R;
+    r.mx = b.mx;
+    r.mn = b.mn;
+    r.e = e;
+    r.ie = 1.0 / e;
+    r.w = b.w;
+    r.rho2 = split2(r.rho);
+    r.irho2 = split2(r.irho);
+    r.R2 = split2(r.R);
+    r.mx2 = split2(r.mx);
+    r.mn2 = split2(r.mn);
+    r.e2 = split2(r.e);
+    r.ie2 = split2(r.ie);
+    r.w2 = split2(r.w);
+    return r;
+}
+
+// a2/a3 for time-varying jobs: suffix entries (f, w) and the two prefix
+// tables. The geometric factor of a prefix block folds in the later steps
+// that inherit its end price: e_h = exp((lg_h + (M + L) ln rho_h)/N) for the
+// first block, e_m = exp((lg_m + L ln rho_m)/N) for the second.
+__global__ void k_steps_tables(const bt_job *jobs, const bt_jparams *prm, const double *steps, int prec,
+                               float4 *suf32, double2 *suf64, bt_spentry *tab) {
+    const bt_job J = jobs[blockIdx.y];
+    const bt_jparams &Pj = prm[J.prm_off];
+    const double *st = steps + 3 * J.off_pow;
+    const int64_t nsuf = 1ll << J.L, nh = 1ll << J.H, nm = 1ll << J.M;
+    const int64_t total = J.suf_len + nh + nm;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx;
+        if (i < J.suf_len) {
+            double f = 0.0, w = 0.0;  // padding: weight 0
+            if (i < nsuf) {
+                const sblock b = walk_steps((uint64_t)i, J.L, st + 3 * J.P);
+                f = suffix_f(J.field, b, J.N);
+                w = b.w;
+            }
+            if (prec == BT_PREC_FP64) {
+                suf64[J.off_suf + i] = make_double2(f, w);
+            } else {
+                const int gx = Pj.gexp;
+                const double fh = ldexp(rint(ldexp(f, -gx)), gx);
+                const float2 w2 = split2(w);
+                suf32[J.off_suf + i] = make_float4((float)fh, -(float)(f - fh), w2.x, w2.y);
+            }
+            continue;
+        }
+        i -= J.suf_len;
+        if (i < nh) {
+            const sblock b = walk_steps((uint64_t)i, J.H, st);
+            const double e = exp((b.lg + (double)(J.M + J.L) * log(b.rho)) / (double)J.N);
+            tab[J.off_ph + i] = make_spentry(b, e);
+            continue;
+        }
+        i -= nh;
+        const sblock b = walk_steps((uint64_t)i, J.M, st + 3 * J.H);
+        const double e = exp((b.lg + (double)J.L * log(b.rho)) / (double)J.N);
+        tab[J.off_pm + i] = make_spentry(b, e);
+    }
+}
+
+// Per-prefix affine form and weight in FP32 pairs.
+struct sstate {
+    df32 tau, beta, cst, w;
+};
+__device__ __forceinline__ sstate steps_state(const bt_job &J, const bt_jparams &P, const bt_spentry *tab,
+                                              int64_t q) {
+    const bt_spentry &eh = tab[J.off_ph + (q >> J.M)];
+    const bt_spentry &em = tab[J.off_pm + (q & ((1ll << J.M) - 1))];
+    sstate r;
+    const df32 rho_h = df_from2(eh.rho2), rho_m = df_from2(em.rho2);
+    const df32 ir = df_mul(df_from2(eh.irho2), df_from2(em.irho2));  // S0 / S_P
+    const df32 sp = df_mul(rho_h, rho_m);                              // S_P / S0
+    const df32 kk = df_from2(P.KoS0_2);
+    r.cst = df_make(0.0f, 0.0f);
+    switch (J.field) {
+    case BT_F_ARITH:
+        // Sigma_P / S_P = R_h / rho_m + R_m
+        r.tau = df_sub(df_add(df_mul(df_from2(eh.R2), df_from2(em.irho2)), df_from2(em.R2)),
+                       df_mul(df_from2(P.NKoS0_2), ir));
+        r.beta = df_mul(df_from2(P.S0oN_2), sp);
+        break;
+    case BT_F_EURO:
+        r.tau = df_neg(df_mul(kk, ir));
+        r.beta = df_mul(df_from2(P.S0_2), sp);
+        break;
+    case BT_F_GEO:
+        r.tau = df_neg(df_mul(kk, df_mul(df_from2(eh.ie2), df_from2(em.ie2))));
+        r.beta = df_mul(df_from2(P.S0_2), df_mul(df_from2(eh.e2), df_from2(em.e2)));
+        break;
+    case BT_F_LOOKMAX: {
+        // M_P / S0 = max(mx_h, rho_h mx_m); tau = -max(M_P, K) / S_P, C = max(M_P - K, 0)
+        const df32 a = df_from2(eh.mx2), b = df_mul(rho_h, df_from2(em.mx2));
+        const df32 mr = df_gt(a, b) ? a : b;
+        r.tau = df_neg(df_mul(df_gt(mr, kk) ? mr : kk, ir));
+        if (df_gt(mr, kk)) r.cst = df_mul(df_from2(P.S0_2), df_sub(mr, kk));
+        r.beta = df_mul(df_from2(P.S0_2), sp);
+        break;
+    }
+    default: {
+        const df32 a = df_from2(eh.mn2), b = df_mul(rho_h, df_from2(em.mn2));
+        const df32 mr = df_gt(a, b) ? b : a;
+        r.tau = df_neg(df_mul(df_gt(mr, kk) ? kk : mr, ir));
+        if (df_gt(kk, mr)) r.cst = df_mul(df_from2(P.S0_2), df_sub(kk, mr));
+        r.beta = df_mul(df_from2(P.S0_2), sp);
+        break;
+    }
+    }
+    r.w = df_mul(df_from2(eh.w2), df_from2(em.w2));
+    return r;
+}
+
+// One work item, FP32: per path y = lambda f_hi + A_hi, c = lambda (-f_lo) - A_lo,
+// z = sat(+-(y - c)), weighted z w_hi + z w_lo, eight-wide tree, TwoSum into
+// the prefix's running sum; prefixes combined in pairs, the block in FP64.
+template <int MODE>
+__device__ __forceinline__ void item_steps32(const bt_exact_args &a, const smem_job &sj, const float4 *s_suf,
+                                             const bt_spentry *tab, double2 *red) {
+    const bt_job &J = sj.J;
+    const bt_jparams &P = sj.P;
+    const int64_t item_local = sj.item - J.item_begin + J.item_offset;
+    const int64_t qbase = item_local << BT_LOW_BITS;
+    const int64_t nP = 1ll << J.P;
+    float B[BT_PT], Ah[BT_PT], nAl[BT_PT];
+    df32 om[BT_PT];
+    df32 cst = df_make(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) {
+        const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
+        if (q < nP) {
+            const sstate s = steps_state(J, P, tab, q);
+            const scale32 sc = scale_prefix(s.tau, P, q);
+            B[j] = sc.B;
+            Ah[j] = sc.Ah;
+            nAl[j] = sc.nAl;
+            om[j] = df_mul(df_mul(s.w, s.beta), sc.rinv);
+            cst = df_add_pos(cst, df_mul(s.w, s.cst));
+        } else {
+            B[j] = 0.0f;
+            Ah[j] = nAl[j] = __int_as_float(0x7fc00000);  // sat(NaN) = 0
+            om[j] = df_make(0.0f, 0.0f);
+        }
+    }
+    float g[BT_PT], e[BT_PT];
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) g[j] = e[j] = 0.0f;
+    for (int s = 0; s < J.suf_len; s += BT_UNROLL) {
+        float4 f4[BT_UNROLL];
+#pragma unroll
+        for (int i = 0; i < BT_UNROLL; ++i) f4[i] = s_suf[s + i];
+#pragma unroll
+        for (int j = 0; j < BT_PT; ++j) {
+            float v[BT_UNROLL];
+#pragma unroll
+            for (int i = 0; i < BT_UNROLL; ++i) {
+                const float y = __fmaf_rn(B[j], f4[i].x, Ah[j]);
+                const float c = __fmaf_rn(B[j], f4[i].y, nAl[j]);
+                const float z = (MODE & BT_MODE_CALL) ? __saturatef(__fsub_rn(y, c)) : __saturatef(__fsub_rn(c, y));
+                v[i] = __fmaf_rn(f4[i].z, z, __fmul_rn(f4[i].w, z));
+            }
+#pragma unroll
+            for (int w = 1; w < BT_UNROLL; w *= 2)
+#pragma unroll
+                for (int i = 0; i < BT_UNROLL; i += 2 * w) v[i] = __fadd_rn(v[i], v[i + w]);
+            const float sN = __fadd_rn(g[j], v[0]);
+            e[j] = __fadd_rn(e[j], __fsub_rn(v[0], __fsub_rn(sN, g[j])));
+            g[j] = sN;
+        }
+    }
+    df32 tot = df_make(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) tot = df_add_pos(tot, df_mul(om[j], fast_two_sum(g[j], e[j])));
+    double v = df_to_double(tot);
+    if (J.field == BT_F_LOOKMAX || J.field == BT_F_LOOKMIN) v += df_to_double(cst);
+    const double2 sum = (MODE & BT_MODE_CALL) ? block_sum2(v, 0.0, red) : block_sum2(0.0, v, red);
+    if (threadIdx.x == 0) a.partials[J.part_off + item_local] = sum;
+}
+
+// One work item, FP64 (the accuracy reference): y = tau + f, payoff/beta =
+// max(+-y, 0), weighted by w_s with one FMA.
+template <int MODE>
+__device__ __forceinline__ void item_steps64(const bt_exact_args &a, const smem_job &sj, const double2 *s_suf,
+                                             const bt_spentry *tab, double2 *red) {
+    const bt_job &J = sj.J;
+    const bt_jparams &P = sj.P;
+    const int64_t item_local = sj.item - J.item_begin + J.item_offset;
+    const int64_t qbase = item_local << BT_LOW_BITS;
+    const int64_t nP = 1ll << J.P;
+    double tau[BT_PT64], om[BT_PT64], cst = 0.0;
+#pragma unroll
+    for (int j = 0; j < BT_PT64; ++j) {
+        const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
+        tau[j] = nan("");
+        om[j] = 0.0;
+        if (q >= nP) continue;
+        const bt_spentry &eh = tab[J.off_ph + (q >> J.M)];
+        const bt_spentry &em = tab[J.off_pm + (q & ((1ll << J.M) - 1))];
+        const double ir = eh.irho * em.irho, sp = eh.rho * em.rho, w = eh.w * em.w;
+        double beta = P.S0 * sp, c = 0.0;
+        switch (J.field) {
+        case BT_F_ARITH:
+            tau[j] = fma(eh.R, em.irho, em.R) - P.NKoS0 * ir;
+            beta = P.S0oN * sp;
+            break;
+        case BT_F_EURO: tau[j] = -P.KoS0 * ir; break;
+        case BT_F_GEO:
+            tau[j] = -P.KoS0 * eh.ie * em.ie;
+            beta = P.S0 * eh.e * em.e;
+            break;
+        case BT_F_LOOKMAX: {
+            const double mr = fmax(eh.mx, eh.rho * em.mx);
+            tau[j] = -fmax(mr, P.KoS0) * ir;
+            c = fmax(P.S0 * mr - P.K, 0.0);
+            break;
+        }
+        default: {
+            const double mr = fmin(eh.mn, eh.rho * em.mn);
+            tau[j] = -fmin(mr, P.KoS0) * ir;
+            c = fmax(P.K - P.S0 * mr, 0.0);
+            break;
+        }
+        }
+        om[j] = w * beta;
+        cst += w * c;
+    }
+    double acc[BT_PT64];
+#pragma unroll
+    for (int j = 0; j < BT_PT64; ++j) acc[j] = 0.0;
+    for (int s = 0; s < J.suf_len; ++s) {
+        const double2 fw = s_suf[s];
+#pragma unroll
+        for (int j = 0; j < BT_PT64; ++j) {
+            const double y = tau[j] + fw.x;
+            // NaN (a masked prefix) contributes nothing
+            const double z = (MODE & BT_MODE_CALL) ? (y > 0.0 ? y : 0.0) : (y < 0.0 ? -y : 0.0);
+            acc[j] = fma(fw.y, z, acc[j]);
+        }
+    }
+    double v = 0.0;
+#pragma unroll
+    for (int j = 0; j < BT_PT64; ++j) v = fma(om[j], acc[j], v);
+    if (J.field == BT_F_LOOKMAX || J.field == BT_F_LOOKMIN) v += cst;
+    const double2 sum = (MODE & BT_MODE_CALL) ? block_sum2(v, 0.0, red) : block_sum2(0.0, v, red);
+    if (threadIdx.x == 0) a.partials[J.part_off + item_local] = sum;
+}
+
+__global__ void __launch_bounds__(BT_THREADS, 2) k_steps32(bt_exact_args a, const bt_spentry *tab) {
+    extern __shared__ float4 s_suf4[];
+    __shared__ smem_job sj;
+    __shared__ double2 red[BT_THREADS / 32];
+    int cur_job = -1;
+    while (next_item<float4>(a, sj, s_suf4, reinterpret_cast<const float4 *>(a.suf32), cur_job)) {
+        if (sj.J.mode == BT_MODE_CALL) item_steps32<BT_MODE_CALL>(a, sj, s_suf4, tab, red);
+        else item_steps32<BT_MODE_PUT>(a, sj, s_suf4, tab, red);
+    }
+}
+
+__global__ void __launch_bounds__(BT_THREADS, 2) k_steps64(bt_exact_args a, const bt_spentry *tab) {
+    extern __shared__ double2 s_suf2[];
+    __shared__ smem_job sj;
+    __shared__ double2 red[BT_THREADS / 32];
+    int cur_job = -1;
+    while (next_item<double2>(a, sj, s_suf2, reinterpret_cast<const double2 *>(a.suf64), cur_job)) {
+        if (sj.J.mode == BT_MODE_CALL) item_steps64<BT_MODE_CALL>(a, sj, s_suf2, tab, red);
+        else item_steps64<BT_MODE_PUT>(a, sj, s_suf2, tab, red);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+#define BT_STEPS_SMEM ((size_t)(1 << BT_MAX_L) * 16)
+
+extern "C" int bt_launch_steps_params(const bt_option *d_opts, const bt_job *d_jobs, const double *d_steps,
+                                      bt_jparams *d_prm, int n_jobs, void *stream) {
+    if (n_jobs <= 0) return 0;
+    k_steps_params<<<(n_jobs + 63) / 64, 64, 0, (cudaStream_t)stream>>>(d_opts, d_jobs, d_steps, d_prm, n_jobs);
+    return (int)cudaGetLastError();
+}
+
+extern "C" int bt_launch_steps_tables(const bt_job *d_jobs, const bt_jparams *d_prm, const double *d_steps,
+                                      int n_jobs, int max_len, int prec, float4 *suf32, double2 *suf64,
+                                      bt_spentry *tab, void *stream) {
+    if (n_jobs <= 0) return 0;
+    int bx = (max_len + 255) / 256;
+    if (bx > 64) bx = 64;
+    if (bx < 1) bx = 1;
+    dim3 grid(bx, n_jobs);
+    k_steps_tables<<<grid, 256, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, d_steps, prec, suf32, suf64, tab);
+    return (int)cudaGetLastError();
+}
+
+// Persistent grid: SMs x resident blocks at the full suffix table size.
+extern "C" int bt_launch_steps(const bt_exact_args *a, const bt_spentry *tab, int prec, int device, void *stream) {
+    if (a->n_run_items <= 0) return 0;
+    const void *k = prec == BT_PREC_FP64 ? (const void *)k_steps64 : (const void *)k_steps32;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BT_STEPS_SMEM);
+    if (e != cudaSuccess) return (int)e;
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BT_THREADS, BT_STEPS_SMEM);
+    if (e != cudaSuccess) return (int)e;
+    if (per < 1) per = 1;
+    int64_t grid = (int64_t)sms * per;
+    if (grid > a->n_run_items) grid = a->n_run_items;
+    if (prec == BT_PREC_FP64)
+        k_steps64<<<(unsigned)grid, BT_THREADS, BT_STEPS_SMEM, (cudaStream_t)stream>>>(*a, tab);
+    else
+        k_steps32<<<(unsigned)grid, BT_THREADS, BT_STEPS_SMEM, (cudaStream_t)stream>>>(*a, tab);
+    return (int)cudaGetLastError();
+}
