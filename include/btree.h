@@ -189,6 +189,28 @@ void bt_exact_plan_destroy(bt_exact_plan *plan);
 bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, int32_t n, const double *steps,
                                bt_precision prec, bt_result *out, void *stream);
 
+/* Payoff plug-ins ------------------------------------------------------------ */
+/* Any V(x) of the whole path (the general expected value of eq. expval, and
+ * eq. f13 for payoffs beyond the eight built in): `source` is CUDA C++
+ * defining struct Payoff with the state-machine interface documented in
+ * btree_payoff.cuh. bt_plugin_compile appends it to that header and builds
+ * the generic pass for the context's GPU with the run-time compiler
+ * (libnvrtc, loaded on first use: BT_EUNSUPPORTED without it). A compile
+ * error returns BT_EINVAL; the compiler's log (also on success) goes to
+ * log[0..log_size) if log is not NULL. The plug-in belongs to the caller
+ * until bt_plugin_destroy. */
+typedef struct bt_payoff_plugin bt_payoff_plugin;
+bt_status bt_plugin_compile(bt_ctx *ctx, const char *source, char *log, size_t log_size, bt_payoff_plugin **out);
+void bt_plugin_destroy(bt_payoff_plugin *plugin);
+/* V = e^{-rate T} sum_x p(x) V(x) for opts[0..n), every path evaluated
+ * (N <= 40; FP64 weights and sums, two state steps per path on average).
+ * steps: as for bt_price_exact_steps, or NULL for each option's own tree
+ * (tree_kind, sigma, ...). params: host array [n][8] handed to the plug-in,
+ * or NULL for param[0] = K and zeros. out[i].value, paths = 2^N, err_est =
+ * 1e-13 |value|. Synchronous on `stream`. */
+bt_status bt_price_exact_plugin(bt_ctx *ctx, const bt_payoff_plugin *plugin, const bt_option *opts, int32_t n,
+                                const double *steps, const double *params, bt_result *out, void *stream);
+
 /* Greeks of the exhaustive value ------------------------------------------- */
 /* Not in the paper: derivatives of eq. f13 for opts[0..n): value[i] = V and
  * grad[4 i + 0..3] = dV/dS0, dV/dsigma, dV/drate, dV/dK. One derivative pass

@@ -113,6 +113,10 @@ def lib():
         _proto(L, "bt_price_mc", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _vp, _vp])
         _proto(L, "bt_price_mc_ex", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _i32, _vp, _vp, _vp])
         _proto(L, "bt_price_exact_steps", [_vp, _vp, _i32, _vp, C.c_int, _vp, _vp])
+        _proto(L, "bt_plugin_compile", [_vp, C.c_char_p, C.c_char_p, C.c_size_t, C.POINTER(_vp)])
+        _proto(L, "bt_price_exact_plugin", [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp])
+        L.bt_plugin_destroy.argtypes = [_vp]
+        L.bt_plugin_destroy.restype = None
         _proto(L, "bt_price_mc_shard", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _i32, _i32, _vp, _vp, _vp])
         _proto(L, "bt_philox4x32_10", [_vp, _vp, _vp, _vp, _i32])
         _proto(L, "bt_greeks_exact", [_vp, _vp, _i32, C.c_int, _vp, _vp, _vp])
@@ -276,6 +280,41 @@ def bt_price_exact_steps(ctx, opts, steps, prec=BT_PREC_FP32_COMP, stream=None) 
     out = np.zeros(len(a), dtype=RESULT_DTYPE)
     _check(lib().bt_price_exact_steps(ctx, a.ctypes.data, len(a), st.ctypes.data, prec, out.ctypes.data,
                                       _stream(stream)))
+    return out
+
+
+def bt_plugin_compile(ctx, source: str):
+    """Compiles a payoff plug-in (struct Payoff, see include/btree_payoff.cuh).
+    Returns (handle, compiler log); raises BtError with the log on errors."""
+    log = C.create_string_buffer(16384)
+    h = _vp()
+    st = lib().bt_plugin_compile(ctx, source.encode(), log, len(log), C.byref(h))
+    if st != BT_OK:
+        raise BtError(st, lib().bt_last_error().decode() + "\n" + log.value.decode(errors="replace"))
+    return h, log.value.decode(errors="replace")
+
+
+def bt_plugin_destroy(plugin):
+    lib().bt_plugin_destroy(plugin)
+
+
+def bt_price_exact_plugin(ctx, plugin, opts, steps=None, params=None, stream=None) -> np.ndarray:
+    a = options_array(opts)
+    st = None
+    if steps is not None:
+        if isinstance(steps, (list, tuple)):
+            steps = np.concatenate([np.asarray(s, dtype=np.float64).reshape(-1, 3) for s in steps])
+        st = np.ascontiguousarray(np.asarray(steps, dtype=np.float64).reshape(-1, 3))
+        if st.shape[0] != int(a["N"].sum()):
+            raise ValueError("steps holds %d steps, the options need %d" % (st.shape[0], int(a["N"].sum())))
+    pr = None
+    if params is not None:
+        pr = np.zeros((len(a), 8))
+        p_in = np.asarray(params, dtype=np.float64).reshape(len(a), -1)
+        pr[:, :p_in.shape[1]] = p_in
+    out = np.zeros(len(a), dtype=RESULT_DTYPE)
+    _check(lib().bt_price_exact_plugin(ctx, plugin, a.ctypes.data, len(a), None if st is None else st.ctypes.data,
+                                       None if pr is None else pr.ctypes.data, out.ctypes.data, _stream(stream)))
     return out
 
 

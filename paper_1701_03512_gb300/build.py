@@ -37,13 +37,23 @@ def _sources():
 
 def _headers():
     return sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
-                  glob.glob(os.path.join(HERE, "..", "include", "*.h")))
+                  glob.glob(os.path.join(HERE, "..", "include", "*.h")) +
+                  glob.glob(os.path.join(HERE, "..", "include", "*.cuh")))
+
+
+def _embed_payoff_header():
+    """The plug-in header as a C++ string literal, for the run-time compiler."""
+    hdr = open(os.path.join(HERE, "..", "include", "btree_payoff.cuh")).read()
+    if ")BTPSRC" in hdr:
+        raise RuntimeError("btree_payoff.cuh must not contain the delimiter )BTPSRC")
+    with open(os.path.join(OBJ_DIR, "btree_payoff_src.inc"), "w") as f:
+        f.write('R"BTPSRC(' + hdr + ')BTPSRC"\n')
 
 
 def _compile(src: str, extra=()) -> str:
     obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
     cmd = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
-           "-I", os.path.join(HERE, "..", "include"), "-c", src, "-o", obj, *extra]
+           "-I", os.path.join(HERE, "..", "include"), "-I", OBJ_DIR, "-c", src, "-o", obj, *extra]
     if src.endswith(".cpp"):
         cmd.insert(1, "-x")
         cmd.insert(2, "cu")
@@ -64,6 +74,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if not force and not needs_build():
         return LIB
     os.makedirs(OBJ_DIR, exist_ok=True)
+    _embed_payoff_header()
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
