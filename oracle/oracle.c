@@ -754,3 +754,102 @@ double orc_steps_price(const orc_steps_model *m, int nthreads) {
     free(ws); free(th); free(started);
     return m->disc * nsum_get(&tot);
 }
+
+/* ------------------------------------------------------------------------ */
+/* b-ary trees (end of Section 3)                                            */
+/* ------------------------------------------------------------------------ */
+static int branch_digit(const orc_branch_model *m, uint64_t idx, int t) {
+    /* digit of step t (1-based), the first step most significant */
+    uint64_t v = idx;
+    for (int k = m->N; k > t; --k) v /= (uint64_t)m->b;
+    return (int)(v % (uint64_t)m->b);
+}
+
+static double branch_quantity(const orc_branch_model *m, uint64_t idx) {
+    int N = m->N;
+    double sum = 0.0, lsum = 0.0, mx = -INFINITY, mn = INFINITY, St = m->S0;
+    for (int t = 1; t <= N; ++t) {
+        int x = branch_digit(m, idx, t);
+        St = St * m->f[(t - 1) * m->b + x];
+        sum += St;
+        lsum += log(St);
+        if (St > mx) mx = St;
+        if (St < mn) mn = St;
+    }
+    switch (m->payoff) {
+    case ORC_EURO_CALL: case ORC_EURO_PUT: return St;
+    case ORC_ARITH_CALL: case ORC_ARITH_PUT: return sum / (double)N;
+    case ORC_GEO_CALL: case ORC_GEO_PUT: return exp(lsum / (double)N);
+    case ORC_LOOK_CALL: return mx;
+    default: return mn;
+    }
+}
+
+double orc_branch_path_payoff(const orc_branch_model *m, uint64_t idx) {
+    return payoff_of(m->payoff, m->K, branch_quantity(m, idx));
+}
+
+double orc_branch_path_prob(const orc_branch_model *m, uint64_t idx) {
+    double w = 1.0;
+    for (int t = 1; t <= m->N; ++t) w *= m->q[(t - 1) * m->b + branch_digit(m, idx, t)];
+    return w;
+}
+
+typedef struct { const orc_branch_model *m; uint64_t lo, hi; nsum acc; } branch_worker_t;
+
+static void *branch_worker_run(void *arg) {
+    branch_worker_t *w = (branch_worker_t *)arg;
+    w->acc.s = 0.0; w->acc.c = 0.0;
+    for (uint64_t i = w->lo; i < w->hi; ++i)
+        nsum_add(&w->acc, orc_branch_path_prob(w->m, i) * orc_branch_path_payoff(w->m, i));
+    return NULL;
+}
+
+double orc_branch_price(const orc_branch_model *m, int nthreads) {
+    if (m->N < 1 || m->b < 2) return NAN;
+    uint64_t total = 1;
+    for (int t = 0; t < m->N; ++t) {
+        if (total > ((uint64_t)1 << 62) / (uint64_t)m->b) return NAN;
+        total *= (uint64_t)m->b;
+    }
+    int M = nthreads < 1 ? 1 : nthreads;
+    if ((uint64_t)M > total) M = (int)total;
+    branch_worker_t *ws = (branch_worker_t *)calloc((size_t)M, sizeof(branch_worker_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)M, sizeof(pthread_t));
+    int *started = (int *)calloc((size_t)M, sizeof(int));
+    for (int k = 0; k < M; ++k) {
+        ws[k].m = m;
+        ws[k].lo = total / (uint64_t)M * (uint64_t)k + (k < (int)(total % (uint64_t)M) ? (uint64_t)k : total % (uint64_t)M);
+        ws[k].hi = total / (uint64_t)M * (uint64_t)(k + 1) +
+                   (k + 1 < (int)(total % (uint64_t)M) ? (uint64_t)(k + 1) : total % (uint64_t)M);
+        started[k] = (M > 1) && pthread_create(&th[k], NULL, branch_worker_run, &ws[k]) == 0;
+        if (!started[k]) branch_worker_run(&ws[k]);
+    }
+    nsum tot = {0.0, 0.0};
+    for (int k = 0; k < M; ++k) {
+        if (started[k]) pthread_join(th[k], NULL);
+        nsum_add(&tot, ws[k].acc.s);
+        nsum_add(&tot, ws[k].acc.c);
+    }
+    free(ws); free(th); free(started);
+    return m->disc * nsum_get(&tot);
+}
+
+double orc_branch_european_backward(const orc_branch_model *m) {
+    /* node (t, j), j = 0..(b-1) t, price S0 u^{j - c t} with u = f[0][b-1]^{1/c} */
+    const int N = m->N, b = m->b;
+    const double c = 0.5 * (double)(b - 1);
+    const double u = pow(m->f[b - 1], 1.0 / c);
+    const int W = (b - 1) * N + 1;
+    double *V = (double *)malloc(sizeof(double) * (size_t)W);
+    for (int j = 0; j < W; ++j) V[j] = payoff_of(m->payoff, m->K, m->S0 * pow(u, (double)j - c * N));
+    for (int t = N - 1; t >= 0; --t)
+        for (int j = 0; j <= (b - 1) * t; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < b; ++k) v += m->q[k] * V[j + k];
+            V[j] = v;
+        }
+    double r = m->disc * V[0];
+    free(V);
+    return r;
+}

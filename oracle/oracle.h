@@ -136,6 +136,31 @@ void orc_steps_sum_range(const orc_steps_model *m, uint64_t lo, uint64_t hi, dou
  * down to a power of two), partials added in rank order (eq. f14, f15). */
 double orc_steps_price(const orc_steps_model *m, int nthreads);
 
+/* Trees with b branches per node (the end of Section 3: the partition of the
+ * paths applies to trees with more than two branches, e.g. trinomial trees).
+ * A path is N digits x_t in 0..b-1, the first step the most significant digit
+ * of the path index in base b; digit k of step t multiplies the price by
+ * f[t-1][k] with probability q[t-1][k] (each row of q sums to 1).
+ * p(x) = prod_t q[t-1][x_t]. Payoffs as above. */
+typedef struct {
+    int32_t N, b;
+    int32_t payoff, pad;
+    double S0, K;
+    double disc;                 /* e^{-qT} */
+    const double *f, *q;         /* N x b each, step 1 first */
+} orc_branch_model;
+
+double orc_branch_path_payoff(const orc_branch_model *m, uint64_t idx);
+double orc_branch_path_prob(const orc_branch_model *m, uint64_t idx);
+/* Discounted value: b^N paths split into nthreads contiguous index ranges
+ * (Section 3's partition by leading digits when nthreads is a power of b),
+ * partials added in rank order. Needs b^N < 2^63. */
+double orc_branch_price(const orc_branch_model *m, int nthreads);
+/* European value by backward induction on a recombining b-ary lattice with
+ * the same moves at every step (f[0], q[0] used for all steps; f_k = u^{k - c}
+ * with c = (b-1)/2 so that node (t, j) has price S0 u^{j - c t}). */
+double orc_branch_european_backward(const orc_branch_model *m);
+
 /* Pathwise Greeks by enumeration for CRR trees: grad = dV/d(S0, sigma, rate, K).
  * Returns the value. */
 double orc_greeks_crr(int N, int payoff, double S0, double K, double rate, double sigma,

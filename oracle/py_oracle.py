@@ -44,6 +44,12 @@ class StepsModel(C.Structure):
                 ("p", C.POINTER(C.c_double))]
 
 
+class BranchModel(C.Structure):
+    _fields_ = [("N", C.c_int32), ("b", C.c_int32), ("payoff", C.c_int32), ("pad", C.c_int32),
+                ("S0", C.c_double), ("K", C.c_double), ("disc", C.c_double),
+                ("f", C.POINTER(C.c_double)), ("q", C.POINTER(C.c_double))]
+
+
 def lib():
     global _lib
     with _lock:
@@ -77,6 +83,11 @@ def lib():
             L.orc_steps_path_prob.argtypes = [ps, u64]; L.orc_steps_path_prob.restype = d
             L.orc_steps_sum_range.argtypes = [ps, u64, u64, pd, pd]
             L.orc_steps_price.argtypes = [ps, C.c_int]; L.orc_steps_price.restype = d
+            pb = C.POINTER(BranchModel)
+            L.orc_branch_path_payoff.argtypes = [pb, u64]; L.orc_branch_path_payoff.restype = d
+            L.orc_branch_path_prob.argtypes = [pb, u64]; L.orc_branch_path_prob.restype = d
+            L.orc_branch_price.argtypes = [pb, C.c_int]; L.orc_branch_price.restype = d
+            L.orc_branch_european_backward.argtypes = [pb]; L.orc_branch_european_backward.restype = d
             _lib = L
     return _lib
 
@@ -246,3 +257,31 @@ def steps_path_payoff(o: dict, steps, b: int) -> float:
 def steps_path_prob(o: dict, steps, b: int) -> float:
     m, keep = steps_model(o, steps)
     return lib().orc_steps_path_prob(C.byref(m), b)
+
+
+# ---------------------------------------------------------------------------
+# b-ary trees: moves[N][2b] = (factor of digit 0..b-1, probability of digit 0..b-1)
+# ---------------------------------------------------------------------------
+def branch_model(o: dict, moves, b: int):
+    mv = np.asarray(moves, dtype=np.float64).reshape(o["N"], 2 * b)
+    f = np.ascontiguousarray(mv[:, :b])
+    q = np.ascontiguousarray(mv[:, b:])
+    pd = C.POINTER(C.c_double)
+    m = BranchModel(o["N"], b, o["payoff"], 0, o["S0"], o["K"], math.exp(-o["rate"] * o["T"]),
+                    f.ctypes.data_as(pd), q.ctypes.data_as(pd))
+    return m, (f, q)
+
+
+def branch_price(o: dict, moves, b: int, nthreads: int = 8) -> float:
+    m, keep = branch_model(o, moves, b)
+    return lib().orc_branch_price(C.byref(m), nthreads)
+
+
+def branch_european_backward(o: dict, moves, b: int) -> float:
+    m, keep = branch_model(o, moves, b)
+    return lib().orc_branch_european_backward(C.byref(m))
+
+
+def branch_path_prob(o: dict, moves, b: int, idx: int) -> float:
+    m, keep = branch_model(o, moves, b)
+    return lib().orc_branch_path_prob(C.byref(m), idx)

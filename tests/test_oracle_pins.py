@@ -425,3 +425,63 @@ def test_steps_put_call_parity_and_weights(oracle):
     assert c - q == pytest.approx(disc * (EA - 97.0), rel=1e-12)
     o = W.opt(N, 100.0, 97.0, 0.05, 0.2, 1.0, W.EURO_CALL)
     assert math.fsum(oracle.steps_path_prob(o, steps, b) for b in range(1 << N)) == pytest.approx(1.0, abs=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# b-ary trees (the end of Section 3: trinomial and wider trees)
+# ---------------------------------------------------------------------------
+def _numpy_branch(o, moves, b):
+    N = o["N"]
+    idx = np.arange(b ** N, dtype=np.int64)
+    x = (idx[:, None] // (b ** (N - 1 - np.arange(N)))[None, :]) % b
+    f = moves[:, :b][np.arange(N)[None, :], x]
+    q = moves[:, b:][np.arange(N)[None, :], x]
+    S = o["S0"] * np.cumprod(f, axis=1)
+    w = np.prod(q, axis=1)
+    pay = o["payoff"]
+    X = {0: S[:, -1], 1: S[:, -1], 2: S.mean(axis=1), 3: S.mean(axis=1),
+         4: np.exp(np.log(S).mean(axis=1)), 5: np.exp(np.log(S).mean(axis=1)),
+         6: S.max(axis=1), 7: S.min(axis=1)}[pay]
+    v = np.maximum(X - o["K"], 0.0) if pay % 2 == 0 else np.maximum(o["K"] - X, 0.0)
+    return math.exp(-o["rate"] * o["T"]) * math.fsum(w * v)
+
+
+@pytest.mark.parametrize("payoff", range(8))
+def test_branch_trinomial_matches_numpy_brute_force(oracle, payoff):
+    moves = W.branch_moves(11, 8, 3)
+    o = W.opt(8, 100.0, 101.0, 0.03, 0.2, 1.0, payoff)
+    assert oracle.branch_price(o, moves, 3, 4) == pytest.approx(_numpy_branch(o, moves, 3), rel=1e-13, abs=1e-13)
+
+
+@pytest.mark.parametrize("payoff", range(8))
+def test_branch_binary_and_zero_middle_reduce_to_the_binomial_walk(oracle, payoff):
+    N = 11
+    steps = W.step_factors(21, N)
+    o = W.opt(N, 100.0, 99.0, 0.04, 0.2, 1.0, payoff)
+    ref = oracle.steps_price(o, steps, 4)
+    u, d, p = steps[:, 0], steps[:, 1], steps[:, 2]
+    two = np.stack([d, u, 1 - p, p], axis=1)                       # digit 1 = up
+    assert oracle.branch_price(o, two, 2, 4) == pytest.approx(ref, rel=1e-13, abs=1e-13)
+    three = np.stack([d, np.sqrt(u * d), u, 1 - p, np.zeros(N), p], axis=1)
+    assert oracle.branch_price(o, three, 3, 4) == pytest.approx(ref, rel=1e-13, abs=1e-13)
+
+
+def test_branch_european_on_a_recombining_trinomial_lattice(oracle):
+    """Constant moves (1/u, 1, u): the path sum equals backward induction."""
+    N, u = 12, math.exp(0.3 * math.sqrt(3 * 1.0 / 12))
+    q = [0.2, 0.5, 0.3]
+    moves = np.tile([1 / u, 1.0, u] + q, (N, 1))
+    for pay in (W.EURO_CALL, W.EURO_PUT):
+        o = W.opt(N, 100.0, 103.0, 0.05, 0.3, 1.0, pay)
+        assert oracle.branch_price(o, moves, 3, 4) == pytest.approx(
+            oracle.branch_european_backward(o, moves, 3), rel=1e-12)
+
+
+def test_branch_zero_strike_closed_forms(oracle):
+    N = 9
+    moves = W.branch_moves(5, N, 3)
+    g = np.sum(moves[:, :3] * moves[:, 3:], axis=1)
+    disc = math.exp(-0.02)
+    for pay, v in ((W.EURO_CALL, 100.0 * np.prod(g)), (W.ASIAN_ARITH_CALL, 100.0 / N * np.sum(np.cumprod(g)))):
+        o = W.opt(N, 100.0, 0.0, 0.02, 0.2, 1.0, pay)
+        assert oracle.branch_price(o, moves, 3, 4) == pytest.approx(disc * v, rel=1e-13)
