@@ -211,6 +211,22 @@ void bt_plugin_destroy(bt_payoff_plugin *plugin);
 bt_status bt_price_exact_plugin(bt_ctx *ctx, const bt_payoff_plugin *plugin, const bt_option *opts, int32_t n,
                                 const double *steps, const double *params, bt_result *out, void *stream);
 
+/* Trees with b branches per node (the end of Section 3: the partition of the
+ * paths applies to trinomial and wider trees). A path is N digits in
+ * 0..b-1, the first step the most significant digit of its index in base b.
+ * moves: host array, for each option's steps in turn (step 1 first, options
+ * concatenated), b factors then b probabilities indexed by the digit: digit
+ * k of step t multiplies the price by factor k with probability k (factors
+ * > 0, probabilities in [0,1] summing to 1 within 1e-12, else BT_EINVAL).
+ * With plugin NULL each option's own payoff (opts[i].payoff, K) is priced;
+ * else the plug-in with params as for bt_price_exact_plugin. 2 <= branches
+ * <= 8, b^N <= 2^48 (BT_EUNSUPPORTED above). Of opts[i]: N, payoff, S0, K,
+ * rate, T. Every path is evaluated by the generic pass of btree_payoff.cuh
+ * (FP64). paths = b^N. Synchronous on `stream`. */
+bt_status bt_price_exact_branching(bt_ctx *ctx, const bt_payoff_plugin *plugin, const bt_option *opts, int32_t n,
+                                   int32_t branches, const double *moves, const double *params, bt_result *out,
+                                   void *stream);
+
 /* Greeks of the exhaustive value ------------------------------------------- */
 /* Not in the paper: derivatives of eq. f13 for opts[0..n): value[i] = V and
  * grad[4 i + 0..3] = dV/dS0, dV/dsigma, dV/drate, dV/dK. One derivative pass

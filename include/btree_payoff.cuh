@@ -15,22 +15,25 @@
  *     __device__ static double value(const state &s, int N, const double *param);
  *
  * so that V(x) = value(step(...step(start(S0), S_1, 1, x_1)..., S_N, N, x_N))
- * with x_t the move of step t (1 = up), S_t the price after it, and param the
- * option's eight user parameters. A functional of the bits alone (the
- * general V of eq. expval) ignores S.
+ * with x_t the move of step t (a digit 0..b-1 in a tree with b branches per
+ * node; 1 = up, 0 = down in a binomial tree), S_t the price after it, and
+ * param the option's eight user parameters. A functional of the moves alone
+ * (the general V of eq. expval) ignores S.
  * It is compiled either into the caller's own CUDA code (instantiate
  * btp::run<Payoff> in a kernel) or at run time from source with
  * bt_plugin_compile (btree.h), which appends the plug-in source to this
  * header and builds it for the current GPU.
  *
- * The pass: an option's path index splits into P = N - L prefix steps and
- * L = min(N, 12) suffix steps. A work item is 256 prefixes, one per thread;
- * a thread walks its prefix once, then visits its 2^L suffixes in order as a
- * depth-first walk that keeps the state of every level, so consecutive
- * suffixes share their common first steps and a path costs two state steps
- * on average. Weights and the sum are FP64; the block's sum goes to one
- * partial per work item, in a fixed order. This header has no includes: it
- * is also the source that the run-time compiler sees. */
+ * The pass: a path is N digits in base b, the first step the most
+ * significant (the leading digits are Section 3's partition); its index
+ * splits into P = N - L prefix steps and L suffix steps, b^L <= 4096. A work
+ * item is 256 prefixes, one per thread; a thread walks its prefix once, then
+ * visits its b^L suffixes in order as a depth-first walk (an odometer over
+ * the suffix digits) that keeps the state of every level, so consecutive
+ * suffixes share their common first steps and a path costs about
+ * b/(b-1) state steps. Weights and the sum are FP64; the block's sum goes to
+ * one partial per work item, in a fixed order. This header has no includes:
+ * it is also the source that the run-time compiler sees. */
 #ifndef BTREE_PAYOFF_CUH
 #define BTREE_PAYOFF_CUH
 
@@ -41,9 +44,11 @@ namespace btp {
 #define BTP_PARAMS 8
 
 struct job {
-    int N, L, P, pad;
-    long long item_begin, n_items;  /* items of this option: ceil(2^P / 256) */
-    const double *steps;            /* device: (u_t, d_t, p_t) for t = 1..N */
+    int N, L, P, b;                 /* steps, suffix and prefix steps, branches */
+    long long item_begin, n_items;  /* items of this option: ceil(b^P / 256) */
+    long long n_prefixes, n_leaves; /* b^P, b^L */
+    const double *moves;            /* device: step t at 2b (t-1): factor of digit 0..b-1,
+                                       then the probability of digit 0..b-1 */
     double S0;
     double param[BTP_PARAMS];
 };
@@ -83,35 +88,43 @@ __device__ void run(const args &a) {
         const long long item = s_item - J.item_begin;
         const long long q = item * BTP_THREADS + threadIdx.x;  /* this thread's prefix */
         double acc = 0.0;
-        if (q < (1ll << J.P)) {
-            /* prefix walk: steps 1..P, the most significant bit first */
+        if (q < J.n_prefixes) {
+            const int b = J.b;
+            /* prefix walk: steps 1..P, the most significant digit first */
             double S = J.S0, w = 1.0;
             state st = Payoff::start(J.S0, J.param);
-            for (int t = 1; t <= J.P; ++t) {
-                const bool up = (q >> (J.P - t)) & 1;
-                const double *f = J.steps + 3 * (t - 1);
-                S *= up ? f[0] : f[1];
-                w *= up ? f[2] : 1.0 - f[2];
-                st = Payoff::step(st, S, t, up, J.param);
+            long long place = J.n_prefixes / b;
+            for (int t = 1; t <= J.P; ++t, place /= b) {
+                const int x = (int)((q / place) % b);
+                const double *mv = J.moves + 2 * b * (t - 1);
+                S *= mv[x];
+                w *= mv[b + x];
+                st = Payoff::step(st, S, t, x, J.param);
             }
             /* suffix leaves in order; level d holds the state after d suffix steps */
             state ss[BTP_MAX_L + 1];
             double sS[BTP_MAX_L + 1], sw[BTP_MAX_L + 1];
+            int dig[BTP_MAX_L];
             ss[0] = st;
             sS[0] = S;
             sw[0] = w;
             const int L = J.L;
-            const long long n_leaves = 1ll << L;
-            for (long long s = 0; s < n_leaves; ++s) {
-                /* the first suffix step that differs from the previous leaf */
-                const int d0 = s == 0 ? 0 : L - 1 - __ffsll(s) + 1;
+            for (int d = 0; d < L; ++d) dig[d] = 0;
+            for (long long s = 0; s < J.n_leaves; ++s) {
+                /* advance the odometer; d0 is the first suffix step that changed */
+                int d0 = 0;
+                if (s > 0) {
+                    d0 = L - 1;
+                    while (dig[d0] == b - 1) dig[d0--] = 0;
+                    ++dig[d0];
+                }
                 for (int d = d0; d < L; ++d) {
-                    const bool up = (s >> (L - 1 - d)) & 1;
+                    const int x = dig[d];
                     const int t = J.P + d + 1;
-                    const double *f = J.steps + 3 * (t - 1);
-                    sS[d + 1] = sS[d] * (up ? f[0] : f[1]);
-                    sw[d + 1] = sw[d] * (up ? f[2] : 1.0 - f[2]);
-                    ss[d + 1] = Payoff::step(ss[d], sS[d + 1], t, up, J.param);
+                    const double *mv = J.moves + 2 * b * (t - 1);
+                    sS[d + 1] = sS[d] * mv[x];
+                    sw[d + 1] = sw[d] * mv[b + x];
+                    ss[d + 1] = Payoff::step(ss[d], sS[d + 1], t, x, J.param);
                 }
                 acc = fma(sw[L], Payoff::value(ss[L], J.N, J.param), acc);
             }

@@ -117,6 +117,7 @@ def lib():
         _proto(L, "bt_price_exact_plugin", [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp])
         L.bt_plugin_destroy.argtypes = [_vp]
         L.bt_plugin_destroy.restype = None
+        _proto(L, "bt_price_exact_branching", [_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp])
         _proto(L, "bt_price_mc_shard", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _i32, _i32, _vp, _vp, _vp])
         _proto(L, "bt_philox4x32_10", [_vp, _vp, _vp, _vp, _i32])
         _proto(L, "bt_greeks_exact", [_vp, _vp, _i32, C.c_int, _vp, _vp, _vp])
@@ -315,6 +316,28 @@ def bt_price_exact_plugin(ctx, plugin, opts, steps=None, params=None, stream=Non
     out = np.zeros(len(a), dtype=RESULT_DTYPE)
     _check(lib().bt_price_exact_plugin(ctx, plugin, a.ctypes.data, len(a), None if st is None else st.ctypes.data,
                                        None if pr is None else pr.ctypes.data, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def bt_price_exact_branching(ctx, opts, branches, moves, plugin=None, params=None, stream=None) -> np.ndarray:
+    """Trees with `branches` branches per node: moves per option [N][2b]
+    (factors of digits 0..b-1, then their probabilities), a list of those or
+    one concatenated array."""
+    a = options_array(opts)
+    if isinstance(moves, (list, tuple)):
+        moves = np.concatenate([np.asarray(m, dtype=np.float64).reshape(-1, 2 * branches) for m in moves])
+    mv = np.ascontiguousarray(np.asarray(moves, dtype=np.float64).reshape(-1, 2 * branches))
+    if mv.shape[0] != int(a["N"].sum()):
+        raise ValueError("moves holds %d steps, the options need %d" % (mv.shape[0], int(a["N"].sum())))
+    pr = None
+    if params is not None:
+        pr = np.zeros((len(a), 8))
+        p_in = np.asarray(params, dtype=np.float64).reshape(len(a), -1)
+        pr[:, :p_in.shape[1]] = p_in
+    out = np.zeros(len(a), dtype=RESULT_DTYPE)
+    _check(lib().bt_price_exact_branching(ctx, plugin, a.ctypes.data, len(a), branches, mv.ctypes.data,
+                                          None if pr is None else pr.ctypes.data, out.ctypes.data,
+                                          _stream(stream)))
     return out
 
 

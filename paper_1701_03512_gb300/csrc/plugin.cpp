@@ -138,91 +138,89 @@ extern "C" void bt_plugin_destroy(bt_payoff_plugin *pl) {
     delete pl;
 }
 
-extern "C" bt_status bt_price_exact_plugin(bt_ctx *ctx, const bt_payoff_plugin *pl, const bt_option *opts, int32_t n,
-                                           const double *steps, const double *params, bt_result *out,
-                                           void *stream) {
-    if (!ctx || !pl || !opts || !out || n < 1) return bt_fail(BT_EINVAL, "bt_price_exact_plugin: bad arguments");
-    if (pl->device != ctx->device) return bt_fail(BT_EINVAL, "bt_price_exact_plugin: plug-in built for another GPU");
-    // per-step factors: the caller's, else each option's recombining tree
-    int64_t nsteps = 0;
-    for (int i = 0; i < n; ++i) {
-        if (opts[i].N < 1 || opts[i].N > BT_MAX_N_EXACT)
-            return bt_fail(opts[i].N > BT_MAX_N_EXACT ? BT_EUNSUPPORTED : BT_EINVAL, "option %d: N=%d outside 1..%d",
-                           i, opts[i].N, BT_MAX_N_EXACT);
-        nsteps += opts[i].N;
-    }
-    std::vector<double> st((size_t)(3 * nsteps));
+extern "C" int bt_branch_builtin_grid(int device);
+extern "C" int bt_launch_branch_builtin(const btp::args *a, int grid, void *stream);
+
+// Runs the generic pass over opts[0..n) on a b-ary tree whose moves are given
+// per step as b factors then b probabilities (host array `moves`, options
+// concatenated), with the plug-in kernel or, if pl is NULL, the built-in
+// payoffs. Per-item partials are added on the host in item order.
+static bt_status generic_run(bt_ctx *ctx, const bt_payoff_plugin *pl, const bt_option *opts, int n, int b,
+                             const std::vector<double> &moves, const double *params, bt_result *out, void *stream) {
     std::vector<btp::job> jobs((size_t)n);
-    std::vector<int64_t> step_off((size_t)n);
+    std::vector<int64_t> move_off((size_t)n);
     int64_t o = 0, items = 0;
     for (int i = 0; i < n; ++i) {
         const bt_option &op = opts[i];
-        if (!(op.S0 > 0.0 && std::isfinite(op.S0) && op.T > 0.0 && std::isfinite(op.rate)))
-            return bt_fail(BT_EINVAL, "option %d: needs S0 > 0, T > 0 and a finite rate", i);
-        if (steps) {
-            for (int t = 0; t < op.N; ++t) {
-                const double u = steps[3 * (o + t)], d = steps[3 * (o + t) + 1], p = steps[3 * (o + t) + 2];
-                if (!(std::isfinite(u) && d > 0.0 && u > d && p > 0.0 && p < 1.0))
-                    return bt_fail(BT_EINVAL, "option %d step %d: needs 0 < d < u and 0 < p < 1", i, t + 1);
-            }
-            memcpy(&st[3 * o], steps + 3 * o, sizeof(double) * 3 * op.N);
-        } else {
-            bt_status s = validate_option(&op, i, BT_MAX_N_EXACT);
-            if (s != BT_OK) return s;
-            double u, d, p;
-            host_tree(&op, &u, &d, &p);
-            for (int t = 0; t < op.N; ++t) {
-                st[3 * (o + t)] = u;
-                st[3 * (o + t) + 1] = d;
-                st[3 * (o + t) + 2] = p;
-            }
-        }
         btp::job &J = jobs[i];
         memset(&J, 0, sizeof(J));
         J.N = op.N;
-        J.L = std::min(op.N, BTP_MAX_L);
-        J.P = op.N - J.L;
+        J.b = b;
+        int L = 0;
+        long long leaves = 1;
+        while (L < op.N && leaves * b <= 4096) {
+            leaves *= b;
+            ++L;
+        }
+        J.L = L;
+        J.P = op.N - L;
+        J.n_leaves = leaves;
+        long long pre = 1;
+        for (int t = 0; t < J.P; ++t) pre *= b;
+        J.n_prefixes = pre;
         J.item_begin = items;
-        J.n_items = std::max<int64_t>(1, ((1ll << J.P) + BTP_THREADS - 1) / BTP_THREADS);
+        J.n_items = std::max<long long>(1, (pre + BTP_THREADS - 1) / BTP_THREADS);
         J.S0 = op.S0;
-        if (params) memcpy(J.param, params + BTP_PARAMS * i, sizeof(J.param));
-        else J.param[0] = op.K;
+        if (pl) {
+            if (params) memcpy(J.param, params + BTP_PARAMS * i, sizeof(J.param));
+            else J.param[0] = op.K;
+        } else {
+            J.param[0] = op.K;
+            J.param[1] = (double)op.payoff;
+        }
         items += J.n_items;
-        step_off[i] = 3 * o;  // J.steps is set once the device copy exists
+        move_off[i] = 2 * b * o;  // J.moves is set once the device copy exists
         o += op.N;
     }
+    if (items > ((int64_t)1 << 31)) return bt_fail(BT_EUNSUPPORTED, "%lld work items", (long long)items);
     size_t off = 0;
     const size_t o_jobs = off; off = up256(off + sizeof(btp::job) * n);
-    const size_t o_st = off; off = up256(off + sizeof(double) * st.size());
+    const size_t o_mv = off; off = up256(off + sizeof(double) * moves.size());
     const size_t o_part = off; off = up256(off + sizeof(double) * items);
     const size_t o_cnt = off; off = up256(off + sizeof(unsigned long long));
     cudaSetDevice(ctx->device);
     void *arena = nullptr;
     bt_status rs = ctx_alloc(ctx, off, &arena);
     if (rs != BT_OK) return rs;
-    char *b = (char *)arena;
-    const double *d_st = (const double *)(b + o_st);
-    for (int i = 0; i < n; ++i) jobs[i].steps = d_st + step_off[i];
+    char *base = (char *)arena;
+    const double *d_mv = (const double *)(base + o_mv);
+    for (int i = 0; i < n; ++i) jobs[i].moves = d_mv + move_off[i];
     cudaStream_t sm = ctx_stream(ctx, stream);
     std::vector<double> part((size_t)items);
-    cudaError_t e = cudaMemcpyAsync(b + o_jobs, jobs.data(), sizeof(btp::job) * n, cudaMemcpyHostToDevice, sm);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_st, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, sm);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b + o_cnt, 0, sizeof(unsigned long long), sm);
+    cudaError_t e = cudaMemcpyAsync(base + o_jobs, jobs.data(), sizeof(btp::job) * n, cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_mv, moves.data(), sizeof(double) * moves.size(), cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_cnt, 0, sizeof(unsigned long long), sm);
     if (e == cudaSuccess) {
         btp::args a;
         memset(&a, 0, sizeof(a));
-        a.jobs = (const btp::job *)(b + o_jobs);
+        a.jobs = (const btp::job *)(base + o_jobs);
         a.n_jobs = n;
         a.n_items = items;
-        a.partials = (double *)(b + o_part);
-        a.counter = (unsigned long long *)(b + o_cnt);
-        void *kargs[] = {&a};
-        const int grid = (int)std::min<int64_t>(pl->grid, items);
-        e = cudaLaunchKernel((const void *)pl->kern, dim3(grid), dim3(BTP_THREADS), kargs, 0, sm);
+        a.partials = (double *)(base + o_part);
+        a.counter = (unsigned long long *)(base + o_cnt);
+        if (pl) {
+            void *kargs[] = {&a};
+            const int grid = (int)std::min<int64_t>(pl->grid, items);
+            e = cudaLaunchKernel((const void *)pl->kern, dim3(grid), dim3(BTP_THREADS), kargs, 0, sm);
+        } else {
+            const int grid = (int)std::min<int64_t>(bt_branch_builtin_grid(ctx->device), items);
+            e = (cudaError_t)bt_launch_branch_builtin(&a, grid, sm);
+        }
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(part.data(), b + o_part, sizeof(double) * items, cudaMemcpyDeviceToHost, sm);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(part.data(), base + o_part, sizeof(double) * items, cudaMemcpyDeviceToHost, sm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
-    if (e != cudaSuccess) rs = bt_cuda_fail(e, "bt_price_exact_plugin");
+    if (e != cudaSuccess) rs = bt_cuda_fail(e, "generic path pass");
     cudaStreamSynchronize(sm);
     ctx_free(ctx, arena, off);
     if (rs != BT_OK) return rs;
@@ -235,12 +233,91 @@ extern "C" bt_status bt_price_exact_plugin(bt_ctx *ctx, const bt_payoff_plugin *
             c += std::fabs(s) >= std::fabs(x) ? (s - t) + x : (x - t) + s;
             s = t;
         }
+        long long paths = 1;
+        for (int t = 0; t < J.N; ++t) paths *= b;
         bt_result &r = out[i];
         r.value = std::exp(-opts[i].rate * opts[i].T) * (s + c);
         r.err_est = 1e-13 * std::fabs(r.value);
         r.stderr_mc = 0.0;
         r.var_plain = 0.0;
-        r.paths = 1ll << J.N;
+        r.paths = paths;
     }
     return BT_OK;
+}
+
+static bt_status check_scalars(const bt_option &op, int i) {
+    if (!(op.S0 > 0.0 && std::isfinite(op.S0) && op.T > 0.0 && std::isfinite(op.T) && std::isfinite(op.rate) &&
+          op.K >= 0.0 && std::isfinite(op.K)))
+        return bt_fail(BT_EINVAL, "option %d: needs S0 > 0, K >= 0, T > 0 and a finite rate", i);
+    if (op.payoff < 0 || op.payoff > 7) return bt_fail(BT_EINVAL, "option %d: bad payoff %d", i, op.payoff);
+    return BT_OK;
+}
+
+extern "C" bt_status bt_price_exact_plugin(bt_ctx *ctx, const bt_payoff_plugin *pl, const bt_option *opts, int32_t n,
+                                           const double *steps, const double *params, bt_result *out,
+                                           void *stream) {
+    if (!ctx || !pl || !opts || !out || n < 1) return bt_fail(BT_EINVAL, "bt_price_exact_plugin: bad arguments");
+    if (pl->device != ctx->device) return bt_fail(BT_EINVAL, "bt_price_exact_plugin: plug-in built for another GPU");
+    // binomial moves in digit order: (d, u) and (1 - p, p); the caller's steps, else each option's tree
+    std::vector<double> mv;
+    int64_t o = 0;
+    for (int i = 0; i < n; ++i) {
+        const bt_option &op = opts[i];
+        if (op.N < 1 || op.N > BT_MAX_N_EXACT)
+            return bt_fail(op.N > BT_MAX_N_EXACT ? BT_EUNSUPPORTED : BT_EINVAL, "option %d: N=%d outside 1..%d", i,
+                           op.N, BT_MAX_N_EXACT);
+        bt_status s = check_scalars(op, i);
+        if (s != BT_OK) return s;
+        double u = 0, d = 0, p = 0;
+        if (!steps) {
+            if ((s = validate_option(&op, i, BT_MAX_N_EXACT)) != BT_OK) return s;
+            host_tree(&op, &u, &d, &p);
+        }
+        for (int t = 0; t < op.N; ++t) {
+            if (steps) {
+                u = steps[3 * (o + t)];
+                d = steps[3 * (o + t) + 1];
+                p = steps[3 * (o + t) + 2];
+                if (!(std::isfinite(u) && d > 0.0 && u > d && p > 0.0 && p < 1.0))
+                    return bt_fail(BT_EINVAL, "option %d step %d: needs 0 < d < u and 0 < p < 1", i, t + 1);
+            }
+            mv.insert(mv.end(), {d, u, 1.0 - p, p});
+        }
+        o += op.N;
+    }
+    return generic_run(ctx, pl, opts, n, 2, mv, params, out, stream);
+}
+
+extern "C" bt_status bt_price_exact_branching(bt_ctx *ctx, const bt_payoff_plugin *pl, const bt_option *opts,
+                                              int32_t n, int32_t branches, const double *moves,
+                                              const double *params, bt_result *out, void *stream) {
+    if (!ctx || !opts || !moves || !out || n < 1) return bt_fail(BT_EINVAL, "bt_price_exact_branching: bad arguments");
+    if (branches < 2 || branches > 8) return bt_fail(BT_EINVAL, "branches = %d outside 2..8", branches);
+    if (pl && pl->device != ctx->device) return bt_fail(BT_EINVAL, "plug-in built for another GPU");
+    const int b = branches;
+    int64_t total_steps = 0;
+    for (int i = 0; i < n; ++i) {
+        const bt_option &op = opts[i];
+        bt_status s = check_scalars(op, i);
+        if (s != BT_OK) return s;
+        // b^N paths, at most 2^48
+        double lg = (double)op.N * std::log2((double)b);
+        if (op.N < 1 || lg > 48.0)
+            return bt_fail(op.N < 1 ? BT_EINVAL : BT_EUNSUPPORTED, "option %d: %d^%d paths outside 1..2^48", i, b, op.N);
+        for (int t = 0; t < op.N; ++t) {
+            const double *mv = moves + 2 * b * (total_steps + t);
+            double psum = 0.0;
+            for (int k = 0; k < b; ++k) {
+                if (!(std::isfinite(mv[k]) && mv[k] > 0.0 && mv[b + k] >= 0.0 && mv[b + k] <= 1.0))
+                    return bt_fail(BT_EINVAL, "option %d step %d: factors must be > 0, probabilities in [0,1]", i,
+                                   t + 1);
+                psum += mv[b + k];
+            }
+            if (std::fabs(psum - 1.0) > 1e-12)
+                return bt_fail(BT_EINVAL, "option %d step %d: probabilities sum to %.17g", i, t + 1, psum);
+        }
+        total_steps += op.N;
+    }
+    std::vector<double> mv(moves, moves + 2 * b * total_steps);
+    return generic_run(ctx, pl, opts, n, b, mv, params, out, stream);
 }

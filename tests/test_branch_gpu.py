@@ -1,0 +1,101 @@
+"""Trees with b branches per node (the end of Section 3) on the GPU: the
+generic pass with the built-in payoffs against the oracle's b-ary
+enumeration, a recombining trinomial lattice against backward induction,
+b = 2 against the built-in binomial pass, and a plug-in on a trinomial tree
+against numpy brute force."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1701_03512_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bt():
+    from paper_1701_03512_gb300 import build as b
+    b.build()
+    from paper_1701_03512_gb300 import btree
+    return btree
+
+
+@pytest.fixture(scope="module")
+def ctx(bt):
+    c = bt.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("b,N", [(3, 1), (3, 6), (3, 10), (4, 6), (5, 5)])
+def test_builtin_payoffs_against_the_oracle(bt, ctx, oracle, b, N):
+    opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for pay in range(8) for K in (95.0, 103.0)]
+    moves = [W.branch_moves(7 * N + i + b, N, b) for i in range(len(opts))]
+    got = bt.bt_price_exact_branching(ctx.h, opts, b, moves)
+    for o, m, g in zip(opts, moves, got):
+        ref = oracle.branch_price(o, m, b, 8)
+        assert abs(g["value"] - ref) <= 1e-12 * abs(ref) + 1e-13, (o, g["value"], ref)
+        assert g["paths"] == b ** N
+
+
+def test_recombining_trinomial_european_against_backward_induction(bt, ctx, oracle):
+    N = 15
+    u = math.exp(0.25 * math.sqrt(3 / 15))
+    moves = np.tile([1 / u, 1.0, u, 0.18, 0.64, 0.18], (N, 1))
+    for pay in (W.EURO_CALL, W.EURO_PUT):
+        o = W.opt(N, 100.0, 100.0, 0.0, 0.25, 1.0, pay)
+        got = bt.bt_price_exact_branching(ctx.h, [o], 3, [moves])["value"][0]
+        assert abs(got - oracle.branch_european_backward(o, moves, 3)) <= 1e-12 * got
+
+
+def test_two_branches_match_the_binomial_pass(bt, ctx):
+    N = 22
+    opts = [W.opt(N, 100.0, 101.0, 0.05, 0.3, 1.0, pay) for pay in range(8)]
+    u, d, p = bt.bt_tree_params(opts[0])
+    moves = [np.tile([d, u, 1 - p, p], (N, 1))] * len(opts)
+    got = bt.bt_price_exact_branching(ctx.h, opts, 2, moves)["value"]
+    ref = ctx.price_exact(opts, 0)["value"]
+    assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref) + 1e-13)
+
+
+def test_plugin_on_a_trinomial_tree(bt, ctx):
+    src = r"""
+    struct Payoff {   // up-and-out call, barrier param[1]
+        struct state { double S; int out; };
+        __device__ static state start(double S0, const double *) { return {S0, 0}; }
+        __device__ static state step(const state &s, double S, int, int, const double *p) {
+            return {S, s.out || S >= p[1]};
+        }
+        __device__ static double value(const state &s, int, const double *p) {
+            return s.out ? 0.0 : fmax(s.S - p[0], 0.0);
+        }
+    };"""
+    h, _ = bt.bt_plugin_compile(ctx.h, src)
+    try:
+        N, b = 9, 3
+        moves = W.branch_moves(3, N, b)
+        o = W.opt(N, 100.0, 97.0, 0.02, 0.2, 1.0, W.EURO_CALL)
+        got = bt.bt_price_exact_branching(ctx.h, [o], b, [moves], plugin=h, params=[[97.0, 115.0]])["value"][0]
+        idx = np.arange(b ** N)
+        x = (idx[:, None] // (b ** (N - 1 - np.arange(N)))[None, :]) % b
+        S = 100.0 * np.cumprod(moves[:, :b][np.arange(N)[None, :], x], axis=1)
+        w = np.prod(moves[:, b:][np.arange(N)[None, :], x], axis=1)
+        v = np.where(S.max(axis=1) >= 115.0, 0.0, np.maximum(S[:, -1] - 97.0, 0.0))
+        ref = math.exp(-0.02) * math.fsum(w * v)
+        assert abs(got - ref) <= 1e-12 * ref
+    finally:
+        bt.bt_plugin_destroy(h)
+
+
+def test_invalid_moves(bt, ctx):
+    o = W.opt(4, 100.0, 100.0, 0.0, 0.2, 1.0, W.EURO_CALL)
+    mv = W.branch_moves(1, 4, 3)
+    bad = mv.copy()
+    bad[2, 4] += 0.01     # probabilities no longer sum to 1
+    with pytest.raises(bt.BtError) as e:
+        bt.bt_price_exact_branching(ctx.h, [o], 3, [bad])
+    assert e.value.status == bt.BT_EINVAL
+    with pytest.raises(bt.BtError) as e:
+        bt.bt_price_exact_branching(ctx.h, [dict(o, N=31)], 3, [W.branch_moves(1, 31, 3)])
+    assert e.value.status == bt.BT_EUNSUPPORTED
