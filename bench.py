@@ -33,7 +33,9 @@ Two further measurements ride on the same line (rank 0, N=1 only):
             2^16 strata x 2^14 Philox samples: samples/s and steps/s against
             the integer/FP32 issue peak;
   greeks  -- the derivative pass over 512 N=28 options (value and four
-            Greeks each), host arrays in and out.
+            Greeks each), host arrays in and out;
+  widened -- time-varying trees (FP32, N=32) and the generic FP64 path walk
+            on binomial (N=28) and trinomial (N=17) trees.
 
 Multi-GPU (torchrun): every rank prices its own copy of the batch (weak
 scaling, independent problems, no collective on the data path); the value is
@@ -80,6 +82,7 @@ def parse():
     ap.add_argument("--serving-loads", default="0.5,0.8,0.95")
     ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--no-greeks", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     return ap.parse_args()
 
 
@@ -335,6 +338,54 @@ def greeks_bench(bt, W, ctx, reps=3):
 
 
 # ---------------------------------------------------------------------------
+# Widened paths: time-varying trees, the generic pass (plug-ins, b-ary trees)
+# ---------------------------------------------------------------------------
+def _timed(fn, reps=3):
+    fn()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        ts.append(time.perf_counter() - t0)
+    return statistics.median(ts)
+
+
+def extras_bench(bt, W, ctx, sms, fmax):
+    import numpy as np
+    peak = sms * 128 * fmax * 1e6
+    out = {}
+    # time-varying trees, FP32: 16 options at N=32 (arithmetic call/put, lookback call, geometric call)
+    N = 32
+    opts = [W.opt(N, 100.0, 90.0 + 5 * (i % 4), 0.03, 0.2, 1.0, pay)
+            for i, pay in enumerate([W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT, W.LOOKBACK_FIXED_CALL,
+                                     W.ASIAN_GEO_CALL] * 4)]
+    steps = [W.step_factors(900 + i, N, 0.01, 0.05) for i in range(len(opts))]
+    t = _timed(lambda: bt.bt_price_exact_steps(ctx.h, opts, steps, bt.BT_PREC_FP32_COMP))
+    paths = len(opts) * 2.0 ** N
+    out["steps"] = {"workload": "time-varying trees (per-step u_t, d_t, p_t), 16 options x 2^32 paths, FP32_COMP, "
+                                "host arrays in and out",
+                    "ms": 1e3 * t, "payoff_paths_per_s": paths / t, "ops_per_payoff_path": 3,
+                    "frac_of_issue_peak": 3 * paths / t / peak}
+    # generic pass, built-in payoffs, binomial and trinomial
+    N2 = 28
+    o2 = [W.opt(N2, 100.0, 100.0, 0.05, 0.2, 1.0, pay) for pay in (W.ASIAN_ARITH_CALL, W.LOOKBACK_FIXED_CALL)]
+    u, d, p = bt.bt_tree_params(o2[0])
+    mv2 = [np.tile([d, u, 1 - p, p], (N2, 1))] * 2
+    t = _timed(lambda: bt.bt_price_exact_branching(ctx.h, o2, 2, mv2))
+    out["generic_binomial"] = {"workload": "generic pass (FP64 path walk), arithmetic Asian and lookback calls, "
+                                           "N=28, 2 x 2^28 paths", "ms": 1e3 * t,
+                               "payoff_paths_per_s": 2 * 2.0 ** N2 / t}
+    N3 = 17
+    o3 = [W.opt(N3, 100.0, 100.0, 0.05, 0.2, 1.0, pay) for pay in (W.ASIAN_ARITH_CALL, W.LOOKBACK_FIXED_CALL)]
+    mv3 = [W.branch_moves(3, N3, 3), W.branch_moves(4, N3, 3)]
+    t = _timed(lambda: bt.bt_price_exact_branching(ctx.h, o3, 3, mv3))
+    out["generic_trinomial"] = {"workload": "generic pass, trinomial trees, arithmetic Asian and lookback calls, "
+                                            "N=17, 2 x 3^17 paths", "ms": 1e3 * t,
+                                "payoff_paths_per_s": 2 * 3.0 ** N3 / t}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
 def run_reference(args, rank):
@@ -479,11 +530,13 @@ def main():
         v, sample = cpu_oracle_sample(opts, args.cpu_seconds, threads)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
 
-    serving = mc = greeks = None
+    serving = mc = greeks = extras = None
     if world == 1 and not args.no_mc:
         mc = mc_bench(bt, W, ctx, sms, fmax)
     if world == 1 and not args.no_greeks:
         greeks = greeks_bench(bt, W, ctx)
+    if world == 1 and not args.no_extras:
+        extras = extras_bench(bt, W, ctx, sms, fmax)
     if world == 1 and not args.no_serving:
         loads = [float(x) for x in args.serving_loads.split(",") if x]
         sctx = bt.Context(local_rank, device_budget_bytes=12 << 30)   # 8 GiB server pool + plain scratch
@@ -498,7 +551,7 @@ def main():
             "fp32_peak_frac": roof["frac"], "clocks": clocks, "e2e": e2e,
             # per step: k_params, k_tables, k_class_tables, k_exact32, k_finalize
             "gpu_launches": 5 * args.steps, "roofline": roof, "cpu_baseline": cpu,
-            "serving": serving, "mc": mc, "greeks": greeks}
+            "serving": serving, "mc": mc, "greeks": greeks, "widened": extras}
     print(json.dumps(line), flush=True)
     bt.bt_exact_plan_destroy(plan)
     ctx.close()
