@@ -476,6 +476,48 @@ __device__ __forceinline__ pref32 prefix32(const bt_job &J, const bt_jparams &P,
     return r;
 }
 
+// Payoffs/lambda of eight suffixes under one prefix: y = lambda (tau_hi + f_hi)
+// exactly, c = -lambda (tau_lo + f_lo), z = sat(+-(y - c)); returns the
+// eight-wide addition tree of the call (MODE & CALL) and put z.
+template <int MODE>
+__device__ __forceinline__ void tree8(const float4 *f4, float B, float Ah, float nAl, float &tc, float &tp) {
+    float y[BT_UNROLL], c[BT_UNROLL];
+#pragma unroll
+    for (int i = 0; i < BT_UNROLL / 2; ++i) {
+        y[2 * i] = __fmaf_rn(B, f4[i].x, Ah);
+        c[2 * i] = __fmaf_rn(B, f4[i].y, nAl);
+        y[2 * i + 1] = __fmaf_rn(B, f4[i].z, Ah);
+        c[2 * i + 1] = __fmaf_rn(B, f4[i].w, nAl);
+    }
+    if (MODE & BT_MODE_CALL) {
+        float z[BT_UNROLL];
+#pragma unroll
+        for (int i = 0; i < BT_UNROLL; ++i) z[i] = __saturatef(__fsub_rn(y[i], c[i]));
+#pragma unroll
+        for (int w = 1; w < BT_UNROLL; w *= 2)
+#pragma unroll
+            for (int i = 0; i < BT_UNROLL; i += 2 * w) z[i] = __fadd_rn(z[i], z[i + w]);
+        tc = z[0];
+    }
+    if (MODE & BT_MODE_PUT) {
+        float z[BT_UNROLL];
+#pragma unroll
+        for (int i = 0; i < BT_UNROLL; ++i) z[i] = __saturatef(__fsub_rn(c[i], y[i]));
+#pragma unroll
+        for (int w = 1; w < BT_UNROLL; w *= 2)
+#pragma unroll
+            for (int i = 0; i < BT_UNROLL; i += 2 * w) z[i] = __fadd_rn(z[i], z[i + w]);
+        tp = z[0];
+    }
+}
+
+// g + t as (sum, compensation): Fast2Sum (|g| >= |t| after the first add).
+__device__ __forceinline__ void fast_acc(float &g, float &e, float t) {
+    const float sN = __fadd_rn(g, t);
+    e = __fadd_rn(e, __fsub_rn(t, __fsub_rn(sN, g)));
+    g = sN;
+}
+
 template <int MODE>
 __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &sj, const float2 *s_suf,
                                        double2 *red) {
@@ -485,9 +527,9 @@ __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &s
     const int64_t qbase = item_local << BT_LOW_BITS;
     const int64_t nP = 1ll << J.P;
 
+    // the loop needs only the scaled affine form; w_low beta / lambda and C
+    // are recomputed at the end (keeps registers for the sixteen-wide trees)
     float B[BT_PT], Ah[BT_PT], nAl[BT_PT];
-    df32 om[BT_PT];
-    df32 cst = df_make(0.0f, 0.0f);
 #pragma unroll
     for (int j = 0; j < BT_PT; ++j) {
         const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
@@ -495,8 +537,6 @@ __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &s
         B[j] = pr.B;
         Ah[j] = pr.Ah;
         nAl[j] = pr.nAl;
-        om[j] = pr.om;
-        cst = df_add_pos(cst, pr.cst);
     }
     df32 accC[BT_PT], accP[BT_PT];
 #pragma unroll
@@ -508,45 +548,36 @@ __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &s
         float gc[BT_PT], ec[BT_PT], gp[BT_PT], ep[BT_PT];
 #pragma unroll
         for (int j = 0; j < BT_PT; ++j) gc[j] = ec[j] = gp[j] = ep[j] = 0.0f;
-        for (int s = s0; s < s1; s += BT_UNROLL) {
+        int s = s0;
+        // sixteen suffixes per step: two eight-wide trees, one add, one Fast2Sum
+        for (; s + 2 * BT_UNROLL <= s1; s += 2 * BT_UNROLL) {
+            float tc[BT_PT], tp[BT_PT];
+            float4 f4[BT_UNROLL / 2];
+#pragma unroll
+            for (int i = 0; i < BT_UNROLL / 2; ++i) f4[i] = *reinterpret_cast<const float4 *>(s_suf + s + 2 * i);
+#pragma unroll
+            for (int j = 0; j < BT_PT; ++j) tree8<MODE>(f4, B[j], Ah[j], nAl[j], tc[j], tp[j]);
+#pragma unroll
+            for (int i = 0; i < BT_UNROLL / 2; ++i)
+                f4[i] = *reinterpret_cast<const float4 *>(s_suf + s + BT_UNROLL + 2 * i);
+#pragma unroll
+            for (int j = 0; j < BT_PT; ++j) {
+                float uc, up;
+                tree8<MODE>(f4, B[j], Ah[j], nAl[j], uc, up);
+                if (MODE & BT_MODE_CALL) fast_acc(gc[j], ec[j], __fadd_rn(tc[j], uc));
+                if (MODE & BT_MODE_PUT) fast_acc(gp[j], ep[j], __fadd_rn(tp[j], up));
+            }
+        }
+        if (s < s1) {  // an odd eight at the end of the group
             float4 f4[BT_UNROLL / 2];
 #pragma unroll
             for (int i = 0; i < BT_UNROLL / 2; ++i) f4[i] = *reinterpret_cast<const float4 *>(s_suf + s + 2 * i);
 #pragma unroll
             for (int j = 0; j < BT_PT; ++j) {
-                // y = lambda (tau_hi + f_hi), c = -lambda (tau_lo + f_lo); payoff/beta = sat(y - c)/lambda
-                float y[BT_UNROLL], c[BT_UNROLL];
-#pragma unroll
-                for (int i = 0; i < BT_UNROLL / 2; ++i) {
-                    y[2 * i] = __fmaf_rn(B[j], f4[i].x, Ah[j]);
-                    c[2 * i] = __fmaf_rn(B[j], f4[i].y, nAl[j]);
-                    y[2 * i + 1] = __fmaf_rn(B[j], f4[i].z, Ah[j]);
-                    c[2 * i + 1] = __fmaf_rn(B[j], f4[i].w, nAl[j]);
-                }
-                if (MODE & BT_MODE_CALL) {
-                    float z[BT_UNROLL];
-#pragma unroll
-                    for (int i = 0; i < BT_UNROLL; ++i) z[i] = __saturatef(__fsub_rn(y[i], c[i]));
-#pragma unroll
-                    for (int w = 1; w < BT_UNROLL; w *= 2)
-#pragma unroll
-                        for (int i = 0; i < BT_UNROLL; i += 2 * w) z[i] = __fadd_rn(z[i], z[i + w]);
-                    const float sN = __fadd_rn(gc[j], z[0]);  // Fast2Sum (|gc| >= |z0| after the first add)
-                    ec[j] = __fadd_rn(ec[j], __fsub_rn(z[0], __fsub_rn(sN, gc[j])));
-                    gc[j] = sN;
-                }
-                if (MODE & BT_MODE_PUT) {
-                    float z[BT_UNROLL];
-#pragma unroll
-                    for (int i = 0; i < BT_UNROLL; ++i) z[i] = __saturatef(__fsub_rn(c[i], y[i]));
-#pragma unroll
-                    for (int w = 1; w < BT_UNROLL; w *= 2)
-#pragma unroll
-                        for (int i = 0; i < BT_UNROLL; i += 2 * w) z[i] = __fadd_rn(z[i], z[i + w]);
-                    const float sN = __fadd_rn(gp[j], z[0]);
-                    ep[j] = __fadd_rn(ep[j], __fsub_rn(z[0], __fsub_rn(sN, gp[j])));
-                    gp[j] = sN;
-                }
+                float uc, up;
+                tree8<MODE>(f4, B[j], Ah[j], nAl[j], uc, up);
+                if (MODE & BT_MODE_CALL) fast_acc(gc[j], ec[j], uc);
+                if (MODE & BT_MODE_PUT) fast_acc(gp[j], ep[j], up);
             }
         }
         const df32 w = df_from2(P.W2[k]);
@@ -557,18 +588,22 @@ __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &s
         }
     }
     df32 totC = df_make(0.0f, 0.0f), totP = df_make(0.0f, 0.0f);
+    df32 cst = df_make(0.0f, 0.0f);
 #pragma unroll
     for (int j = 0; j < BT_PT; ++j) {
-        if (MODE & BT_MODE_CALL) totC = df_add_pos(totC, df_mul(om[j], accC[j]));
-        if (MODE & BT_MODE_PUT) totP = df_add_pos(totP, df_mul(om[j], accP[j]));
+        const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
+        const pref32 pr = prefix32(J, P, a, q, q < nP);
+        cst = df_add_pos(cst, pr.cst);
+        if (MODE & BT_MODE_CALL) totC = df_add_pos(totC, df_mul(pr.om, accC[j]));
+        if (MODE & BT_MODE_PUT) totP = df_add_pos(totP, df_mul(pr.om, accP[j]));
     }
     double vc = df_to_double(totC), vp = df_to_double(totP);
     if (J.field == BT_F_LOOKMAX) vc += df_to_double(cst);
     if (J.field == BT_F_LOOKMIN) vp += df_to_double(cst);
-    double2 s = block_sum2(vc, vp, red);
+    double2 sum2 = block_sum2(vc, vp, red);
     if (threadIdx.x == 0) {
         const double wh = P.wh[__popcll((unsigned long long)item_local)];
-        a.partials[J.part_off + item_local] = make_double2(s.x * wh, s.y * wh);
+        a.partials[J.part_off + item_local] = make_double2(sum2.x * wh, sum2.y * wh);
     }
 }
 
