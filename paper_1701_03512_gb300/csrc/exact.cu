@@ -549,26 +549,32 @@ __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &s
 #pragma unroll
         for (int j = 0; j < BT_PT; ++j) gc[j] = ec[j] = gp[j] = ep[j] = 0.0f;
         int s = s0;
-        // sixteen suffixes per step: two eight-wide trees, one add, one Fast2Sum
-        for (; s + 2 * BT_UNROLL <= s1; s += 2 * BT_UNROLL) {
+        // 32 suffixes per step: four eight-wide trees added in turn, one Fast2Sum
+        for (; s + 4 * BT_UNROLL <= s1; s += 4 * BT_UNROLL) {
             float tc[BT_PT], tp[BT_PT];
-            float4 f4[BT_UNROLL / 2];
 #pragma unroll
-            for (int i = 0; i < BT_UNROLL / 2; ++i) f4[i] = *reinterpret_cast<const float4 *>(s_suf + s + 2 * i);
+            for (int j = 0; j < BT_PT; ++j) tc[j] = tp[j] = 0.0f;
+#pragma unroll 2
+            for (int r = 0; r < 4; ++r) {
+                float4 f4[BT_UNROLL / 2];
 #pragma unroll
-            for (int j = 0; j < BT_PT; ++j) tree8<MODE>(f4, B[j], Ah[j], nAl[j], tc[j], tp[j]);
+                for (int i = 0; i < BT_UNROLL / 2; ++i)
+                    f4[i] = *reinterpret_cast<const float4 *>(s_suf + s + r * BT_UNROLL + 2 * i);
 #pragma unroll
-            for (int i = 0; i < BT_UNROLL / 2; ++i)
-                f4[i] = *reinterpret_cast<const float4 *>(s_suf + s + BT_UNROLL + 2 * i);
+                for (int j = 0; j < BT_PT; ++j) {
+                    float uc, up;
+                    tree8<MODE>(f4, B[j], Ah[j], nAl[j], uc, up);
+                    if (MODE & BT_MODE_CALL) tc[j] = __fadd_rn(tc[j], uc);
+                    if (MODE & BT_MODE_PUT) tp[j] = __fadd_rn(tp[j], up);
+                }
+            }
 #pragma unroll
             for (int j = 0; j < BT_PT; ++j) {
-                float uc, up;
-                tree8<MODE>(f4, B[j], Ah[j], nAl[j], uc, up);
-                if (MODE & BT_MODE_CALL) fast_acc(gc[j], ec[j], __fadd_rn(tc[j], uc));
-                if (MODE & BT_MODE_PUT) fast_acc(gp[j], ep[j], __fadd_rn(tp[j], up));
+                if (MODE & BT_MODE_CALL) fast_acc(gc[j], ec[j], tc[j]);
+                if (MODE & BT_MODE_PUT) fast_acc(gp[j], ep[j], tp[j]);
             }
         }
-        if (s < s1) {  // an odd eight at the end of the group
+        for (; s < s1; s += BT_UNROLL) {  // the last one to three eights of the group
             float4 f4[BT_UNROLL / 2];
 #pragma unroll
             for (int i = 0; i < BT_UNROLL / 2; ++i) f4[i] = *reinterpret_cast<const float4 *>(s_suf + s + 2 * i);
