@@ -549,13 +549,13 @@ __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &s
 #pragma unroll
         for (int j = 0; j < BT_PT; ++j) gc[j] = ec[j] = gp[j] = ep[j] = 0.0f;
         int s = s0;
-        // 32 suffixes per step: four eight-wide trees added in turn, one Fast2Sum
-        for (; s + 4 * BT_UNROLL <= s1; s += 4 * BT_UNROLL) {
+        // 64 suffixes per step: eight eight-wide trees added in turn, one Fast2Sum
+        for (; s + 8 * BT_UNROLL <= s1; s += 8 * BT_UNROLL) {
             float tc[BT_PT], tp[BT_PT];
 #pragma unroll
             for (int j = 0; j < BT_PT; ++j) tc[j] = tp[j] = 0.0f;
 #pragma unroll 2
-            for (int r = 0; r < 4; ++r) {
+            for (int r = 0; r < 8; ++r) {
                 float4 f4[BT_UNROLL / 2];
 #pragma unroll
                 for (int i = 0; i < BT_UNROLL / 2; ++i)
@@ -574,7 +574,7 @@ __device__ __forceinline__ void item32(const bt_exact_args &a, const smem_job &s
                 if (MODE & BT_MODE_PUT) fast_acc(gp[j], ep[j], tp[j]);
             }
         }
-        for (; s < s1; s += BT_UNROLL) {  // the last one to three eights of the group
+        for (; s < s1; s += BT_UNROLL) {  // the last one to seven eights of the group
             float4 f4[BT_UNROLL / 2];
 #pragma unroll
             for (int i = 0; i < BT_UNROLL / 2; ++i) f4[i] = *reinterpret_cast<const float4 *>(s_suf + s + 2 * i);
