@@ -230,6 +230,36 @@ __device__ __forceinline__ sstate steps_state(const bt_job &J, const bt_jparams 
 // One work item, FP32: per path y = lambda f_hi + A_hi, c = lambda (-f_lo) - A_lo,
 // z = sat(+-(y - c)), weighted z w_hi + z w_lo, eight-wide tree, TwoSum into
 // the prefix's running sum; prefixes combined in pairs, the block in FP64.
+// Weighted payoffs/lambda of eight suffixes under one prefix, summed by an
+// eight-wide tree: y = lambda f_hi + A_hi, c = lambda (-f_lo) - A_lo,
+// z = sat(+-(y - c)), v = w_hi z + w_lo z.
+template <int MODE>
+__device__ __forceinline__ float wtree8(const float4 *f4, float B, float Ah, float nAl) {
+    float v[BT_UNROLL];
+#pragma unroll
+    for (int i = 0; i < BT_UNROLL; ++i) {
+        const float y = __fmaf_rn(B, f4[i].x, Ah);
+        const float c = __fmaf_rn(B, f4[i].y, nAl);
+        const float z = (MODE & BT_MODE_CALL) ? __saturatef(__fsub_rn(y, c)) : __saturatef(__fsub_rn(c, y));
+        v[i] = __fmaf_rn(f4[i].z, z, __fmul_rn(f4[i].w, z));
+    }
+#pragma unroll
+    for (int w = 1; w < BT_UNROLL; w *= 2)
+#pragma unroll
+        for (int i = 0; i < BT_UNROLL; i += 2 * w) v[i] = __fadd_rn(v[i], v[i + w]);
+    return v[0];
+}
+
+// g + t as (sum, compensation): Fast2Sum (|g| >= |t| after the first add).
+__device__ __forceinline__ void fast_acc_s(float &g, float &e, float t) {
+    const float sN = __fadd_rn(g, t);
+    e = __fadd_rn(e, __fsub_rn(t, __fsub_rn(sN, g)));
+    g = sN;
+}
+
+// One work item, FP32: eight-wide trees of weighted payoffs, eight trees
+// added in turn per Fast2Sum into the prefix's running sum; prefixes combined
+// in pairs (w beta / lambda and C recomputed after the loop), the block in FP64.
 template <int MODE>
 __device__ __forceinline__ void item_steps32(const bt_exact_args &a, const smem_job &sj, const float4 *s_suf,
                                              const bt_spentry *tab, double2 *red) {
@@ -239,54 +269,55 @@ __device__ __forceinline__ void item_steps32(const bt_exact_args &a, const smem_
     const int64_t qbase = item_local << BT_LOW_BITS;
     const int64_t nP = 1ll << J.P;
     float B[BT_PT], Ah[BT_PT], nAl[BT_PT];
-    df32 om[BT_PT];
-    df32 cst = df_make(0.0f, 0.0f);
 #pragma unroll
     for (int j = 0; j < BT_PT; ++j) {
         const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
         if (q < nP) {
-            const sstate s = steps_state(J, P, tab, q);
-            const scale32 sc = scale_prefix(s.tau, P, q);
+            const scale32 sc = scale_prefix(steps_state(J, P, tab, q).tau, P, q);
             B[j] = sc.B;
             Ah[j] = sc.Ah;
             nAl[j] = sc.nAl;
-            om[j] = df_mul(df_mul(s.w, s.beta), sc.rinv);
-            cst = df_add_pos(cst, df_mul(s.w, s.cst));
         } else {
             B[j] = 0.0f;
             Ah[j] = nAl[j] = __int_as_float(0x7fc00000);  // sat(NaN) = 0
-            om[j] = df_make(0.0f, 0.0f);
         }
     }
     float g[BT_PT], e[BT_PT];
 #pragma unroll
     for (int j = 0; j < BT_PT; ++j) g[j] = e[j] = 0.0f;
-    for (int s = 0; s < J.suf_len; s += BT_UNROLL) {
+    int s = 0;
+    for (; s + 8 * BT_UNROLL <= J.suf_len; s += 8 * BT_UNROLL) {
+        float t[BT_PT];
+#pragma unroll
+        for (int j = 0; j < BT_PT; ++j) t[j] = 0.0f;
+#pragma unroll 2
+        for (int r = 0; r < 8; ++r) {
+            float4 f4[BT_UNROLL];
+#pragma unroll
+            for (int i = 0; i < BT_UNROLL; ++i) f4[i] = s_suf[s + r * BT_UNROLL + i];
+#pragma unroll
+            for (int j = 0; j < BT_PT; ++j) t[j] = __fadd_rn(t[j], wtree8<MODE>(f4, B[j], Ah[j], nAl[j]));
+        }
+#pragma unroll
+        for (int j = 0; j < BT_PT; ++j) fast_acc_s(g[j], e[j], t[j]);
+    }
+    for (; s < J.suf_len; s += BT_UNROLL) {
         float4 f4[BT_UNROLL];
 #pragma unroll
         for (int i = 0; i < BT_UNROLL; ++i) f4[i] = s_suf[s + i];
 #pragma unroll
-        for (int j = 0; j < BT_PT; ++j) {
-            float v[BT_UNROLL];
-#pragma unroll
-            for (int i = 0; i < BT_UNROLL; ++i) {
-                const float y = __fmaf_rn(B[j], f4[i].x, Ah[j]);
-                const float c = __fmaf_rn(B[j], f4[i].y, nAl[j]);
-                const float z = (MODE & BT_MODE_CALL) ? __saturatef(__fsub_rn(y, c)) : __saturatef(__fsub_rn(c, y));
-                v[i] = __fmaf_rn(f4[i].z, z, __fmul_rn(f4[i].w, z));
-            }
-#pragma unroll
-            for (int w = 1; w < BT_UNROLL; w *= 2)
-#pragma unroll
-                for (int i = 0; i < BT_UNROLL; i += 2 * w) v[i] = __fadd_rn(v[i], v[i + w]);
-            const float sN = __fadd_rn(g[j], v[0]);
-            e[j] = __fadd_rn(e[j], __fsub_rn(v[0], __fsub_rn(sN, g[j])));
-            g[j] = sN;
-        }
+        for (int j = 0; j < BT_PT; ++j) fast_acc_s(g[j], e[j], wtree8<MODE>(f4, B[j], Ah[j], nAl[j]));
     }
-    df32 tot = df_make(0.0f, 0.0f);
+    df32 tot = df_make(0.0f, 0.0f), cst = df_make(0.0f, 0.0f);
 #pragma unroll
-    for (int j = 0; j < BT_PT; ++j) tot = df_add_pos(tot, df_mul(om[j], fast_two_sum(g[j], e[j])));
+    for (int j = 0; j < BT_PT; ++j) {
+        const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
+        if (q >= nP) continue;
+        const sstate st = steps_state(J, P, tab, q);
+        const scale32 sc = scale_prefix(st.tau, P, q);
+        tot = df_add_pos(tot, df_mul(df_mul(df_mul(st.w, st.beta), sc.rinv), fast_two_sum(g[j], e[j])));
+        cst = df_add_pos(cst, df_mul(st.w, st.cst));
+    }
     double v = df_to_double(tot);
     if (J.field == BT_F_LOOKMAX || J.field == BT_F_LOOKMIN) v += df_to_double(cst);
     const double2 sum = (MODE & BT_MODE_CALL) ? block_sum2(v, 0.0, red) : block_sum2(0.0, v, red);
