@@ -63,7 +63,7 @@ UNIT = "paths/s"
 N_DEFAULT = 36
 SETS_DEFAULT = 64
 OPS_PER_PATH = 3            # algorithmic: FMA (affine), max(.,0), accumulate
-OPS_EXECUTED_PAIR = 6.75    # per payoff-path in the fused call+put pass (54 ops / 8)
+OPS_EXECUTED_PAIR = 6.125   # inner-loop ops per call+put path pair (392 per 64 pairs)
 
 
 def parse():
@@ -519,7 +519,7 @@ def main():
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s", "frac": achieved / peak_gops,
             "traffic": profiled_traffic(args.N),
             "kernel": "k_exact32", "kernel_ms": 1e3 * kernel_s,
-            "ops_per_payoff_path": OPS_PER_PATH, "ops_executed_per_payoff_path": OPS_EXECUTED_PAIR,
+            "ops_per_payoff_path": OPS_PER_PATH, "ops_executed_per_payoff_path": OPS_EXECUTED_PAIR / 2,
             "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock, MEASURED_PEAKS.json)" % (sms, fmax)}
     if clocks.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e9)
