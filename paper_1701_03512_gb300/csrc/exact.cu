@@ -960,7 +960,7 @@ __device__ __forceinline__ prefd prefix_deriv(const bt_job &J, const bt_jparams 
 // up-count moment (for dV/dp), the u-derivative and the in-the-money mass.
 template <int MODE, bool CLS>
 __device__ __forceinline__ void greeks_tail(const bt_exact_args &a, const smem_job &sj, int64_t item_local,
-                                            const df32 *accV, const df32 *accK, const float *Nw, const df32 *Fw,
+                                            const df32 *accV, const df32 *accK, const df32 *Nw, const df32 *Fw,
                                             const df32 *Dw, double *red4) {
     const bt_job &J = sj.J;
     const bt_jparams &P = sj.P;
@@ -989,8 +989,9 @@ __device__ __forceinline__ void greeks_tail(const bt_exact_args &a, const smem_j
         tV += Vq;
         tK += kq * Vq + df_to_double(df_mul(om, accK[j])) + cq * (double)J.L * P.p;
         tD += wl * ((double)dv.Cp +
-                    sgn * ((double)dv.ap * Nw[j] + (double)dv.bp * df_to_double(Fw[j]) + (double)dv.b * df_to_double(Dw[j])));
-        tP += wl * (dv.C > 0.0f ? 1.0 : (double)Nw[j]);
+                    sgn * ((double)dv.ap * df_to_double(Nw[j]) + (double)dv.bp * df_to_double(Fw[j]) +
+                           (double)dv.b * df_to_double(Dw[j])));
+        tP += wl * (dv.C > 0.0f ? 1.0 : df_to_double(Nw[j]));
     }
     // deterministic block sum of four doubles
     for (int o = 16; o > 0; o >>= 1) {
@@ -1016,6 +1017,42 @@ __device__ __forceinline__ void greeks_tail(const bt_exact_args &a, const smem_j
     }
 }
 
+// Per-path derivative pass over eight suffixes under one prefix: the
+// payoff/lambda tree (as tree8), the in-the-money count and the tree of
+// df_s/du over the in-the-money suffixes.
+template <int MODE>
+__device__ __forceinline__ void greeks8(const float4 *f4, const float4 *d4, float B, float Ah, float nAl, float &tz,
+                                        float &td, float &cn) {
+    const float fh[BT_UNROLL] = {f4[0].x, f4[0].z, f4[1].x, f4[1].z, f4[2].x, f4[2].z, f4[3].x, f4[3].z};
+    const float fl[BT_UNROLL] = {f4[0].y, f4[0].w, f4[1].y, f4[1].w, f4[2].y, f4[2].w, f4[3].y, f4[3].w};
+    const float fd[BT_UNROLL] = {d4[0].x, d4[0].y, d4[0].z, d4[0].w, d4[1].x, d4[1].y, d4[1].z, d4[1].w};
+    float z[BT_UNROLL], t[BT_UNROLL];
+#pragma unroll
+    for (int i = 0; i < BT_UNROLL; ++i) {
+        const float y = __fmaf_rn(B, fh[i], Ah);
+        const float c = __fmaf_rn(B, fl[i], nAl);
+        z[i] = (MODE & BT_MODE_CALL) ? __saturatef(__fsub_rn(y, c)) : __saturatef(__fsub_rn(c, y));
+        // in the money (the NaN padding saturates to 0 and is never selected)
+        const bool itm = z[i] > 0.0f;
+        cn += itm ? 1.0f : 0.0f;
+        t[i] = itm ? fd[i] : 0.0f;
+    }
+#pragma unroll
+    for (int w = 1; w < BT_UNROLL; w *= 2)
+#pragma unroll
+        for (int i = 0; i < BT_UNROLL; i += 2 * w) {
+            z[i] = __fadd_rn(z[i], z[i + w]);
+            t[i] = __fadd_rn(t[i], t[i + w]);
+        }
+    tz = __fadd_rn(tz, z[0]);
+    td = __fadd_rn(td, t[0]);
+}
+
+// One work item of the derivative pass (per-path table). Per up-count group
+// and prefix: sum of payoff/lambda (eight trees per Fast2Sum), in-the-money
+// count (exact) and sum of df_s/du (eight trees per TwoSum). The sum of f over
+// the in-the-money suffixes follows from the payoff sum: each in-the-money z
+// is lambda |tau + f|, so sum f = +-sum z / lambda - tau N_w.
 template <int MODE>
 __device__ __forceinline__ void item_greeks(const bt_exact_args &a, const smem_job &sj, const float2 *s_suf,
                                             const float *s_sufd, double *red4) {
@@ -1033,75 +1070,73 @@ __device__ __forceinline__ void item_greeks(const bt_exact_args &a, const smem_j
         Ah[j] = pr.Ah;
         nAl[j] = pr.nAl;
     }
-    df32 accV[BT_PT], accK[BT_PT], Fw[BT_PT], Dw[BT_PT];
-    float Nw[BT_PT];
+    df32 accV[BT_PT], accK[BT_PT], Nw[BT_PT], Dw[BT_PT];
 #pragma unroll
-    for (int j = 0; j < BT_PT; ++j) {
-        accV[j] = accK[j] = Fw[j] = Dw[j] = df_make(0.0f, 0.0f);
-        Nw[j] = 0.0f;
-    }
+    for (int j = 0; j < BT_PT; ++j) accV[j] = accK[j] = Nw[j] = Dw[j] = df_make(0.0f, 0.0f);
     for (int k = 0; k <= J.L; ++k) {
         const int s0 = J.goff[k], s1 = J.goff[k + 1];
-        // group sums as (sum, compensation) pairs; the count is exact in FP32
-        float g[BT_PT], e[BT_PT], cn[BT_PT], cf[BT_PT], ef[BT_PT], cd[BT_PT], ed[BT_PT];
+        float g[BT_PT], e[BT_PT], cd[BT_PT], ed[BT_PT], cn[BT_PT];
 #pragma unroll
-        for (int j = 0; j < BT_PT; ++j) g[j] = e[j] = cn[j] = cf[j] = ef[j] = cd[j] = ed[j] = 0.0f;
-        for (int s = s0; s < s1; s += BT_UNROLL) {
+        for (int j = 0; j < BT_PT; ++j) g[j] = e[j] = cd[j] = ed[j] = cn[j] = 0.0f;
+        int s = s0;
+        for (; s + 8 * BT_UNROLL <= s1; s += 8 * BT_UNROLL) {
+            float tz[BT_PT], td[BT_PT];
+#pragma unroll
+            for (int j = 0; j < BT_PT; ++j) tz[j] = td[j] = 0.0f;
+#pragma unroll 1
+            for (int r = 0; r < 8; ++r) {
+                const int sr = s + r * BT_UNROLL;
+                float4 f4[BT_UNROLL / 2], d4[BT_UNROLL / 4];
+#pragma unroll
+                for (int i = 0; i < BT_UNROLL / 2; ++i) f4[i] = *reinterpret_cast<const float4 *>(s_suf + sr + 2 * i);
+#pragma unroll
+                for (int i = 0; i < BT_UNROLL / 4; ++i) d4[i] = *reinterpret_cast<const float4 *>(s_sufd + sr + 4 * i);
+#pragma unroll
+                for (int j = 0; j < BT_PT; ++j) greeks8<MODE>(f4, d4, B[j], Ah[j], nAl[j], tz[j], td[j], cn[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < BT_PT; ++j) {
+                fast_acc(g[j], e[j], tz[j]);
+                const df32 ts = two_sum(cd[j], td[j]);
+                cd[j] = ts.hi;
+                ed[j] = __fadd_rn(ed[j], ts.lo);
+            }
+        }
+        for (; s < s1; s += BT_UNROLL) {
             float4 f4[BT_UNROLL / 2], d4[BT_UNROLL / 4];
 #pragma unroll
             for (int i = 0; i < BT_UNROLL / 2; ++i) f4[i] = *reinterpret_cast<const float4 *>(s_suf + s + 2 * i);
 #pragma unroll
             for (int i = 0; i < BT_UNROLL / 4; ++i) d4[i] = *reinterpret_cast<const float4 *>(s_sufd + s + 4 * i);
-            const float fh[BT_UNROLL] = {f4[0].x, f4[0].z, f4[1].x, f4[1].z, f4[2].x, f4[2].z, f4[3].x, f4[3].z};
-            const float fl[BT_UNROLL] = {f4[0].y, f4[0].w, f4[1].y, f4[1].w, f4[2].y, f4[2].w, f4[3].y, f4[3].w};
-            const float fd[BT_UNROLL] = {d4[0].x, d4[0].y, d4[0].z, d4[0].w, d4[1].x, d4[1].y, d4[1].z, d4[1].w};
-            float ff[BT_UNROLL];
-#pragma unroll
-            for (int i = 0; i < BT_UNROLL; ++i) ff[i] = __fsub_rn(fh[i], fl[i]);  // f = f_hi - (-f_lo)
 #pragma unroll
             for (int j = 0; j < BT_PT; ++j) {
-                float z[BT_UNROLL], tf[BT_UNROLL], td[BT_UNROLL];
-#pragma unroll
-                for (int i = 0; i < BT_UNROLL; ++i) {
-                    const float y = __fmaf_rn(B[j], fh[i], Ah[j]);
-                    const float c = __fmaf_rn(B[j], fl[i], nAl[j]);
-                    z[i] = (MODE & BT_MODE_CALL) ? __saturatef(__fsub_rn(y, c)) : __saturatef(__fsub_rn(c, y));
-                    // in the money (the NaN padding saturates to 0 and is never selected)
-                    const bool itm = z[i] > 0.0f;
-                    cn[j] += itm ? 1.0f : 0.0f;
-                    tf[i] = itm ? ff[i] : 0.0f;
-                    td[i] = itm ? fd[i] : 0.0f;
-                }
-#pragma unroll
-                for (int w = 1; w < BT_UNROLL; w *= 2)
-#pragma unroll
-                    for (int i = 0; i < BT_UNROLL; i += 2 * w) {
-                        z[i] = __fadd_rn(z[i], z[i + w]);
-                        tf[i] = __fadd_rn(tf[i], tf[i + w]);
-                        td[i] = __fadd_rn(td[i], td[i + w]);
-                    }
-                float sN = __fadd_rn(g[j], z[0]);
-                e[j] = __fadd_rn(e[j], __fsub_rn(z[0], __fsub_rn(sN, g[j])));
-                g[j] = sN;
-                const df32 tsf = two_sum(cf[j], tf[0]);
-                cf[j] = tsf.hi;
-                ef[j] = __fadd_rn(ef[j], tsf.lo);
-                const df32 tsd = two_sum(cd[j], td[0]);
-                cd[j] = tsd.hi;
-                ed[j] = __fadd_rn(ed[j], tsd.lo);
+                float tz = 0.0f, td = 0.0f;
+                greeks8<MODE>(f4, d4, B[j], Ah[j], nAl[j], tz, td, cn[j]);
+                fast_acc(g[j], e[j], tz);
+                const df32 ts = two_sum(cd[j], td);
+                cd[j] = ts.hi;
+                ed[j] = __fadd_rn(ed[j], ts.lo);
             }
         }
         const df32 w = df_from2(P.W2[k]);
-        const float wf = (float)P.W[k];
 #pragma unroll
         for (int j = 0; j < BT_PT; ++j) {
             const df32 wg = df_mul(w, fast_two_sum(g[j], e[j]));
             accV[j] = df_add_pos(accV[j], wg);
             accK[j] = df_add_pos(accK[j], df_mul_f(wg, (float)k));
-            Nw[j] = __fmaf_rn(wf, cn[j], Nw[j]);
-            Fw[j] = df_add(Fw[j], df_mul(w, two_sum(cf[j], ef[j])));
+            Nw[j] = df_add_pos(Nw[j], df_mul_f(w, cn[j]));
             Dw[j] = df_add(Dw[j], df_mul(w, two_sum(cd[j], ed[j])));
         }
+    }
+    df32 Fw[BT_PT];
+#pragma unroll
+    for (int j = 0; j < BT_PT; ++j) {
+        const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
+        Fw[j] = df_make(0.0f, 0.0f);
+        if (q >= nP) continue;
+        const df32 tau = prefix_state(J, P, a, q).tau;
+        const df32 zl = df_mul(accV[j], scale_prefix(tau, P, q).rinv);  // sum of |tau + f| over ITM
+        Fw[j] = df_sub((MODE & BT_MODE_CALL) ? zl : df_neg(zl), df_mul(tau, Nw[j]));
     }
     greeks_tail<MODE, false>(a, sj, item_local, accV, accK, Nw, Fw, Dw, red4);
 }
@@ -1125,13 +1160,9 @@ __device__ __forceinline__ void item_greeks_cls(const bt_exact_args &a, const sm
         df32 om, cw;
         prefix_cls(J, P, a, q, q < nP, tau[j], om, cw);
     }
-    df32 accV[BT_PT], accK[BT_PT], Fw[BT_PT], Dw[BT_PT];
-    float Nw[BT_PT];
+    df32 accV[BT_PT], accK[BT_PT], Fw[BT_PT], Dw[BT_PT], Nw[BT_PT];
 #pragma unroll
-    for (int j = 0; j < BT_PT; ++j) {
-        accV[j] = accK[j] = Fw[j] = Dw[j] = df_make(0.0f, 0.0f);
-        Nw[j] = 0.0f;
-    }
+    for (int j = 0; j < BT_PT; ++j) accV[j] = accK[j] = Fw[j] = Dw[j] = Nw[j] = df_make(0.0f, 0.0f);
     for (int k = 0; k <= J.L; ++k) {
         df32 g[BT_PT], cf[BT_PT], cd[BT_PT];
         float cn[BT_PT];
@@ -1157,13 +1188,12 @@ __device__ __forceinline__ void item_greeks_cls(const bt_exact_args &a, const sm
             }
         }
         const df32 w = df_from2(P.W2[k]);
-        const float wf = (float)P.W[k];
 #pragma unroll
         for (int j = 0; j < BT_PT; ++j) {
             const df32 wg = df_mul(w, fast_two_sum(g[j].hi, g[j].lo));
             accV[j] = df_add_pos(accV[j], wg);
             accK[j] = df_add_pos(accK[j], df_mul_f(wg, (float)k));
-            Nw[j] = __fmaf_rn(wf, cn[j], Nw[j]);
+            Nw[j] = df_add_pos(Nw[j], df_mul_f(w, cn[j]));
             Fw[j] = df_add(Fw[j], df_mul(w, fast_two_sum(cf[j].hi, cf[j].lo)));
             Dw[j] = df_add(Dw[j], df_mul(w, two_sum(cd[j].hi, cd[j].lo)));
         }
@@ -1171,7 +1201,7 @@ __device__ __forceinline__ void item_greeks_cls(const bt_exact_args &a, const sm
     greeks_tail<MODE, true>(a, sj, item_local, accV, accK, Nw, Fw, Dw, red4);
 }
 
-__global__ void __launch_bounds__(BT_THREADS, 1) k_greeks32(bt_exact_args a) {
+__global__ void __launch_bounds__(BT_THREADS, 2) k_greeks32(bt_exact_args a) {
     extern __shared__ float4 smem_raw[];
     float2 *s_suf = reinterpret_cast<float2 *>(smem_raw);
     float *s_sufd = reinterpret_cast<float *>(s_suf + BT_SUF_MAX_EVEN);  // 16-byte aligned for float4 loads
