@@ -256,3 +256,68 @@ def test_budget_is_enforced(bt):
         assert bt.bt_device_bytes(c.h) == 0
     finally:
         c.close()
+
+
+def test_maximum_size_n40(bt, ctx, oracle):
+    """N = 40, the largest tree the exhaustive pass takes: an arithmetic call
+    and put pair (one fused pass of 2^40 paths each) against the oracle's
+    meet-in-the-middle value, and the class payoffs against the exact DPs."""
+    opts = [W.opt(40, 100.0, 102.0, 0.04, 0.25, 1.0, W.ASIAN_ARITH_CALL),
+            W.opt(40, 100.0, 102.0, 0.04, 0.25, 1.0, W.ASIAN_ARITH_PUT),
+            W.opt(40, 100.0, 97.0, 0.04, 0.25, 1.0, W.ASIAN_GEO_CALL),
+            W.opt(40, 100.0, 110.0, 0.04, 0.25, 1.0, W.LOOKBACK_FIXED_CALL),
+            W.opt(40, 100.0, 92.0, 0.04, 0.25, 1.0, W.LOOKBACK_FIXED_PUT)]
+    got = ctx.price_exact(opts, 1)
+    assert np.all(got["paths"] == 2 ** 40)
+    ref = [oracle.asian_mitm(o, 20) if o["payoff"] in (2, 3) else oracle.exact(o) for o in opts]
+    _check(got["value"], ref, opts, 1, "N=40")
+
+
+def test_degenerate_strikes(bt, ctx, oracle):
+    """K = 0: every path is in the money and the arithmetic call is the mean
+    of the average price, (S0/N) sum_t e^{rate t dt} on a risk-neutral tree;
+    a strike far above every price gives exactly 0 for the calls (and the
+    puts are the discounted strike minus that mean)."""
+    N, r, T = 30, 0.05, 1.0
+    mean_avg = 100.0 / N * sum(math.exp(r * t * T / N) for t in range(1, N + 1))
+    disc = math.exp(-r * T)
+    zero_k = [W.opt(N, 100.0, 0.0, r, 0.2, T, W.ASIAN_ARITH_CALL), W.opt(N, 100.0, 0.0, r, 0.2, T, W.EURO_CALL)]
+    got = ctx.price_exact(zero_k, 1)["value"]
+    assert abs(got[0] - disc * mean_avg) <= 1e-9 * disc * mean_avg
+    assert abs(got[1] - 100.0) <= 1e-9 * 100.0
+    big = 1e7
+    far = [W.opt(N, 100.0, big, r, 0.2, T, pay) for pay in (0, 2, 4, 6)]
+    assert np.all(ctx.price_exact(far, 1)["value"] == 0.0)
+    put = ctx.price_exact([W.opt(N, 100.0, big, r, 0.2, T, W.ASIAN_ARITH_PUT)], 1)["value"][0]
+    ref = disc * (big - mean_avg)
+    assert abs(put - ref) <= 1e-9 * ref
+
+
+def test_empty_and_single_step(bt, ctx, oracle):
+    with pytest.raises(bt.BtError) as e:
+        bt.bt_price_exact(ctx.h, [], 1)
+    assert e.value.status == bt.BT_EINVAL
+    for pay in range(8):
+        o = W.opt(1, 100.0, 100.0, 0.05, 0.2, 1.0, pay)
+        for prec in (0, 1):
+            got = ctx.price_exact([o], prec)["value"][0]
+            ref = oracle.price_exhaustive(o, 1)
+            assert abs(got - ref) <= tol(prec, 1, pay) * abs(ref) + 1e-12 * 100.0, (pay, prec, got, ref)
+
+
+def test_probability_limit_of_the_fp32_path(bt, ctx, oracle):
+    """min(p, 1-p) >= 0.004 is accepted in FP32 and matches the oracle; below
+    it FP32 is refused and FP64 still prices."""
+    u = 1.05
+    d = 1 / u
+    for p, ok in ((0.004, True), (0.996, True), (0.0039, False)):
+        o = W.opt(24, 100.0, 100.0, 0.0, 0.2, 1.0, W.ASIAN_ARITH_CALL, W.TREE_EXPLICIT, u=u, d=d, p=p)
+        if ok:
+            got = ctx.price_exact([o], 1)["value"][0]
+            ref = oracle.exact(o)
+            assert abs(got - ref) <= tol(1, 24) * abs(ref) + 1e-12 * 100.0
+        else:
+            with pytest.raises(bt.BtError) as e:
+                ctx.price_exact([o], 1)
+            assert e.value.status == bt.BT_EUNSUPPORTED
+            assert ctx.price_exact([o], 0)["value"][0] > 0.0
