@@ -127,6 +127,18 @@ def cpu_oracle_sample(opts, seconds, threads):
     return paths / dt, sample
 
 
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                v = ln.split(":", 1)[1].strip()
+                return {"0xd4f": "Arm Neoverse-V2 (part 0xd4f)"}.get(v, v)
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_threads():
     try:
         return len(os.sched_getaffinity(0))
@@ -291,7 +303,7 @@ MC_OPS_PER_STEP = 14   # Philox-4x32-10 per 4 steps: 10 rounds x (2 wide multipl
                        # (the key schedule is the same for every thread); + compare, select, multiply, add
 
 
-def mc_bench(bt, W, ctx, sms, fmax, reps=3):
+def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
     import torch
     N, mb, R = 252, 16, 1 << 14
     o = W.opt(N, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
@@ -310,8 +322,17 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3):
     samples = float(R) * (1 << mb)
     steps = samples * (N - mb)
     peak = sms * 128 * fmax * 1e6
+    cpu = None
+    if with_cpu:
+        from oracle import py_oracle as O
+        mb_c, R_c = 4, 256
+        t0 = time.perf_counter()
+        O.mc(o, mb_c, R_c, 1)
+        dt = time.perf_counter() - t0
+        cpu = {"samples_per_s": (1 << mb_c) * R_c / dt, "cores": 1, "kind": "oracle",
+               "sample": "2^%d strata x %d samples of the same option, one thread" % (mb_c, R_c)}
     return {"workload": "Partitioned MC, arithmetic Asian call, N=%d, S0=K=100, rate 0.05, sigma 0.2, T=1, "
-                        "2^%d strata x %d samples" % (N, mb, R),
+                        "2^%d strata x %d samples" % (N, mb, R), "cpu_baseline": cpu,
             "samples_per_s": samples / t, "steps_per_s": steps / t, "ms": 1e3 * t,
             "value": float(r[0]["value"]), "stderr": float(r[0]["stderr_mc"]),
             "ops_per_step": MC_OPS_PER_STEP, "frac_of_issue_peak": MC_OPS_PER_STEP * steps / t / peak}
@@ -382,6 +403,20 @@ def extras_bench(bt, W, ctx, sms, fmax):
     out["generic_trinomial"] = {"workload": "generic pass, trinomial trees, arithmetic Asian and lookback calls, "
                                             "N=17, 2 x 3^17 paths", "ms": 1e3 * t,
                                 "payoff_paths_per_s": 2 * 3.0 ** N3 / t}
+    # the paper's runtime workload (Section 5): a European put, K=10, S0=5,
+    # sigma 0.3, rate 0.06, T=1, CRR, N=32; the paper's 64-core Julia run took
+    # 13:38 (818 s) and R 2:22:59 (8579 s) on 2x E5-2650v2 nodes
+    op = W.paper_runtime_workload(32)
+    t_fast = _timed(lambda: bt.bt_price_exact(ctx.h, [op], bt.BT_PREC_FP64))
+    u, d, p = bt.bt_tree_params(op)
+    mvp = [np.tile([d, u, 1 - p, p], (32, 1))]
+    t_walk = _timed(lambda: bt.bt_price_exact_branching(ctx.h, [op], 2, mvp), reps=1)
+    out["paper_runtime_workload"] = {
+        "workload": "European put, K=10, S0=5, sigma 0.3, rate 0.06, T=1, CRR, N=32 (2^32 paths)",
+        "exact_fp64_s": t_fast, "generic_per_path_walk_s": t_walk,
+        "paper_context": {"julia_64_cores_s": 818, "r_64_cores_s": 8579,
+                          "hardware": "8 nodes of 2x Intel E5-2650v2 (16 cores each), QDR InfiniBand",
+                          "note": "context, not the target: the paper's workload on the paper's cluster"}}
     return out
 
 
@@ -528,11 +563,13 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         threads = cpu_threads()
         v, sample = cpu_oracle_sample(opts, args.cpu_seconds, threads)
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+        v1, sample1 = cpu_oracle_sample(opts, max(2.0, args.cpu_seconds / 4), 1)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+               "one_core": {"value": v1, "sample": sample1}, "cpu": cpu_model()}
 
     serving = mc = greeks = extras = None
     if world == 1 and not args.no_mc:
-        mc = mc_bench(bt, W, ctx, sms, fmax)
+        mc = mc_bench(bt, W, ctx, sms, fmax, with_cpu=not args.no_cpu_baseline)
     if world == 1 and not args.no_greeks:
         greeks = greeks_bench(bt, W, ctx)
     if world == 1 and not args.no_extras:
