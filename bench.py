@@ -223,7 +223,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("exact.cu", "df.cuh", "bt_internal.h"):
+    for f in ("exact.cu", "exact_common.cuh", "df.cuh", "bt_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1701_03512_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -99,3 +99,151 @@ __device__ __forceinline__ scale32 scale_prefix(const df32 &tau, const bt_jparam
     r.rinv = fast_two_sum(r0, r0 * res);
     return r;
 }
+
+// ---------------------------------------------------------------------------
+// Per-prefix state of the lattice passes (exact.cu, greeks.cu)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df32 pw2(const bt_pow *t, int e) {
+    bt_pow v = t[e];
+    return df_make(v.hi, v.lo);
+}
+
+struct pref32 {
+    float B, Ah, nAl;
+    df32 om;   // w_low * beta * 2^e
+    df32 cst;  // w_low * C (lookback)
+};
+
+// Per-prefix affine form of the payoff in the suffix factor f:
+// payoff = beta * max(+-(tau + f), 0) + C, with tau, beta, C as FP32 pairs.
+struct pstate {
+    df32 tau, beta, cst;
+};
+__device__ __forceinline__ pstate prefix_state(const bt_job &J, const bt_jparams &P, const bt_exact_args &a,
+                                               int64_t q) {
+    const int64_t h = q >> J.M;
+    const int m = (int)(q & ((1ll << J.M) - 1));
+    const bt_pentry eh = a.ph[J.off_ph + h];
+    const bt_pentry em = a.pm[J.off_pm + m];
+    const int lvl = eh.lvl + em.lvl;
+    const bt_pow *pw = a.pw + J.off_pow + J.N + 1;
+    df32 tau, beta, cst = df_make(0.0f, 0.0f);
+    switch (J.field) {
+    case BT_F_ARITH: {
+        // tau = Sigma_P / S_P - N K / S_P, Sigma_P / S_P = u^{-Delta_m} R_h + R_m
+        df32 Rp = df_add(df_mul(pw2(pw, -em.lvl), df_make(eh.R_hi, eh.R_lo)), df_make(em.R_hi, em.R_lo));
+        df32 X = df_mul(df_from2(P.NKoS0_2), pw2(pw, -lvl));
+        tau = df_sub(Rp, X);
+        beta = df_mul(df_from2(P.S0oN_2), pw2(pw, lvl));
+        break;
+    }
+    case BT_F_EURO:
+        tau = df_neg(df_mul(df_from2(P.KoS0_2), pw2(pw, -lvl)));
+        beta = df_mul(df_from2(P.S0_2), pw2(pw, lvl));
+        break;
+    case BT_F_GEO: {
+        const int I = (int)eh.D + J.M * (int)eh.lvl + (int)em.D + J.L * lvl;
+        const bt_pow *g = a.pw + J.off_geo - J.geo_imin;
+        tau = df_neg(df_mul(df_from2(P.KoS0_2), pw2(g, -I)));
+        beta = df_mul(df_from2(P.S0_2), pw2(g, I));
+        break;
+    }
+    case BT_F_LOOKMAX: {
+        const int lam = max((int)eh.mx, (int)eh.lvl + (int)em.mx);
+        df32 kk = df_mul(df_from2(P.KoS0_2), pw2(pw, -lvl));
+        if (lam > -BT_LVL_NONE / 2) {
+            // tau = -max(M_P, K) / S_P,  C = max(M_P - K, 0)
+            df32 rr = pw2(pw, lam - lvl);
+            tau = df_neg(df_gt(rr, kk) ? rr : kk);
+            df32 c = df_sub(df_mul(df_from2(P.S0_2), pw2(pw, lam)), df_from2(P.K_2));
+            if (c.hi > 0.0f) cst = c;
+        } else {
+            tau = df_neg(kk);
+        }
+        beta = df_mul(df_from2(P.S0_2), pw2(pw, lvl));
+        break;
+    }
+    default: {  // BT_F_LOOKMIN
+        const int lam = min((int)eh.mn, (int)eh.lvl + (int)em.mn);
+        df32 kk = df_mul(df_from2(P.KoS0_2), pw2(pw, -lvl));
+        if (lam < BT_LVL_NONE / 2) {
+            // tau = -min(m_P, K) / S_P,  C = max(K - m_P, 0)
+            df32 rr = pw2(pw, lam - lvl);
+            tau = df_neg(df_gt(rr, kk) ? kk : rr);
+            df32 c = df_sub(df_from2(P.K_2), df_mul(df_from2(P.S0_2), pw2(pw, lam)));
+            if (c.hi > 0.0f) cst = c;
+        } else {
+            tau = df_neg(kk);
+        }
+        beta = df_mul(df_from2(P.S0_2), pw2(pw, lvl));
+        break;
+    }
+    }
+    pstate st;
+    st.tau = tau;
+    st.beta = beta;
+    st.cst = cst;
+    return st;
+}
+
+// Per-prefix affine coefficients: y = B * (tau + f) with B = 2^-e chosen so that
+// |y| <= 1 over the whole suffix range, so that max(y, 0) is a saturating add.
+__device__ __forceinline__ pref32 prefix32(const bt_job &J, const bt_jparams &P, const bt_exact_args &a,
+                                           int64_t q, bool valid) {
+    pref32 r;
+    if (!valid) {
+        r.B = 0.0f;
+        r.Ah = __int_as_float(0x7fc00000);
+        r.nAl = r.Ah;
+        r.om = df_make(0.0f, 0.0f);
+        r.cst = df_make(0.0f, 0.0f);
+        return r;
+    }
+    const pstate st = prefix_state(J, P, a, q);
+    const df32 tau = st.tau, beta = st.beta, cst = st.cst;
+    const scale32 sc = scale_prefix(tau, P, q);
+    r.B = sc.B;
+    r.Ah = sc.Ah;
+    r.nAl = sc.nAl;
+    const df32 rinv = sc.rinv;
+    const int c = __popc((unsigned)(q & ((1 << BT_LOW_BITS) - 1)));
+    r.om = df_mul(df_mul(df_from2(P.wl2[c]), beta), rinv);
+    r.cst = df_mul(df_from2(P.wl2[c]), cst);
+    return r;
+}
+
+// Payoffs/lambda of eight suffixes under one prefix: y = lambda (tau_hi + f_hi)
+// exactly, c = -lambda (tau_lo + f_lo), z = sat(+-(y - c)); returns the
+// eight-wide addition tree of the call (MODE & CALL) and put z.
+// g + t as (sum, compensation): Fast2Sum (|g| >= |t| after the first add).
+__device__ __forceinline__ void fast_acc(float &g, float &e, float t) {
+    const float sN = __fadd_rn(g, t);
+    e = __fadd_rn(e, __fsub_rn(t, __fsub_rn(sN, g)));
+    g = sN;
+}
+
+// g += m * (th + tl) for an unnormalised pair (th, tl): exact product of the
+// high part (TwoProd), then TwoSum into g; m is a small integer (or 0).
+__device__ __forceinline__ void acc_pair(df32 &g, float m, float th, float tl) {
+    const df32 p = two_prod(m, th);
+    const float lo = __fmaf_rn(m, tl, p.lo);
+    const df32 t = two_sum(g.hi, p.hi);
+    g.hi = t.hi;
+    g.lo = __fadd_rn(g.lo, __fadd_rn(t.lo, lo));
+}
+
+// Per-prefix pair coefficients of the class pass: tau, w_low * beta and
+// w_low * C (zero for a prefix past the end of the job).
+__device__ __forceinline__ void prefix_cls(const bt_job &J, const bt_jparams &P, const bt_exact_args &a, int64_t q,
+                                           bool valid, df32 &tau, df32 &om, df32 &cst) {
+    if (!valid) {
+        tau = om = cst = df_make(0.0f, 0.0f);
+        return;
+    }
+    const pstate st = prefix_state(J, P, a, q);
+    const df32 wl = df_from2(P.wl2[__popc((unsigned)(q & ((1 << BT_LOW_BITS) - 1)))]);
+    tau = st.tau;
+    om = df_mul(wl, st.beta);
+    cst = df_mul(wl, st.cst);
+}
+
