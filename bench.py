@@ -403,6 +403,14 @@ def extras_bench(bt, W, ctx, sms, fmax):
     out["generic_trinomial"] = {"workload": "generic pass, trinomial trees, arithmetic Asian and lookback calls, "
                                             "N=17, 2 x 3^17 paths", "ms": 1e3 * t,
                                 "payoff_paths_per_s": 2 * 3.0 ** N3 / t}
+    # the batched workload at N=32 in the all-FP64 kernel (the accuracy reference) beside FP32_COMP
+    o32 = W.batched_exact_workload(32, 0, 64)
+    t64 = _timed(lambda: bt.bt_price_exact(ctx.h, o32, bt.BT_PREC_FP64), reps=1)
+    t32 = _timed(lambda: bt.bt_price_exact(ctx.h, o32, bt.BT_PREC_FP32_COMP), reps=2)
+    out["batched_n32_fp64_vs_fp32"] = {
+        "workload": "batched arithmetic-Asian call+put, N=32, 64 sets (seed 0), host arrays in and out",
+        "fp64_s": t64, "fp32_comp_s": t32, "fp64_payoff_paths_per_s": 128 * 2.0 ** 32 / t64,
+        "fp32_comp_payoff_paths_per_s": 128 * 2.0 ** 32 / t32}
     # the paper's runtime workload (Section 5): a European put, K=10, S0=5,
     # sigma 0.3, rate 0.06, T=1, CRR, N=32; the paper's 64-core Julia run took
     # 13:38 (818 s) and R 2:22:59 (8579 s) on 2x E5-2650v2 nodes
