@@ -220,7 +220,7 @@ bt_status bt_price_exact_plugin(bt_ctx *ctx, const bt_payoff_plugin *plugin, con
  * > 0, probabilities in [0,1] summing to 1 within 1e-12, else BT_EINVAL).
  * With plugin NULL each option's own payoff (opts[i].payoff, K) is priced;
  * else the plug-in with params as for bt_price_exact_plugin. 2 <= branches
- * <= 8, b^N <= 2^48 (BT_EUNSUPPORTED above). Of opts[i]: N, payoff, S0, K,
+ * <= 8, b^N <= 2^40 (BT_EUNSUPPORTED above). Of opts[i]: N, payoff, S0, K,
  * rate, T. Every path is evaluated by the generic pass of btree_payoff.cuh
  * (FP64). paths = b^N. Synchronous on `stream`. */
 bt_status bt_price_exact_branching(bt_ctx *ctx, const bt_payoff_plugin *plugin, const bt_option *opts, int32_t n,

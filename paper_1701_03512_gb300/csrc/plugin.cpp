@@ -300,10 +300,10 @@ extern "C" bt_status bt_price_exact_branching(bt_ctx *ctx, const bt_payoff_plugi
         const bt_option &op = opts[i];
         bt_status s = check_scalars(op, i);
         if (s != BT_OK) return s;
-        // b^N paths, at most 2^48
+        // b^N paths, at most 2^40 (about a minute of the generic walk)
         double lg = (double)op.N * std::log2((double)b);
-        if (op.N < 1 || lg > 48.0)
-            return bt_fail(op.N < 1 ? BT_EINVAL : BT_EUNSUPPORTED, "option %d: %d^%d paths outside 1..2^48", i, b, op.N);
+        if (op.N < 1 || lg > 40.0 + 1e-9)
+            return bt_fail(op.N < 1 ? BT_EINVAL : BT_EUNSUPPORTED, "option %d: %d^%d paths outside 1..2^40", i, b, op.N);
         for (int t = 0; t < op.N; ++t) {
             const double *mv = moves + 2 * b * (total_steps + t);
             double psum = 0.0;
