@@ -564,6 +564,8 @@ def main():
             "kernel": "k_exact32", "kernel_ms": 1e3 * kernel_s,
             "ops_per_payoff_path": OPS_PER_PATH, "ops_executed_per_payoff_path": OPS_EXECUTED_PAIR / 2,
             "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock, MEASURED_PEAKS.json)" % (sms, fmax)}
+    # the same throughput counted as executed: the inner loop's 6.125 instructions per call+put pair
+    roof["frac_as_executed"] = roof["frac"] * (OPS_EXECUTED_PAIR / 2) / OPS_PER_PATH
     if clocks.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e9)
 
