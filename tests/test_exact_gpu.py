@@ -321,3 +321,13 @@ def test_probability_limit_of_the_fp32_path(bt, ctx, oracle):
                 ctx.price_exact([o], 1)
             assert e.value.status == bt.BT_EUNSUPPORTED
             assert ctx.price_exact([o], 0)["value"][0] > 0.0
+
+
+def test_paper_section5_parameters_to_the_contract(bt, ctx, oracle):
+    """The Section 5 tree (Seydel, sigma = 3, S0 = 20, K = 100, N = 32: prices
+    spread over ten decades) for every payoff, FP32 and FP64, against the
+    oracle at the contract tolerance -- not only the paper's three decimals."""
+    opts = [W.opt(32, 20.0, 100.0, 0.06, 3.0, 1.0, pay, W.TREE_SEYDEL) for pay in range(8)]
+    ref = [oracle.asian_mitm(o, 16) if o["payoff"] in (2, 3) else oracle.exact(o) for o in opts]
+    for prec in (0, 1):
+        _check(ctx.price_exact(opts, prec)["value"], ref, opts, prec, "Section 5 tree")
