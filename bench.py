@@ -321,6 +321,8 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
     t = statistics.median(ts)
     samples = float(R) * (1 << mb)
     steps = samples * (N - mb)
+    # plain MC with the same total number of draws (eq. mc14 comparison)
+    plain = bt.bt_price_mc(ctx.h, [o], 0, int(samples), 7, stream)[0]
     peak = sms * 128 * fmax * 1e6
     cpu = None
     if with_cpu:
@@ -335,6 +337,8 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
                         "2^%d strata x %d samples" % (N, mb, R), "cpu_baseline": cpu,
             "samples_per_s": samples / t, "steps_per_s": steps / t, "ms": 1e3 * t,
             "value": float(r[0]["value"]), "stderr": float(r[0]["stderr_mc"]),
+            "plain_mc_same_draws": {"value": float(plain["value"]), "stderr": float(plain["stderr_mc"]),
+                                    "variance_ratio": float((plain["stderr_mc"] / r[0]["stderr_mc"]) ** 2)},
             "ops_per_step": MC_OPS_PER_STEP, "frac_of_issue_peak": MC_OPS_PER_STEP * steps / t / peak}
 
 
