@@ -222,9 +222,15 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the code (comments and blank space removed) the path-sum
+    kernel is built from, to tell whether the committed counters still apply."""
+    import re
     h = hashlib.sha256()
     for f in ("exact.cu", "exact_common.cuh", "df.cuh", "bt_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1701_03512_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1701_03512_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -12,11 +12,17 @@
 // table (sorted by k) in shared memory, each thread holds four prefixes in
 // registers, and every path costs one FP32 FMA for lambda (tau + f), one FMA
 // for the low-order correction, one saturating add for max(., 0) and its
-// share of an eight-wide addition tree. Each tree's sum enters the group sum
-// through TwoSum (compensated), group sums are folded with the weight w(k) by
-// error-free transformations, prefixes are combined in FP32 pairs, and the
-// block's total goes to FP64 (eq. f14); block partials are added in a fixed
-// order per option (eq. f15).
+// share of an eight-wide addition tree (a call and a put of the same tree
+// share the two FMAs). Eight trees are added in turn and enter the group sum
+// through one Fast2Sum (compensated), group sums are folded with the weight
+// w(k) by error-free transformations, prefixes are combined in FP32 pairs,
+// and the block's total goes to FP64 (eq. f14); block partials are added in
+// a fixed order per option (eq. f15).
+//
+// The European, geometric and lookback payoffs take a table of recombined
+// suffix classes instead (k_class_tables, item32_cls): within an up-count
+// group their f_s depends on one integer key, so each class is evaluated once
+// per prefix in FP32-pair arithmetic and weighted by its multiplicity.
 //
 // Rounding design of the FP32 path. The per-prefix scale lambda = 2^-e
 // (256 - h)/256, with 2^e bounding |tau + f| over the suffix range and h a
