@@ -7,9 +7,12 @@
 // key = (seed_lo, seed_hi)) and goes up iff that word is below
 // thr = round(p 2^32). The Shared-Sample estimator (Remark of Section 4) uses
 // counter word 2 = 0 for every stratum, i.e. the same R suffixes under every
-// prefix. A block owns 1024 consecutive samples of one stratum; per-item
-// (count, mean, M2) go to scratch and are combined per stratum (Chan et al.'s
-// pairwise update) and then across strata in FP64 (eq. mc12 and its variance).
+// prefix. A work item is 1024 consecutive samples of one stratum: one warp
+// runs it in the Partitioned kernel (k_mc_warp), one block in the
+// Shared-Sample kernel (k_mc, whose strata states sit in shared memory).
+// Per-item (count, mean, M2) go to scratch and are combined per stratum
+// (Chan et al.'s pairwise update) and then across strata in FP64 (eq. mc12
+// and its variance). A shard runs the strata m = shard + j n_shards only.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
