@@ -5,7 +5,7 @@
  *
  * General conventions
  *   - Every call returns a bt_status and never aborts or throws across the ABI.
- *     On failure, bt_last_error() returns a thread-local message.
+ *     On failure, bt_last_error(ctx) returns a thread-local message.
  *   - Host arrays belong to the caller and are read or written only during
  *     the call (inputs are copied before the call returns).
  *   - Device memory is owned by the library (a context allocates it within the
@@ -97,8 +97,10 @@ typedef struct bt_ctx bt_ctx;
 /* Library and context ------------------------------------------------------ */
 const char *bt_version(void);
 const char *bt_status_str(bt_status s);
-/* Thread-local message of the last failed call on this thread ("" if none). */
-const char *bt_last_error(void);
+/* Message of the last failed call on the calling thread ("" if none). The
+ * message is thread-local, not per context: ctx is accepted for symmetry with
+ * the other calls and may be NULL. */
+const char *bt_last_error(const bt_ctx *ctx);
 
 /* Create a context on CUDA device `device` that may hold up to
  * `device_budget_bytes` of library-owned device memory (0 = 8 GiB).
@@ -303,7 +305,7 @@ typedef struct {
     int32_t max_active;            /* requests admitted at once (slots); 0 = 256           */
     int32_t n_streams;             /* path-sum launches in flight; 0 = 3                    */
     int32_t max_items_per_launch;  /* 2^10-prefix work items per launch; 0 = 1216           */
-    int32_t use_fp64;              /* 0 = BT_PREC_FP32_COMP, 1 = BT_PREC_FP64               */
+    int32_t use_fp64;              /* precision bt_serve_replay submits with: 0 = FP32_COMP, 1 = FP64 */
     size_t device_budget_bytes;    /* device memory for slots, tables, partials; 0 = 8 GiB */
 } bt_server_cfg;
 typedef struct {
@@ -320,9 +322,11 @@ typedef struct {
 /* Starts the scheduler thread; allocates device_budget_bytes from the context
  * (BT_EBUDGET if that exceeds the context's budget). */
 bt_status bt_server_start(bt_ctx *ctx, const bt_server_cfg *cfg, bt_server **out);
-/* Queues one option; returns at once with a ticket. Validation errors as
- * bt_price_exact; BT_EBUDGET if one request alone exceeds the pool. */
-bt_status bt_submit(bt_server *srv, const bt_option *opt, uint64_t *ticket);
+/* Queues one option, priced at precision `prec`; returns at once with a
+ * ticket. Requests of both precisions share the server (each launch runs one
+ * precision's kernel). Validation errors as bt_price_exact; BT_EBUDGET if one
+ * request alone exceeds the pool. */
+bt_status bt_submit(bt_server *srv, const bt_option *opt, bt_precision prec, uint64_t *ticket);
 /* Waits up to timeout_ms for the ticket's result (BT_ETIMEOUT on expiry; the
  * request stays queued). A ticket can be collected once. */
 bt_status bt_wait(bt_server *srv, uint64_t ticket, int32_t timeout_ms, bt_result *out);

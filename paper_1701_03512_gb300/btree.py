@@ -93,7 +93,7 @@ def lib():
         L = C.CDLL(LIB_PATH)
         _proto(L, "bt_version", [], C.c_char_p)
         _proto(L, "bt_status_str", [C.c_int], C.c_char_p)
-        _proto(L, "bt_last_error", [], C.c_char_p)
+        _proto(L, "bt_last_error", [_vp], C.c_char_p)
         _proto(L, "bt_create", [C.c_int, _sz, C.POINTER(_vp)])
         _proto(L, "bt_destroy", [_vp], None)
         _proto(L, "bt_device_bytes", [_vp], _sz)
@@ -122,7 +122,7 @@ def lib():
         _proto(L, "bt_philox4x32_10", [_vp, _vp, _vp, _vp, _i32])
         _proto(L, "bt_greeks_exact", [_vp, _vp, _i32, C.c_int, _vp, _vp, _vp])
         _proto(L, "bt_server_start", [_vp, C.POINTER(bt_server_cfg), C.POINTER(_vp)])
-        _proto(L, "bt_submit", [_vp, _vp, C.POINTER(C.c_uint64)])
+        _proto(L, "bt_submit", [_vp, _vp, C.c_int, C.POINTER(C.c_uint64)])
         _proto(L, "bt_wait", [_vp, C.c_uint64, _i32, _vp])
         _proto(L, "bt_poll", [_vp, C.c_uint64, _vp, C.POINTER(_i32)])
         _proto(L, "bt_server_stats", [_vp, C.POINTER(bt_server_stats_t)])
@@ -135,7 +135,7 @@ def lib():
 
 def _check(status):
     if status != BT_OK:
-        raise BtError(status, lib().bt_last_error().decode())
+        raise BtError(status, lib().bt_last_error(None).decode())
 
 
 def _stream(s):
@@ -291,7 +291,7 @@ def bt_plugin_compile(ctx, source: str):
     h = _vp()
     st = lib().bt_plugin_compile(ctx, source.encode(), log, len(log), C.byref(h))
     if st != BT_OK:
-        raise BtError(st, lib().bt_last_error().decode() + "\n" + log.value.decode(errors="replace"))
+        raise BtError(st, lib().bt_last_error(None).decode() + "\n" + log.value.decode(errors="replace"))
     return h, log.value.decode(errors="replace")
 
 
@@ -383,10 +383,10 @@ def bt_server_start(ctx, **cfg):
     return h
 
 
-def bt_submit(srv, opt) -> int:
+def bt_submit(srv, opt, prec=BT_PREC_FP32_COMP) -> int:
     a = options_array(opt)
     t = C.c_uint64()
-    _check(lib().bt_submit(srv, a.ctypes.data, C.byref(t)))
+    _check(lib().bt_submit(srv, a.ctypes.data, prec, C.byref(t)))
     return t.value
 
 

@@ -32,7 +32,7 @@ bt_status bt_cuda_fail(int err, const char *what) {
     return bt_fail(BT_ECUDA, "%s: %s", what, cudaGetErrorString((cudaError_t)err));
 }
 
-extern "C" const char *bt_last_error(void) { return g_err; }
+extern "C" const char *bt_last_error(const bt_ctx *) { return g_err; }
 extern "C" const char *bt_version(void) { return "libbtree 0.1 (sm_103a)"; }
 extern "C" const char *bt_status_str(bt_status s) {
     switch (s) {

@@ -83,6 +83,7 @@ struct request {
     uint64_t ticket;
     bt_option opt;
     bt_job job;  // shape and table offsets (pool-relative)
+    int prec = BT_PREC_FP32_COMP;
     int slot = -1;
     size_t mem_off = 0, mem_bytes = 0;
     int64_t next_item = 0, done_items = 0;
@@ -122,7 +123,6 @@ struct bt_server {
     bt_job *h_setup_jobs = nullptr, *d_setup_jobs = nullptr;
     bt_option *h_setup_opts = nullptr;
     std::vector<launch_slot> slots;
-    int grid = 0;
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -147,7 +147,6 @@ struct bt_server {
 };
 
 static void server_loop(bt_server *S);
-#define S_PREC(S) ((S)->cfg.use_fp64 ? BT_PREC_FP64 : BT_PREC_FP32_COMP)
 
 static bt_status server_fail(bt_server *S, bt_status s, const char *what) {
     S->fatal = s;
@@ -219,7 +218,6 @@ extern "C" bt_status bt_server_start(bt_ctx *ctx, const bt_server_cfg *cfg_in, b
         return r;
     }
     for (int i = A - 1; i >= 0; --i) S->free_slots.push_back(i);
-    S->grid = cfg.use_fp64 ? ctx->grid64 : ctx->grid32;
     S->th = std::thread(server_loop, S);
     *out = S;
     return BT_OK;
@@ -237,11 +235,12 @@ static size_t request_bytes(const bt_job &J, int prec, size_t *o_suf, size_t *o_
     return off;
 }
 
-extern "C" bt_status bt_submit(bt_server *S, const bt_option *opt, uint64_t *ticket) {
+extern "C" bt_status bt_submit(bt_server *S, const bt_option *opt, bt_precision prec, uint64_t *ticket) {
     if (!S || !opt || !ticket) return bt_fail(BT_EINVAL, "bt_submit: bad arguments");
+    if (prec != BT_PREC_FP64 && prec != BT_PREC_FP32_COMP) return bt_fail(BT_EINVAL, "bt_submit: bad precision %d", (int)prec);
     bt_status s = validate_option(opt, 0, BT_MAX_N_EXACT);
     if (s != BT_OK) return s;
-    if (S_PREC(S) == BT_PREC_FP32_COMP) {
+    if (prec == BT_PREC_FP32_COMP) {
         double u, d, p;
         host_tree(opt, &u, &d, &p);
         if (p < 0.004 || 1.0 - p < 0.004)
@@ -250,9 +249,10 @@ extern "C" bt_status bt_submit(bt_server *S, const bt_option *opt, uint64_t *tic
     request r;
     memset(&r.job, 0, sizeof(r.job));
     int step = 1;
-    plan_one_job(opt, 1, 0, &r.job, &step, S_PREC(S));
+    plan_one_job(opt, 1, 0, &r.job, &step, prec);
+    r.prec = prec;
     size_t a, b, c, d, e;
-    r.mem_bytes = request_bytes(r.job, S_PREC(S), &a, &b, &c, &d, &e);
+    r.mem_bytes = request_bytes(r.job, prec, &a, &b, &c, &d, &e);
     if (r.mem_bytes > S->pool_bytes)
         return bt_fail(BT_EBUDGET, "bt_submit: request needs %zu bytes, pool holds %zu", r.mem_bytes, S->pool_bytes);
     r.opt = *opt;
@@ -397,6 +397,9 @@ static void admit(bt_server *S) {
         }
     }
     if (admitted.empty()) return;
+    // grouped by precision (FP64 = 0 first): one table launch per group
+    std::stable_sort(rq.begin(), rq.end(), [](const request *x, const request *y) { return x->prec < y->prec; });
+    for (size_t i = 0; i < rq.size(); ++i) admitted[i] = rq[i]->ticket;
     // the pinned staging of the previous admission must have been copied
     cudaError_t e = cudaEventSynchronize(S->setup_done);
     // tables of the new requests on the set-up stream; launches wait on its event
@@ -404,7 +407,7 @@ static void admit(bt_server *S) {
     for (size_t i = 0; i < admitted.size(); ++i) {
         request &r = *rq[i];
         size_t o_suf, o_ph, o_pm, o_pw, o_part;
-        request_bytes(r.job, S_PREC(S), &o_suf, &o_ph, &o_pm, &o_pw, &o_part);
+        request_bytes(r.job, r.prec, &o_suf, &o_ph, &o_pm, &o_pw, &o_part);
         bt_job &J = r.job;
         const size_t pool_off = r.mem_off;  // pool-relative; every part is 256-byte aligned
         J.opt = r.slot;
@@ -433,9 +436,14 @@ static void admit(bt_server *S) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(S->d_setup_jobs, S->h_setup_jobs, sizeof(bt_job) * na, cudaMemcpyHostToDevice, st);
     int le = e == cudaSuccess ? bt_launch_params(S->d_opts, S->d_setup_jobs, S->d_prm, na, st) : (int)e;
-    if (!le)
-        le = bt_launch_tables(S->d_setup_jobs, S->d_prm, na, max_len, S_PREC(S), (float2 *)S->pool,
+    // rq is sorted with FP64 (prec 0) first: tables per precision group
+    for (int i0 = 0; i0 < na && !le;) {
+        int i1 = i0;
+        while (i1 < na && rq[i1]->prec == rq[i0]->prec) ++i1;
+        le = bt_launch_tables(S->d_setup_jobs + i0, S->d_prm, i1 - i0, max_len, rq[i0]->prec, (float2 *)S->pool,
                               (double *)S->pool, (bt_pentry *)S->pool, (bt_pentry *)S->pool, (bt_pow *)S->pool, st);
+        i0 = i1;
+    }
     if (!le) le = (int)cudaEventRecord(S->setup_done, st);
     std::lock_guard<std::mutex> lock(S->mu);
     if (le) {
@@ -451,6 +459,7 @@ static void admit(bt_server *S) {
 // enqueued behind it on the same stream.
 static bool launch_work(bt_server *S, launch_slot &L, int li) {
     std::vector<std::pair<request *, int64_t>> pick;
+    int prec = BT_PREC_FP32_COMP;
     std::vector<request *> fin;
     uint32_t wait_mask = 0;
     {
@@ -467,7 +476,9 @@ static bool launch_work(bt_server *S, launch_slot &L, int li) {
             return ra != rb ? ra < rb : a->ticket < b->ticket;
         });
         int64_t budget = S->cfg.max_items_per_launch;
+        prec = cand[0]->prec;  // a launch runs one precision's kernel
         for (request *r : cand) {
+            if (r->prec != prec) continue;
             if (budget <= 0 || (int)pick.size() >= S->cfg.max_active) break;
             const int64_t take = std::min<int64_t>(budget, r->job.n_items - r->next_item);
             pick.push_back({r, take});
@@ -529,7 +540,7 @@ static bool launch_work(bt_server *S, launch_slot &L, int li) {
         a.pw = (const bt_pow *)S->pool;
         a.partials = (double2 *)S->pool;
         a.counter = L.d_counter;
-        le = bt_launch_exact(&a, S_PREC(S), S->grid, L.stream);
+        le = bt_launch_exact(&a, prec, prec == BT_PREC_FP64 ? S->ctx->grid64 : S->ctx->grid32, L.stream);
     }
     if (!le && nf) {
         // the other launches holding items of these requests are in flight on
@@ -537,7 +548,7 @@ static bool launch_work(bt_server *S, launch_slot &L, int li) {
         for (int o = 0; o < (int)S->slots.size() && !le; ++o)
             if (o != li && (wait_mask >> o & 1u)) le = (int)cudaStreamWaitEvent(L.stream, S->slots[o].done, 0);
         if (!le)
-            le = bt_launch_finalize(L.d_fin_jobs, S->d_prm, nf, (const double2 *)S->pool, 0, 1, S_PREC(S), L.d_out,
+            le = bt_launch_finalize(L.d_fin_jobs, S->d_prm, nf, (const double2 *)S->pool, 0, 1, prec, L.d_out,
                                     L.stream);
         if (!le) le = (int)cudaMemcpyAsync(L.h_out, L.d_out, sizeof(bt_result) * nf, cudaMemcpyDeviceToHost, L.stream);
     }
@@ -666,7 +677,8 @@ extern "C" bt_status bt_serve_replay(bt_ctx *ctx, const bt_server_cfg *cfg, cons
         std::thread submitter([&]() {
             for (int i = 0; i < n; ++i) {
                 std::this_thread::sleep_until(at(i));
-                if (bt_submit(S, &opts[i], &tickets[i]) != BT_OK) tickets[i] = 0;
+                if (bt_submit(S, &opts[i], cfg && cfg->use_fp64 ? BT_PREC_FP64 : BT_PREC_FP32_COMP, &tickets[i]) != BT_OK)
+                    tickets[i] = 0;
             }
         });
         submitter.join();

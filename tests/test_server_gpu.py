@@ -118,3 +118,24 @@ def test_submit_rejects_bad_options(bt, ctx):
         assert e.value.status == bt.BT_EINVAL
     finally:
         bt.bt_server_stop(srv)
+
+
+def test_mixed_precisions_in_one_server(bt, ctx):
+    """FP64 and FP32 requests interleaved: each result is bit-identical to
+    pricing it alone at its own precision."""
+    opts = _stream(40, 9, 14, 26)
+    precs = [bt.BT_PREC_FP64 if i % 3 == 0 else bt.BT_PREC_FP32_COMP for i in range(len(opts))]
+    srv = bt.bt_server_start(ctx.h, max_active=16, n_streams=3, max_items_per_launch=200)
+    try:
+        tickets = [bt.bt_submit(srv, o, p) for o, p in zip(opts, precs)]
+        got = [bt.bt_wait(srv, t, 120000) for t in tickets]
+    finally:
+        bt.bt_server_stop(srv)
+    for o, p, g in zip(opts, precs, got):
+        assert g["value"] == bt.bt_price_exact(ctx.h, [o], p)[0]["value"], (o, p)
+    with pytest.raises(bt.BtError):
+        srv2 = bt.bt_server_start(ctx.h)
+        try:
+            bt.bt_submit(srv2, opts[0], 7)
+        finally:
+            bt.bt_server_stop(srv2)

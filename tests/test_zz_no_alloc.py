@@ -37,7 +37,7 @@ def _noalloc(bt, opts, prec):
     out = np.zeros(len(a), dtype=bt.RESULT_DTYPE)
     st = bt.lib().bt_price_exact_noalloc(ctypes.c_void_p(a.ctypes.data), len(a), prec,
                                          ctypes.c_void_p(out.ctypes.data), None)
-    assert st == bt.BT_OK, bt.lib().bt_last_error().decode()
+    assert st == bt.BT_OK, bt.lib().bt_last_error(None).decode()
     return out
 
 
