@@ -38,7 +38,7 @@ typedef enum {
     BT_EBUDGET = 3,       /* the context's device byte budget would be exceeded */
     BT_ECUDA = 4,         /* a CUDA call failed (message carries its error)     */
     BT_ETIMEOUT = 5,      /* a bounded wait expired                             */
-    BT_EUNSUPPORTED = 6   /* valid input outside what this build supports      */
+    BT_EUNSUPPORTED = 6   /* valid input outside what the library supports    */
 } bt_status;
 
 /* Tree parametrisations (Section 2, assumptions A1-A3). */
@@ -124,9 +124,10 @@ bt_status bt_tree_params(const bt_option *opt, double *u, double *d, double *p);
  * immediately followed by the put of identical parameters (or the reverse) is
  * evaluated in one pass over the paths; each still counts its own 2^N paths.
  * out[0..n) receives the results in input order. Synchronous on `stream`.
- * Errors: BT_EINVAL (bad option, message names the index), BT_EUNSUPPORTED
- * (N > 40, or FP32_COMP with min(p,1-p) < 0.004, whose weights leave the FP32
- * range), BT_EBUDGET, BT_ECUDA. */
+ * Errors: BT_EINVAL (bad option, message names the index: N < 1 or N > 40,
+ * S0 <= 0, K < 0, T <= 0, sigma <= 0, p outside (0,1), u <= d, a non-finite
+ * value), BT_EUNSUPPORTED (FP32_COMP with min(p,1-p) < 0.004, whose weights
+ * leave the FP32 range), BT_EBUDGET, BT_ECUDA. */
 bt_status bt_price_exact(bt_ctx *ctx, const bt_option *opts, int32_t n, bt_precision prec,
                          bt_result *out, void *stream);
 

@@ -149,9 +149,7 @@ bt_status host_tree(const bt_option *o, double *u, double *d, double *p) {
 }
 
 bt_status validate_option(const bt_option *o, int idx, int max_n) {
-    if (o->N < 1 || o->N > max_n)
-        return bt_fail(o->N > max_n && max_n == BT_MAX_N_EXACT ? BT_EUNSUPPORTED : BT_EINVAL,
-                       "option %d: N=%d outside 1..%d", idx, o->N, max_n);
+    if (o->N < 1 || o->N > max_n) return bt_fail(BT_EINVAL, "option %d: N=%d outside 1..%d", idx, o->N, max_n);
     if (o->tree_kind < 0 || o->tree_kind > 2) return bt_fail(BT_EINVAL, "option %d: bad tree_kind %d", idx, o->tree_kind);
     if (o->payoff < 0 || o->payoff > 7) return bt_fail(BT_EINVAL, "option %d: bad payoff %d", idx, o->payoff);
     if (!finite_all(*o)) return bt_fail(BT_EINVAL, "option %d: non-finite input", idx);

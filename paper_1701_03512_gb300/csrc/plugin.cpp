@@ -264,8 +264,7 @@ extern "C" bt_status bt_price_exact_plugin(bt_ctx *ctx, const bt_payoff_plugin *
     for (int i = 0; i < n; ++i) {
         const bt_option &op = opts[i];
         if (op.N < 1 || op.N > BT_MAX_N_EXACT)
-            return bt_fail(op.N > BT_MAX_N_EXACT ? BT_EUNSUPPORTED : BT_EINVAL, "option %d: N=%d outside 1..%d", i,
-                           op.N, BT_MAX_N_EXACT);
+            return bt_fail(BT_EINVAL, "option %d: N=%d outside 1..%d", i, op.N, BT_MAX_N_EXACT);
         bt_status s = check_scalars(op, i);
         if (s != BT_OK) return s;
         double u = 0, d = 0, p = 0;

@@ -13,8 +13,7 @@ static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static bt_status validate_steps_option(const bt_option &o, const double *st, int idx, int prec) {
     if (o.N < 1 || o.N > BT_MAX_N_EXACT)
-        return bt_fail(o.N > BT_MAX_N_EXACT ? BT_EUNSUPPORTED : BT_EINVAL, "option %d: N=%d outside 1..%d", idx, o.N,
-                       BT_MAX_N_EXACT);
+        return bt_fail(BT_EINVAL, "option %d: N=%d outside 1..%d", idx, o.N, BT_MAX_N_EXACT);
     if (o.payoff < 0 || o.payoff > 7) return bt_fail(BT_EINVAL, "option %d: bad payoff %d", idx, o.payoff);
     if (!(std::isfinite(o.S0) && std::isfinite(o.K) && std::isfinite(o.rate) && std::isfinite(o.T)))
         return bt_fail(BT_EINVAL, "option %d: non-finite input", idx);
