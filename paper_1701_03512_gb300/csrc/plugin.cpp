@@ -177,6 +177,7 @@ static bt_status generic_run(bt_ctx *ctx, const bt_payoff_plugin *pl, const bt_o
         } else {
             J.param[0] = op.K;
             J.param[1] = (double)op.payoff;
+            J.param[2] = 1.0 / (double)op.N;
         }
         items += J.n_items;
         move_off[i] = 2 * b * o;  // J.moves is set once the device copy exists
