@@ -575,6 +575,30 @@ void orc_mc(const orc_model *m, int mb, int64_t Rm, uint64_t seed, uint32_t stre
     free(pre); free(prob); grid_free(&g);
 }
 
+/* One stratum z of the Partitioned estimator, with the same draws as orc_mc:
+ * its sample mean, unbiased sample variance and P(D_z). */
+void orc_mc_stratum(const orc_model *m, int mb, uint64_t z, int64_t Rm, uint64_t seed, uint32_t stream,
+                    double *mean, double *var, double *prob) {
+    grid_t g;
+    *mean = NAN; *var = NAN; *prob = NAN;
+    if (mb < 0 || mb > m->N || mb > 24 || Rm < 1 || (z >> mb) != 0 || grid_make(m, &g)) return;
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint64_t thr = orc_bernoulli_threshold(m->p);
+    pstate pre;
+    prefix_state(m, &g, mb, z, &pre);
+    double mu = 0.0, M2 = 0.0;
+    for (int64_t i = 0; i < Rm; ++i) {
+        double v = mc_draw(m, &g, &pre, mb, thr, (uint32_t)i, (uint32_t)z, stream, key);
+        double delta = v - mu;
+        mu += delta / (double)(i + 1);
+        M2 += delta * (v - mu);
+    }
+    *mean = mu;
+    *var = Rm > 1 ? M2 / (double)(Rm - 1) : 0.0;
+    *prob = pow(m->p, (double)pre.U) * pow(1.0 - m->p, (double)(mb - pre.U));
+    grid_free(&g);
+}
+
 /* Exact E[V|D_m] and Var[V|D_m] by enumerating the suffixes of every stratum. */
 void orc_stratum_moments(const orc_model *m, int mb, double *mean, double *var, double *prob) {
     grid_t g;

@@ -111,6 +111,10 @@ void orc_mc(const orc_model *m, int mb, int64_t Rm, uint64_t seed, uint32_t stre
             double *theta, double *var, double *stratum_mean, double *stratum_var,
             double *stratum_prob);
 
+/* One stratum z of orc_mc (same draws): mean, unbiased variance, P(D_z). */
+void orc_mc_stratum(const orc_model *m, int mb, uint64_t z, int64_t Rm, uint64_t seed, uint32_t stream,
+                    double *mean, double *var, double *prob);
+
 /* Exact conditional moments per stratum by enumeration (small N):
  * mean_m = E[V | D_m], var_m = Var[V | D_m], prob_m = P(D_m). */
 void orc_stratum_moments(const orc_model *m, int mb, double *mean, double *var, double *prob);

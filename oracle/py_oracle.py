@@ -76,6 +76,7 @@ def lib():
             L.orc_bernoulli_threshold.argtypes = [d]; L.orc_bernoulli_threshold.restype = u64
             L.orc_mc.argtypes = [pm, C.c_int, i64, u64, C.c_uint32, C.c_int, pd, pd, pd, pd, pd]
             L.orc_stratum_moments.argtypes = [pm, C.c_int, pd, pd, pd]
+            L.orc_mc_stratum.argtypes = [pm, C.c_int, u64, i64, u64, C.c_uint32, pd, pd, pd]
             L.orc_greeks_crr.argtypes = [C.c_int, C.c_int, d, d, d, d, d, pd]
             L.orc_greeks_crr.restype = d
             ps = C.POINTER(StepsModel)
@@ -285,3 +286,10 @@ def branch_european_backward(o: dict, moves, b: int) -> float:
 def branch_path_prob(o: dict, moves, b: int, idx: int) -> float:
     m, keep = branch_model(o, moves, b)
     return lib().orc_branch_path_prob(C.byref(m), idx)
+
+
+def mc_stratum(o: dict, mb: int, z: int, Rm: int, seed: int, stream: int = 0):
+    """(mean, unbiased variance, P(D_z)) of one stratum, the same draws as mc()."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    lib().orc_mc_stratum(C.byref(model(o)), mb, z, Rm, seed, stream, C.byref(a), C.byref(b), C.byref(c))
+    return a.value, b.value, c.value

@@ -162,3 +162,20 @@ def test_strata_shards_add_up(bt, ctx, n_shards):
     assert abs(v - full[0]["value"]) <= 1e-13 * full[0]["value"]
     assert abs(np.sqrt(se2) - full[0]["stderr_mc"]) <= 1e-12 * full[0]["stderr_mc"]
     assert paths == full[0]["paths"]
+
+
+def test_full_size_strata_sampled_against_the_oracle(bt, ctx, oracle):
+    """The benchmark's Monte Carlo configuration at full size (N=252, 2^16
+    strata x 2^14 samples): sampled strata recomputed one by one by the
+    oracle with the same Philox draws. The GPU walks the 236 suffix steps in
+    FP32, so the stratum means agree to about 1e-5, not bit for bit."""
+    o = W.opt(252, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
+    mb, R, seed = 16, 1 << 14, 5
+    r, st = bt.bt_price_mc_ex(ctx.h, [o], mb, R, seed, with_strata=True)
+    assert r[0]["paths"] == R << mb
+    for z in (0, 1, 4660, 32768, 65535):
+        mz, vz, pz = oracle.mc_stratum(o, mb, z, R, seed)
+        g_mean, g_var, g_prob = st[0][z]
+        assert abs(g_mean - mz) <= 1e-4 * abs(mz) + 1e-6 * o["S0"], (z, g_mean, mz)
+        assert abs(g_var - vz) <= 1e-3 * vz + 1e-9, (z, g_var, vz)
+        assert abs(g_prob - pz) <= 1e-12 * pz, (z, g_prob, pz)

@@ -485,3 +485,12 @@ def test_branch_zero_strike_closed_forms(oracle):
     for pay, v in ((W.EURO_CALL, 100.0 * np.prod(g)), (W.ASIAN_ARITH_CALL, 100.0 / N * np.sum(np.cumprod(g)))):
         o = W.opt(N, 100.0, 0.0, 0.02, 0.2, 1.0, pay)
         assert oracle.branch_price(o, moves, 3, 4) == pytest.approx(disc * v, rel=1e-13)
+
+
+def test_mc_single_stratum_matches_the_full_run(oracle):
+    """orc_mc_stratum reproduces orc_mc's per-stratum statistics exactly."""
+    o = W.opt(40, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
+    th, var, mean, sv, pr = oracle.mc(o, 5, 300, 17, 0, False, True)
+    for z in (0, 7, 31):
+        mz, vz, pz = oracle.mc_stratum(o, 5, z, 300, 17)
+        assert (mz, vz, pz) == (mean[z], sv[z], pr[z])
