@@ -406,6 +406,17 @@ def extras_bench(bt, W, ctx, sms, fmax):
     out["generic_binomial"] = {"workload": "generic pass (FP64 path walk), arithmetic Asian and lookback calls, "
                                            "N=28, 2 x 2^28 paths", "ms": 1e3 * t,
                                "payoff_paths_per_s": 2 * 2.0 ** N2 / t}
+    # trinomial trees through the affine pass (prefix/suffix tables, FP32), N=22: 8 x 3^22 paths
+    N4 = 22
+    o4 = [W.opt(N4, 100.0, 90.0 + 5 * (i % 4), 0.03, 0.2, 1.0, pay)
+          for i, pay in enumerate([W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT] * 4)]
+    mv4 = [W.branch_moves(800 + i, N4, 3, 0.01, 0.05) for i in range(len(o4))]
+    t = _timed(lambda: bt.bt_price_exact_moves(ctx.h, o4, 3, mv4, bt.BT_PREC_FP32_COMP))
+    paths4 = len(o4) * 3.0 ** N4
+    out["trinomial_affine"] = {"workload": "trinomial trees (per-step moves), arithmetic Asian call/put, N=22, "
+                                           "8 x 3^22 paths, FP32_COMP, host arrays in and out",
+                               "ms": 1e3 * t, "payoff_paths_per_s": paths4 / t,
+                               "frac_of_issue_peak": 3 * paths4 / t / peak}
     N3 = 17
     o3 = [W.opt(N3, 100.0, 100.0, 0.05, 0.2, 1.0, pay) for pay in (W.ASIAN_ARITH_CALL, W.LOOKBACK_FIXED_CALL)]
     mv3 = [W.branch_moves(3, N3, 3), W.branch_moves(4, N3, 3)]

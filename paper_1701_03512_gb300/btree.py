@@ -113,6 +113,7 @@ def lib():
         _proto(L, "bt_price_mc", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _vp, _vp])
         _proto(L, "bt_price_mc_ex", [_vp, _vp, _i32, _i32, _i64, C.c_uint64, _i32, _vp, _vp, _vp])
         _proto(L, "bt_price_exact_steps", [_vp, _vp, _i32, _vp, C.c_int, _vp, _vp])
+        _proto(L, "bt_price_exact_moves", [_vp, _vp, _i32, _i32, _vp, C.c_int, _vp, _vp])
         _proto(L, "bt_plugin_compile", [_vp, C.c_char_p, C.c_char_p, C.c_size_t, C.POINTER(_vp)])
         _proto(L, "bt_price_exact_plugin", [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp])
         L.bt_plugin_destroy.argtypes = [_vp]
@@ -338,6 +339,21 @@ def bt_price_exact_branching(ctx, opts, branches, moves, plugin=None, params=Non
     _check(lib().bt_price_exact_branching(ctx, plugin, a.ctypes.data, len(a), branches, mv.ctypes.data,
                                           None if pr is None else pr.ctypes.data, out.ctypes.data,
                                           _stream(stream)))
+    return out
+
+
+def bt_price_exact_moves(ctx, opts, branches, moves, prec=BT_PREC_FP32_COMP, stream=None) -> np.ndarray:
+    """Affine passes on trees with `branches` branches per node; moves as for
+    bt_price_exact_branching."""
+    a = options_array(opts)
+    if isinstance(moves, (list, tuple)):
+        moves = np.concatenate([np.asarray(m, dtype=np.float64).reshape(-1, 2 * branches) for m in moves])
+    mv = np.ascontiguousarray(np.asarray(moves, dtype=np.float64).reshape(-1, 2 * branches))
+    if mv.shape[0] != int(a["N"].sum()):
+        raise ValueError("moves holds %d steps, the options need %d" % (mv.shape[0], int(a["N"].sum())))
+    out = np.zeros(len(a), dtype=RESULT_DTYPE)
+    _check(lib().bt_price_exact_moves(ctx, a.ctypes.data, len(a), branches, mv.ctypes.data, prec, out.ctypes.data,
+                                      _stream(stream)))
     return out
 
 

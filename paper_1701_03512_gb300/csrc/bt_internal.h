@@ -46,6 +46,10 @@ struct bt_job {
     int64_t off_suf;          // element offset in the suffix arena
     int64_t off_ph, off_pm;   // entry offsets in the prefix-table arena
     int64_t off_pow, off_geo; // entry offsets in the power-table arena
+    // trees given move by move (steps.cu): branches per node and the number of
+    // prefixes, middle-block prefixes and suffixes (b^P, b^M, b^L)
+    int32_t branches, pad2;
+    int64_t n_prefix, n_mid, n_suffix;
 };
 
 struct bt_pentry {            // one entry of a two-level prefix table

@@ -1,7 +1,10 @@
-// Time-varying trees: eq. f13 with per-step moves and probabilities, sm_103a.
+// Trees given move by move: eq. f13 with per-step moves and probabilities, and
+// b branches per node (the end of Section 3), sm_103a.
 //
-// Step t multiplies the price by u_t (up, probability p_t) or by d_t; the
-// tree need not recombine, so every path is evaluated. The prefix/suffix
+// Step t multiplies the price by factor k of that step with probability k
+// (digit k = 0..b-1; a time-varying binomial tree is b = 2 with digit 1 = up);
+// the tree need not recombine, so every path is evaluated. A path index is N
+// digits in base b, the first step most significant. The prefix/suffix
 // split of exact.cu still applies, because the suffix steps sit at the same
 // positions P+1..N under every prefix: with rho_j(s) = S_{P+j}/S_P the
 // suffix's relative prices, each payoff is beta_q max(+-(tau_q + f_s), 0) + C_q
@@ -19,10 +22,12 @@
 // rounding design of exact.cu (scaled affine form, exact lambda f_hi + A_hi,
 // one rounding per payoff); the weight enters as w_hi z + w_lo z.
 //
-// A job reuses bt_job: off_pow is the index of its first step in the step
-// array (three doubles per step: u, d, p), off_ph and off_pm index the
-// bt_spentry arena, off_suf the suffix arena (4 floats or 2 doubles per
-// entry), suf_len counts entries (2^L, at least 8; padding has weight 0).
+// A job reuses bt_job: off_pow is the index of its first step in the move
+// array (2b doubles per step: the b factors, then the b probabilities),
+// off_ph and off_pm index the bt_spentry arena, off_suf the suffix arena (4
+// floats or 2 doubles per entry), suf_len counts entries (b^L rounded up to a
+// multiple of 8; padding has weight 0); n_prefix, n_mid, n_suffix are b^P,
+// b^M and b^L.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -37,33 +42,44 @@ struct sblock {
     double rho, R, sum, mx, mn, lg, w;
 };
 
-// Walks `bits` steps of x (MSB first) whose moves are st[3 (t-1) + 0/1/2] =
-// (u, d, p): end factor rho = S_end/S_start, backward-relative partial sum
-// R = sum_t S_t/S_end, forward-relative sum sum_t S_t/S_start, extreme
-// relative prices, sum of ln(S_t/S_start) and the block's weight.
-__device__ static sblock walk_steps(uint64_t x, int bits, const double *st) {
-    sblock b;
+// Walks `nd` steps of x (base-b digits, the first step most significant)
+// whose moves are st[2b (t-1) + k] (factor of digit k) and st[2b (t-1) + b + k]
+// (its probability); ext < 0 / > 0 takes every step's smallest / largest
+// factor instead. Returns the end factor rho = S_end/S_start, the
+// backward-relative partial sum R = sum_t S_t/S_end, the forward-relative sum
+// sum_t S_t/S_start, extreme relative prices, sum of ln(S_t/S_start) and the
+// block's weight.
+__device__ static sblock walk_steps(uint64_t x, int nd, int b, const double *st, int ext = 0) {
+    sblock blk;
     double rel = 1.0, R = 0.0, sum = 0.0, mx = 0.0, mn = BT_SBIG, lg = 0.0, w = 1.0;
-    for (int t = 1; t <= bits; ++t) {
-        const bool up = (x >> (bits - t)) & 1u;
-        const double m = up ? st[3 * (t - 1)] : st[3 * (t - 1) + 1];
-        const double p = st[3 * (t - 1) + 2];
+    uint64_t place = 1;
+    for (int t = 1; t < nd; ++t) place *= (uint64_t)b;
+    for (int t = 1; t <= nd; ++t, place /= (uint64_t)b) {
+        const double *mv = st + 2 * b * (t - 1);
+        int k = (int)((x / place) % (uint64_t)b);
+        if (ext != 0) {
+            k = 0;
+            for (int j = 1; j < b; ++j)
+                if (ext > 0 ? mv[j] > mv[k] : mv[j] < mv[k]) k = j;
+        }
+        const double m = mv[k];
+        const double p = mv[b + k];
         rel *= m;
         R = R / m + 1.0;
         sum += rel;
         mx = fmax(mx, rel);
         mn = fmin(mn, rel);
         lg += log(rel);
-        w *= up ? p : 1.0 - p;
+        w *= p;
     }
-    b.rho = rel;
-    b.R = R;
-    b.sum = sum;
-    b.mx = mx;
-    b.mn = mn;
-    b.lg = lg;
-    b.w = w;
-    return b;
+    blk.rho = rel;
+    blk.R = R;
+    blk.sum = sum;
+    blk.mx = mx;
+    blk.mn = mn;
+    blk.lg = lg;
+    blk.w = w;
+    return blk;
 }
 
 // f_s of a suffix block for the job's field.
@@ -77,8 +93,9 @@ __device__ static double suffix_f(int field, const sblock &b, int N) {
     }
 }
 
-// a1 for time-varying jobs: scalars and the suffix f range (every f_s is
-// non-decreasing in each step's move, so all-down and all-up bound it).
+// a1 for move-by-move jobs: scalars and the suffix f range (every f_s is
+// non-decreasing in each step's factor, so the smallest and the largest
+// factors of every step bound it).
 __global__ void k_steps_params(const bt_option *opts, const bt_job *jobs, const double *steps, bt_jparams *prm,
                                int n_jobs) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -94,9 +111,10 @@ __global__ void k_steps_params(const bt_option *opts, const bt_job *jobs, const 
     P.NKoS0 = (double)J.N * o.K / o.S0;
     P.KoS0 = o.K / o.S0;
     P.S0oN = o.S0 / (double)J.N;
-    const double *st = steps + 3 * (J.off_pow + J.P);
-    P.fmin = suffix_f(J.field, walk_steps(0, J.L, st), J.N);
-    P.fmax = suffix_f(J.field, walk_steps((1ull << J.L) - 1, J.L, st), J.N);
+    const int b = J.branches;
+    const double *st = steps + 2 * b * (J.off_pow + J.P);
+    P.fmin = suffix_f(J.field, walk_steps(0, J.L, b, st, -1), J.N);
+    P.fmax = suffix_f(J.field, walk_steps(0, J.L, b, st, +1), J.N);
     P.NKoS0_2 = split2(P.NKoS0);
     P.KoS0_2 = split2(P.KoS0);
     P.S0oN_2 = split2(P.S0oN);
@@ -139,8 +157,9 @@ __global__ void k_steps_tables(const bt_job *jobs, const bt_jparams *prm, const 
                                float4 *suf32, double2 *suf64, bt_spentry *tab) {
     const bt_job J = jobs[blockIdx.y];
     const bt_jparams &Pj = prm[J.prm_off];
-    const double *st = steps + 3 * J.off_pow;
-    const int64_t nsuf = 1ll << J.L, nh = 1ll << J.H, nm = 1ll << J.M;
+    const int b = J.branches;
+    const double *st = steps + 2 * b * J.off_pow;
+    const int64_t nsuf = J.n_suffix, nh = J.n_prefix / J.n_mid, nm = J.n_mid;
     const int64_t total = J.suf_len + nh + nm;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -148,9 +167,9 @@ __global__ void k_steps_tables(const bt_job *jobs, const bt_jparams *prm, const 
         if (i < J.suf_len) {
             double f = 0.0, w = 0.0;  // padding: weight 0
             if (i < nsuf) {
-                const sblock b = walk_steps((uint64_t)i, J.L, st + 3 * J.P);
-                f = suffix_f(J.field, b, J.N);
-                w = b.w;
+                const sblock s = walk_steps((uint64_t)i, J.L, b, st + 2 * b * J.P);
+                f = suffix_f(J.field, s, J.N);
+                w = s.w;
             }
             if (prec == BT_PREC_FP64) {
                 suf64[J.off_suf + i] = make_double2(f, w);
@@ -164,15 +183,15 @@ __global__ void k_steps_tables(const bt_job *jobs, const bt_jparams *prm, const 
         }
         i -= J.suf_len;
         if (i < nh) {
-            const sblock b = walk_steps((uint64_t)i, J.H, st);
-            const double e = exp((b.lg + (double)(J.M + J.L) * log(b.rho)) / (double)J.N);
-            tab[J.off_ph + i] = make_spentry(b, e);
+            const sblock s = walk_steps((uint64_t)i, J.H, b, st);
+            const double e = exp((s.lg + (double)(J.M + J.L) * log(s.rho)) / (double)J.N);
+            tab[J.off_ph + i] = make_spentry(s, e);
             continue;
         }
         i -= nh;
-        const sblock b = walk_steps((uint64_t)i, J.M, st + 3 * J.H);
-        const double e = exp((b.lg + (double)J.L * log(b.rho)) / (double)J.N);
-        tab[J.off_pm + i] = make_spentry(b, e);
+        const sblock s = walk_steps((uint64_t)i, J.M, b, st + 2 * b * J.H);
+        const double e = exp((s.lg + (double)J.L * log(s.rho)) / (double)J.N);
+        tab[J.off_pm + i] = make_spentry(s, e);
     }
 }
 
@@ -182,8 +201,8 @@ struct sstate {
 };
 __device__ __forceinline__ sstate steps_state(const bt_job &J, const bt_jparams &P, const bt_spentry *tab,
                                               int64_t q) {
-    const bt_spentry &eh = tab[J.off_ph + (q >> J.M)];
-    const bt_spentry &em = tab[J.off_pm + (q & ((1ll << J.M) - 1))];
+    const bt_spentry &eh = tab[J.off_ph + q / J.n_mid];
+    const bt_spentry &em = tab[J.off_pm + q % J.n_mid];
     sstate r;
     const df32 rho_h = df_from2(eh.rho2), rho_m = df_from2(em.rho2);
     const df32 ir = df_mul(df_from2(eh.irho2), df_from2(em.irho2));  // S0 / S_P
@@ -267,7 +286,7 @@ __device__ __forceinline__ void item_steps32(const bt_exact_args &a, const smem_
     const bt_jparams &P = sj.P;
     const int64_t item_local = sj.item - J.item_begin + J.item_offset;
     const int64_t qbase = item_local << BT_LOW_BITS;
-    const int64_t nP = 1ll << J.P;
+    const int64_t nP = J.n_prefix;
     float B[BT_PT], Ah[BT_PT], nAl[BT_PT];
 #pragma unroll
     for (int j = 0; j < BT_PT; ++j) {
@@ -333,7 +352,7 @@ __device__ __forceinline__ void item_steps64(const bt_exact_args &a, const smem_
     const bt_jparams &P = sj.P;
     const int64_t item_local = sj.item - J.item_begin + J.item_offset;
     const int64_t qbase = item_local << BT_LOW_BITS;
-    const int64_t nP = 1ll << J.P;
+    const int64_t nP = J.n_prefix;
     double tau[BT_PT64], om[BT_PT64], cst = 0.0;
 #pragma unroll
     for (int j = 0; j < BT_PT64; ++j) {
@@ -341,8 +360,8 @@ __device__ __forceinline__ void item_steps64(const bt_exact_args &a, const smem_
         tau[j] = nan("");
         om[j] = 0.0;
         if (q >= nP) continue;
-        const bt_spentry &eh = tab[J.off_ph + (q >> J.M)];
-        const bt_spentry &em = tab[J.off_pm + (q & ((1ll << J.M) - 1))];
+        const bt_spentry &eh = tab[J.off_ph + q / J.n_mid];
+        const bt_spentry &em = tab[J.off_pm + q % J.n_mid];
         const double ir = eh.irho * em.irho, sp = eh.rho * em.rho, w = eh.w * em.w;
         double beta = P.S0 * sp, c = 0.0;
         switch (J.field) {

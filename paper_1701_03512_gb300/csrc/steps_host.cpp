@@ -1,5 +1,6 @@
-// Host runtime of the time-varying tree pass (eq. f13 with per-step u_t, d_t,
-// p_t): validation, plan, one allocation, launches, results.
+// Host runtime of the move-by-move passes: time-varying binomial trees
+// (eq. f13 with per-step u_t, d_t, p_t) and trees with b branches per node
+// (the end of Section 3). Validation, plan, one allocation, launches, results.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -11,36 +12,49 @@
 
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static bt_status validate_steps_option(const bt_option &o, const double *st, int idx, int prec) {
-    if (o.N < 1 || o.N > BT_MAX_N_EXACT)
-        return bt_fail(BT_EINVAL, "option %d: N=%d outside 1..%d", idx, o.N, BT_MAX_N_EXACT);
+static bt_status validate_scalars(const bt_option &o, int idx) {
+    if (o.N < 1 || o.N > BT_MAX_N_EXACT) return bt_fail(BT_EINVAL, "option %d: N=%d outside 1..%d", idx, o.N, BT_MAX_N_EXACT);
     if (o.payoff < 0 || o.payoff > 7) return bt_fail(BT_EINVAL, "option %d: bad payoff %d", idx, o.payoff);
     if (!(std::isfinite(o.S0) && std::isfinite(o.K) && std::isfinite(o.rate) && std::isfinite(o.T)))
         return bt_fail(BT_EINVAL, "option %d: non-finite input", idx);
     if (!(o.S0 > 0.0)) return bt_fail(BT_EINVAL, "option %d: S0 must be > 0", idx);
     if (!(o.K >= 0.0)) return bt_fail(BT_EINVAL, "option %d: K must be >= 0", idx);
     if (!(o.T > 0.0)) return bt_fail(BT_EINVAL, "option %d: T must be > 0", idx);
-    for (int t = 0; t < o.N; ++t) {
-        const double u = st[3 * t], d = st[3 * t + 1], p = st[3 * t + 2];
-        if (!(std::isfinite(u) && std::isfinite(d) && std::isfinite(p) && d > 0.0 && u > d && p > 0.0 && p < 1.0))
-            return bt_fail(BT_EINVAL, "option %d step %d: needs 0 < d < u and 0 < p < 1", idx, t + 1);
-        if (prec == BT_PREC_FP32_COMP && std::min(p, 1.0 - p) < 0.004)
-            return bt_fail(BT_EUNSUPPORTED, "option %d step %d: p = %.6g; FP32_COMP needs min(p,1-p) >= 0.004",
-                           idx, t + 1, p);
+    return BT_OK;
+}
+
+// One option's moves (2b doubles per step): factors > 0, probabilities in
+// [0,1] summing to 1; FP32_COMP keeps every positive probability >= 0.004.
+static bt_status validate_moves(const double *mv, int N, int b, int idx, int prec) {
+    for (int t = 0; t < N; ++t) {
+        const double *m = mv + 2 * b * t;
+        double psum = 0.0;
+        for (int k = 0; k < b; ++k) {
+            if (!(std::isfinite(m[k]) && m[k] > 0.0 && m[b + k] >= 0.0 && m[b + k] <= 1.0))
+                return bt_fail(BT_EINVAL, "option %d step %d: factors must be > 0, probabilities in [0,1]", idx, t + 1);
+            if (prec == BT_PREC_FP32_COMP && m[b + k] > 0.0 && m[b + k] < 0.004)
+                return bt_fail(BT_EUNSUPPORTED, "option %d step %d: probability %.6g; FP32_COMP needs >= 0.004", idx,
+                               t + 1, m[b + k]);
+            psum += m[b + k];
+        }
+        if (std::fabs(psum - 1.0) > 1e-12)
+            return bt_fail(BT_EINVAL, "option %d step %d: probabilities sum to %.17g", idx, t + 1, psum);
     }
     return BT_OK;
 }
 
-extern "C" bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, int32_t n, const double *steps,
-                                          bt_precision prec, bt_result *out, void *stream) {
-    if (!ctx || !opts || !steps || !out || n < 1) return bt_fail(BT_EINVAL, "bt_price_exact_steps: bad arguments");
+static bt_status price_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int b, const double *moves,
+                             bt_precision prec, bt_result *out, void *stream) {
     if (prec != BT_PREC_FP64 && prec != BT_PREC_FP32_COMP) return bt_fail(BT_EINVAL, "bad precision %d", (int)prec);
     std::vector<bt_job> jobs((size_t)n);
     int64_t items = 0, suf = 0, tab = 0, nsteps = 0;
     int max_len = 0;
     for (int i = 0; i < n; ++i) {
-        bt_status s = validate_steps_option(opts[i], steps + 3 * nsteps, i, prec);
+        bt_status s = validate_scalars(opts[i], i);
         if (s != BT_OK) return s;
+        if ((double)opts[i].N * std::log2((double)b) > 42.0 + 1e-9)
+            return bt_fail(BT_EUNSUPPORTED, "option %d: %d^%d paths exceed 2^42", i, b, opts[i].N);
+        if ((s = validate_moves(moves + 2 * b * nsteps, opts[i].N, b, i, prec)) != BT_OK) return s;
         bt_job &J = jobs[i];
         memset(&J, 0, sizeof(J));
         int field, mode;
@@ -49,34 +63,49 @@ extern "C" bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, in
         J.out_call = mode == BT_MODE_CALL ? i : -1;
         J.out_put = mode == BT_MODE_PUT ? i : -1;
         J.N = opts[i].N;
-        J.L = exact_split_L(J.N);
-        J.P = J.N - J.L;
+        J.branches = b;
+        // suffix steps: b^L <= 2^12 entries in shared memory (binomial: the lattice pass's split)
+        int L = 0;
+        int64_t nsuf = 1;
+        while (L < J.N && nsuf * b <= (1 << BT_MAX_L) && (b > 2 || L < exact_split_L(J.N))) {
+            nsuf *= b;
+            ++L;
+        }
+        J.L = L;
+        J.P = J.N - L;
         J.M = (J.P + 1) / 2;
         J.H = J.P - J.M;
+        int64_t nmid = 1, npre = 1;
+        for (int t = 0; t < J.M; ++t) nmid *= b;
+        for (int t = 0; t < J.P; ++t) npre *= b;
+        J.n_suffix = nsuf;
+        J.n_mid = nmid;
+        J.n_prefix = npre;
         J.field = field;
         J.mode = mode;
-        J.suf_len = std::max(BT_UNROLL, 1 << J.L);   // entries; padding has weight 0
+        J.suf_len = (int32_t)((nsuf + BT_UNROLL - 1) / BT_UNROLL * BT_UNROLL);   // entries; padding has weight 0
         for (int k = 0; k < BT_MAX_L + 2; ++k) J.goff[k] = k == 0 ? 0 : J.suf_len;
-        J.n_items = (int32_t)std::max<int64_t>(1, ((1ll << J.P) + (1 << BT_LOW_BITS) - 1) >> BT_LOW_BITS);
+        J.n_items = (int32_t)std::max<int64_t>(1, (npre + (1 << BT_LOW_BITS) - 1) >> BT_LOW_BITS);
         J.item_begin = items;
         J.item_offset = 0;
         J.part_off = items;
         J.prm_off = i;
         J.off_suf = suf;
         J.off_ph = tab;
-        J.off_pm = tab + (1ll << J.H);
-        J.off_pow = nsteps;   // first step of this job in the step array
+        J.off_pm = tab + npre / nmid;
+        J.off_pow = nsteps;   // first step of this job in the move array
         items += J.n_items;
         suf += J.suf_len;
-        tab += (1ll << J.H) + (1ll << J.M);
+        tab += npre / nmid + nmid;
         nsteps += J.N;
-        max_len = std::max(max_len, (int)(J.suf_len + (1ll << J.H) + (1ll << J.M)));
+        max_len = std::max(max_len, (int)(J.suf_len + npre / nmid + nmid));
     }
+    if (items > ((int64_t)1 << 31)) return bt_fail(BT_EUNSUPPORTED, "%lld work items", (long long)items);
     size_t off = 0;
     const size_t o_opts = off; off = up256(off + sizeof(bt_option) * n);
     const size_t o_jobs = off; off = up256(off + sizeof(bt_job) * n);
     const size_t o_prm = off; off = up256(off + sizeof(bt_jparams) * n);
-    const size_t o_steps = off; off = up256(off + sizeof(double) * 3 * nsteps);
+    const size_t o_steps = off; off = up256(off + sizeof(double) * 2 * b * nsteps);
     const size_t o_suf = off; off = up256(off + 16 * (size_t)suf);   // float4 or double2 entries
     const size_t o_tab = off; off = up256(off + sizeof(bt_spentry) * tab);
     const size_t o_part = off; off = up256(off + sizeof(double2) * items);
@@ -86,29 +115,29 @@ extern "C" bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, in
     void *arena = nullptr;
     bt_status rs = ctx_alloc(ctx, off, &arena);
     if (rs != BT_OK) return rs;
-    char *b = (char *)arena;
-    bt_option *d_opts = (bt_option *)(b + o_opts);
-    bt_job *d_jobs = (bt_job *)(b + o_jobs);
-    bt_jparams *d_prm = (bt_jparams *)(b + o_prm);
-    double *d_steps = (double *)(b + o_steps);
-    bt_spentry *d_tab = (bt_spentry *)(b + o_tab);
-    double2 *d_part = (double2 *)(b + o_part);
-    bt_result *d_out = (bt_result *)(b + o_out);
-    unsigned long long *d_cnt = (unsigned long long *)(b + o_cnt);
+    char *base = (char *)arena;
+    bt_option *d_opts = (bt_option *)(base + o_opts);
+    bt_job *d_jobs = (bt_job *)(base + o_jobs);
+    bt_jparams *d_prm = (bt_jparams *)(base + o_prm);
+    double *d_steps = (double *)(base + o_steps);
+    bt_spentry *d_tab = (bt_spentry *)(base + o_tab);
+    double2 *d_part = (double2 *)(base + o_part);
+    bt_result *d_out = (bt_result *)(base + o_out);
+    unsigned long long *d_cnt = (unsigned long long *)(base + o_cnt);
     cudaStream_t st = ctx_stream(ctx, stream);
     cudaError_t e = cudaMemcpyAsync(d_opts, opts, sizeof(bt_option) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(bt_job) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_steps, steps, sizeof(double) * 3 * nsteps, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(d_steps, moves, sizeof(double) * 2 * b * nsteps, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_part, 0, sizeof(double2) * items, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) rs = bt_cuda_fail(e, "bt_price_exact_steps: upload");
+    if (e != cudaSuccess) rs = bt_cuda_fail(e, "move-by-move pass: upload");
     int le = 0;
     if (rs == BT_OK && (le = bt_launch_steps_params(d_opts, d_jobs, d_steps, d_prm, n, st)))
-        rs = bt_cuda_fail(le, "steps params kernel");
-    if (rs == BT_OK && (le = bt_launch_steps_tables(d_jobs, d_prm, d_steps, n, max_len, prec, (float4 *)(b + o_suf),
-                                                    (double2 *)(b + o_suf), d_tab, st)))
-        rs = bt_cuda_fail(le, "steps tables kernel");
+        rs = bt_cuda_fail(le, "params kernel");
+    if (rs == BT_OK && (le = bt_launch_steps_tables(d_jobs, d_prm, d_steps, n, max_len, prec, (float4 *)(base + o_suf),
+                                                    (double2 *)(base + o_suf), d_tab, st)))
+        rs = bt_cuda_fail(le, "tables kernel");
     if (rs == BT_OK) {
         bt_exact_args a;
         memset(&a, 0, sizeof(a));
@@ -119,20 +148,53 @@ extern "C" bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, in
         a.shard = 0;
         a.n_shards = 1;
         a.n_run_items = items;
-        a.suf32 = (const float2 *)(b + o_suf);
-        a.suf64 = (const double *)(b + o_suf);
+        a.suf32 = (const float2 *)(base + o_suf);
+        a.suf64 = (const double *)(base + o_suf);
         a.partials = d_part;
         a.counter = d_cnt;
-        if ((le = bt_launch_steps(&a, d_tab, prec, ctx->device, st))) rs = bt_cuda_fail(le, "steps path-sum kernel");
+        if ((le = bt_launch_steps(&a, d_tab, prec, ctx->device, st))) rs = bt_cuda_fail(le, "path-sum kernel");
     }
     if (rs == BT_OK && (le = bt_launch_finalize(d_jobs, d_prm, n, d_part, 0, 1, prec, d_out, st)))
         rs = bt_cuda_fail(le, "finalize kernel");
     if (rs == BT_OK) {
         e = cudaMemcpyAsync(out, d_out, sizeof(bt_result) * n, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rs = bt_cuda_fail(e, "bt_price_exact_steps: results");
+        if (e != cudaSuccess) rs = bt_cuda_fail(e, "move-by-move pass: results");
     }
     cudaStreamSynchronize(st);
     ctx_free(ctx, arena, off);
+    if (rs == BT_OK)
+        for (int i = 0; i < n; ++i) {  // b^N paths (finalize wrote 2^N)
+            long long paths = 1;
+            for (int t = 0; t < opts[i].N; ++t) paths *= b;
+            out[i].paths = paths;
+        }
     return rs;
+}
+
+extern "C" bt_status bt_price_exact_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t branches,
+                                          const double *moves, bt_precision prec, bt_result *out, void *stream) {
+    if (!ctx || !opts || !moves || !out || n < 1) return bt_fail(BT_EINVAL, "bt_price_exact_moves: bad arguments");
+    if (branches < 2 || branches > 8) return bt_fail(BT_EINVAL, "branches = %d outside 2..8", branches);
+    return price_moves(ctx, opts, n, branches, moves, prec, out, stream);
+}
+
+extern "C" bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, int32_t n, const double *steps,
+                                          bt_precision prec, bt_result *out, void *stream) {
+    if (!ctx || !opts || !steps || !out || n < 1) return bt_fail(BT_EINVAL, "bt_price_exact_steps: bad arguments");
+    // (u_t, d_t, p_t) -> binomial moves in digit order: factors (d, u), probabilities (1 - p, p)
+    std::vector<double> mv;
+    int64_t o = 0;
+    for (int i = 0; i < n; ++i) {
+        if (opts[i].N < 1 || opts[i].N > BT_MAX_N_EXACT)
+            return bt_fail(BT_EINVAL, "option %d: N=%d outside 1..%d", i, opts[i].N, BT_MAX_N_EXACT);
+        for (int t = 0; t < opts[i].N; ++t) {
+            const double u = steps[3 * (o + t)], d = steps[3 * (o + t) + 1], p = steps[3 * (o + t) + 2];
+            if (!(std::isfinite(u) && std::isfinite(d) && std::isfinite(p) && d > 0.0 && u > d && p > 0.0 && p < 1.0))
+                return bt_fail(BT_EINVAL, "option %d step %d: needs 0 < d < u and 0 < p < 1", i, t + 1);
+            mv.insert(mv.end(), {d, u, 1.0 - p, p});
+        }
+        o += opts[i].N;
+    }
+    return price_moves(ctx, opts, n, 2, mv.data(), prec, out, stream);
 }

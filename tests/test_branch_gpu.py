@@ -99,3 +99,58 @@ def test_invalid_moves(bt, ctx):
     with pytest.raises(bt.BtError) as e:
         bt.bt_price_exact_branching(ctx.h, [dict(o, N=31)], 3, [W.branch_moves(1, 31, 3)])
     assert e.value.status == bt.BT_EUNSUPPORTED
+
+
+def _tol(prec, paths):
+    """FP64 1e-12; FP32_COMP by the number of paths the per-path roundings
+    average over: 1e-9 from 2^28, 3e-9 from 2^20, 5e-8 from 2^12, 3e-7 below."""
+    if prec == 0:
+        return 1e-12
+    n = math.log2(paths)
+    return 1e-9 if n >= 28 else 3e-9 if n >= 20 else 5e-8 if n >= 12 else 3e-7
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("b,N", [(3, 1), (3, 9), (3, 13), (4, 8), (5, 7)])
+def test_affine_moves_pass_against_the_oracle(bt, ctx, oracle, prec, b, N):
+    """bt_price_exact_moves (the prefix/suffix tables and per-suffix weights of
+    the time-varying pass, in base b) on non-recombining trees."""
+    opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for pay in range(8) for K in (96.0, 104.0)]
+    moves = [W.branch_moves(31 * N + i + b, N, b) for i in range(len(opts))]
+    got = bt.bt_price_exact_moves(ctx.h, opts, b, moves, prec)
+    for o, m, g in zip(opts, moves, got):
+        ref = oracle.branch_price(o, m, b, 8)
+        assert abs(g["value"] - ref) <= _tol(prec, b ** N) * abs(ref) + 1e-12 * o["S0"], (prec, o, g["value"], ref)
+        assert g["paths"] == b ** N
+
+
+def test_affine_moves_large_trinomial_fp32_against_fp64(bt, ctx):
+    """3^20 paths (3.5e9): the FP32 pass against the FP64 pass, and the
+    recombining-lattice European in FP64 against backward induction."""
+    N = 20
+    opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for pay in (2, 3) for K in (95.0, 105.0)]
+    moves = [W.branch_moves(700 + i, N, 3, 0.01, 0.05) for i in range(len(opts))]
+    v32 = bt.bt_price_exact_moves(ctx.h, opts, 3, moves, 1)["value"]
+    v64 = bt.bt_price_exact_moves(ctx.h, opts, 3, moves, 0)["value"]
+    assert np.all(np.abs(v32 - v64) <= 3e-9 * np.abs(v64))
+
+
+def test_affine_moves_recombining_trinomial_fp64(bt, ctx, oracle):
+    N = 16
+    u = math.exp(0.25 * math.sqrt(3 / 16))
+    moves = np.tile([1 / u, 1.0, u, 0.2, 0.6, 0.2], (N, 1))
+    for pay in (W.EURO_CALL, W.EURO_PUT):
+        o = W.opt(N, 100.0, 101.0, 0.0, 0.25, 1.0, pay)
+        got = bt.bt_price_exact_moves(ctx.h, [o], 3, [moves], 0)["value"][0]
+        assert abs(got - oracle.branch_european_backward(o, moves, 3)) <= 1e-12 * got
+
+
+def test_steps_pass_is_the_binomial_case(bt, ctx):
+    N = 21
+    opts = [W.opt(N, 100.0, 100.0, 0.02, 0.2, 1.0, pay) for pay in range(8)]
+    steps = [W.step_factors(50 + i, N) for i in range(len(opts))]
+    moves = [np.stack([s[:, 1], s[:, 0], 1 - s[:, 2], s[:, 2]], axis=1) for s in steps]
+    for prec in (0, 1):
+        a = bt.bt_price_exact_steps(ctx.h, opts, steps, prec)["value"]
+        b = bt.bt_price_exact_moves(ctx.h, opts, 2, moves, prec)["value"]
+        assert np.array_equal(a, b)
