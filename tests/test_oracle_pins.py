@@ -494,3 +494,25 @@ def test_mc_single_stratum_matches_the_full_run(oracle):
     for z in (0, 7, 31):
         mz, vz, pz = oracle.mc_stratum(o, 5, z, 300, 17)
         assert (mz, vz, pz) == (mean[z], sv[z], pr[z])
+
+
+def test_paper_table5_variances_loosely(oracle, golden_dir):
+    """Table 5 as a loose pin: one run of the Partitioned and Shared-Sample
+    estimators (R = R_m = 1024, Asian put, N=32, Seydel) has its estimate
+    within 4 standard errors of the exact 82.115 and its variance estimate
+    within a factor of two of the paper's 1000-repetition average."""
+    g = json.load(open(os.path.join(golden_dir, "paper_table5_mc.json")))
+    c = g["common"]
+    o = W.opt(c["N"], c["S0"], c["K"], c["rate"], c["sigma"], c["T"], W.ASIAN_ARITH_PUT, W.TREE_SEYDEL)
+    disc2 = math.exp(-2 * c["rate"] * c["T"])
+    disc = math.sqrt(disc2)
+    for i, M in enumerate(g["M"]):
+        if M not in (1, 8, 64):
+            continue
+        mb = M.bit_length() - 1
+        for kind, shared in (("partitioned", False), ("shared", True)):
+            th, var = oracle.mc(o, mb, c["R"], 1000 + M, 0, shared)
+            v, se2 = disc * th, disc2 * var
+            assert abs(v - 82.115) <= 4 * math.sqrt(se2), (kind, M, v, se2)
+            ref = g[kind]["var"][i]
+            assert 0.5 * ref <= se2 <= 2.0 * ref, (kind, M, se2, ref)
