@@ -351,9 +351,16 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
 # ---------------------------------------------------------------------------
 # Greeks: one derivative pass over the N=28 Greeks workload
 # ---------------------------------------------------------------------------
-def greeks_bench(bt, W, ctx, reps=3):
+def greeks_bench(bt, W, ctx, reps=3, with_cpu=True):
     import numpy as np
     opts = W.greeks_workload(28, 1, 256)
+    cpu = {}
+    if with_cpu:
+        from oracle import py_oracle as O
+        oc = dict(opts[0], N=22)
+        cpu = {"cpu_baseline": _oracle_rate(lambda: O.greeks_crr(oc), 2.0 ** 22,
+                                            "value and four derivatives of set 0's arithmetic Asian call at "
+                                            "N=22 (2^22 paths), one thread; unit payoff-paths/s")}
     bt.bt_greeks_exact(ctx.h, opts)
     ts = []
     for _ in range(reps):
@@ -365,7 +372,7 @@ def greeks_bench(bt, W, ctx, reps=3):
     return {"workload": "value and dV/d(S0, sigma, rate, K), 256 sets (seed 1) x {arithmetic Asian call, "
                         "fixed-strike lookback call}, N=28, FP32_COMP, host arrays in and out",
             "ms": 1e3 * t, "options_per_s": len(opts) / t, "payoff_paths_per_s": paths / t,
-            "finite": bool(np.all(np.isfinite(grad)))}
+            "finite": bool(np.all(np.isfinite(grad))), **cpu}
 
 
 # ---------------------------------------------------------------------------
@@ -381,10 +388,20 @@ def _timed(fn, reps=3):
     return statistics.median(ts)
 
 
-def extras_bench(bt, W, ctx, sms, fmax):
+def _oracle_rate(fn, units, sample):
+    """One timed call of the oracle (one host thread) -> its rate in units/s."""
+    t0 = time.perf_counter()
+    fn()
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "cores": 1, "kind": "oracle", "sample": sample}
+
+
+def extras_bench(bt, W, ctx, sms, fmax, with_cpu=True):
     import numpy as np
     peak = sms * 128 * fmax * 1e6
     out = {}
+    if with_cpu:
+        from oracle import py_oracle as O
     # time-varying trees, FP32: 16 options at N=32 (arithmetic call/put, lookback call, geometric call)
     N = 32
     opts = [W.opt(N, 100.0, 90.0 + 5 * (i % 4), 0.03, 0.2, 1.0, pay)
@@ -397,6 +414,10 @@ def extras_bench(bt, W, ctx, sms, fmax):
                                 "host arrays in and out",
                     "ms": 1e3 * t, "payoff_paths_per_s": paths / t, "ops_per_payoff_path": 3,
                     "frac_of_issue_peak": 3 * paths / t / peak}
+    if with_cpu:
+        out["steps"]["cpu_baseline"] = _oracle_rate(
+            lambda: O.steps_sum_range(opts[0], steps[0], 0, 1 << 22), float(1 << 22),
+            "paths [0, 2^22) of option 0 (arithmetic Asian call), one thread")
     # generic pass, built-in payoffs, binomial and trinomial
     N2 = 28
     o2 = [W.opt(N2, 100.0, 100.0, 0.05, 0.2, 1.0, pay) for pay in (W.ASIAN_ARITH_CALL, W.LOOKBACK_FIXED_CALL)]
@@ -406,6 +427,11 @@ def extras_bench(bt, W, ctx, sms, fmax):
     out["generic_binomial"] = {"workload": "generic pass (FP64 path walk), arithmetic Asian and lookback calls, "
                                            "N=28, 2 x 2^28 paths", "ms": 1e3 * t,
                                "payoff_paths_per_s": 2 * 2.0 ** N2 / t}
+    if with_cpu:
+        o2c = dict(o2[0], N=20)
+        out["generic_binomial"]["cpu_baseline"] = _oracle_rate(
+            lambda: O.branch_price(o2c, np.tile([d, u, 1 - p, p], (20, 1)), 2, 1), 2.0 ** 20,
+            "the arithmetic Asian call at N=20 (2^20 paths) through the b-ary enumeration, one thread")
     # trinomial trees through the affine pass (prefix/suffix tables, FP32), N=22: 8 x 3^22 paths
     N4 = 22
     o4 = [W.opt(N4, 100.0, 90.0 + 5 * (i % 4), 0.03, 0.2, 1.0, pay)
@@ -417,6 +443,12 @@ def extras_bench(bt, W, ctx, sms, fmax):
                                            "8 x 3^22 paths, FP32_COMP, host arrays in and out",
                                "ms": 1e3 * t, "payoff_paths_per_s": paths4 / t,
                                "frac_of_issue_peak": 3 * paths4 / t / peak}
+    if with_cpu:
+        o4c = dict(o4[0], N=13)
+        mv4c = W.branch_moves(800, 13, 3, 0.01, 0.05)
+        out["trinomial_affine"]["cpu_baseline"] = _oracle_rate(
+            lambda: O.branch_price(o4c, mv4c, 3, 1), 3.0 ** 13,
+            "the arithmetic Asian call on a trinomial tree at N=13 (3^13 paths), one thread")
     N3 = 17
     o3 = [W.opt(N3, 100.0, 100.0, 0.05, 0.2, 1.0, pay) for pay in (W.ASIAN_ARITH_CALL, W.LOOKBACK_FIXED_CALL)]
     mv3 = [W.branch_moves(3, N3, 3), W.branch_moves(4, N3, 3)]
@@ -424,6 +456,12 @@ def extras_bench(bt, W, ctx, sms, fmax):
     out["generic_trinomial"] = {"workload": "generic pass, trinomial trees, arithmetic Asian and lookback calls, "
                                             "N=17, 2 x 3^17 paths", "ms": 1e3 * t,
                                 "payoff_paths_per_s": 2 * 3.0 ** N3 / t}
+    if with_cpu:
+        o3c = dict(o3[0], N=13)
+        mv3c = W.branch_moves(3, 13, 3)
+        out["generic_trinomial"]["cpu_baseline"] = _oracle_rate(
+            lambda: O.branch_price(o3c, mv3c, 3, 1), 3.0 ** 13,
+            "the arithmetic Asian call on a trinomial tree at N=13 (3^13 paths), one thread")
     # the batched workload at N=32 in the all-FP64 kernel (the accuracy reference) beside FP32_COMP
     o32 = W.batched_exact_workload(32, 0, 64)
     t64 = _timed(lambda: bt.bt_price_exact(ctx.h, o32, bt.BT_PREC_FP64), reps=1)
@@ -602,9 +640,9 @@ def main():
     if world == 1 and not args.no_mc:
         mc = mc_bench(bt, W, ctx, sms, fmax, with_cpu=not args.no_cpu_baseline)
     if world == 1 and not args.no_greeks:
-        greeks = greeks_bench(bt, W, ctx)
+        greeks = greeks_bench(bt, W, ctx, with_cpu=not args.no_cpu_baseline)
     if world == 1 and not args.no_extras:
-        extras = extras_bench(bt, W, ctx, sms, fmax)
+        extras = extras_bench(bt, W, ctx, sms, fmax, with_cpu=not args.no_cpu_baseline)
     if world == 1 and not args.no_serving:
         loads = [float(x) for x in args.serving_loads.split(",") if x]
         sctx = bt.Context(local_rank, device_budget_bytes=12 << 30)   # 8 GiB server pool + plain scratch
