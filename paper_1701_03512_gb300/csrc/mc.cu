@@ -146,13 +146,26 @@ __device__ __forceinline__ void simulate_two(const bt_mc_job &J, unsigned ia, un
     const int L = J.N - J.mb;
     const uint2 key = make_uint2(J.key_lo, J.key_hi);
     walker<FIELD> A, B;
-    for (int j0 = 0; j0 < L; j0 += 4) {
+    const int L4 = L & ~3;
+    int j0 = 0;
+    for (; j0 < L4; j0 += 4) {  // whole blocks of four steps, no per-step bound test
         const uint4 ra = philox4x32_10(make_uint4((unsigned)(j0 >> 2), ia, c2, J.stream), key);
         const uint4 rb = philox4x32_10(make_uint4((unsigned)(j0 >> 2), ib, c2, J.stream), key);
         const unsigned wa[4] = {ra.x, ra.y, ra.z, ra.w};
         const unsigned wb[4] = {rb.x, rb.y, rb.z, rb.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+            A.step(wa[q] < J.thr, J.uf, J.df);
+            B.step(wb[q] < J.thr, J.uf, J.df);
+        }
+    }
+    if (j0 < L) {  // the last one to three steps: words 0..L-j0-1 of the final block
+        const uint4 ra = philox4x32_10(make_uint4((unsigned)(j0 >> 2), ia, c2, J.stream), key);
+        const uint4 rb = philox4x32_10(make_uint4((unsigned)(j0 >> 2), ib, c2, J.stream), key);
+        const unsigned wa[3] = {ra.x, ra.y, ra.z};
+        const unsigned wb[3] = {rb.x, rb.y, rb.z};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
             if (j0 + q < L) {
                 A.step(wa[q] < J.thr, J.uf, J.df);
                 B.step(wb[q] < J.thr, J.uf, J.df);
