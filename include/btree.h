@@ -349,7 +349,9 @@ bt_status bt_wait(bt_server *srv, uint64_t ticket, int32_t timeout_ms, bt_result
 /* Non-blocking: *done = 1 and the result if finished (collects the ticket). */
 bt_status bt_poll(bt_server *srv, uint64_t ticket, bt_result *out, int32_t *done);
 bt_status bt_server_stats(bt_server *srv, bt_server_stats_t *out);
-/* Finishes all queued requests, stops the thread, frees its memory. */
+/* Finishes all queued requests, stops the thread, frees its memory; results
+ * not yet collected are discarded. No other call on srv may be running (a
+ * thread blocked in bt_wait must have returned) or follow. */
 bt_status bt_server_stop(bt_server *srv);
 /* Replays an arrival schedule (seconds from the call) of n single-option
  * requests: mode 1 through a server started with cfg, mode 0 as plain

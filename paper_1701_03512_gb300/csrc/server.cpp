@@ -24,6 +24,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -674,22 +675,33 @@ extern "C" bt_status bt_serve_replay(bt_ctx *ctx, const bt_server_cfg *cfg, cons
         bt_status s = bt_server_start(ctx, cfg, &S);
         if (s != BT_OK) return s;
         std::vector<uint64_t> tickets(n);
+        bt_status rs = BT_OK;  // the first failure, submission or result, and its message
+        int r_idx = -1;
+        std::string r_msg;
         std::thread submitter([&]() {
             for (int i = 0; i < n; ++i) {
                 std::this_thread::sleep_until(at(i));
-                if (bt_submit(S, &opts[i], cfg && cfg->use_fp64 ? BT_PREC_FP64 : BT_PREC_FP32_COMP, &tickets[i]) != BT_OK)
+                const bt_status ss =
+                    bt_submit(S, &opts[i], cfg && cfg->use_fp64 ? BT_PREC_FP64 : BT_PREC_FP32_COMP, &tickets[i]);
+                if (ss != BT_OK) {
                     tickets[i] = 0;
+                    if (rs == BT_OK) {
+                        rs = ss;
+                        r_idx = i;
+                        r_msg = bt_last_error(ctx);  // the submitting thread's message
+                    }
+                }
             }
         });
         submitter.join();
-        bt_status rs = BT_OK;
         for (int i = 0; i < n; ++i) {
-            if (!tickets[i]) {
-                rs = BT_EINVAL;
-                continue;
-            }
+            if (!tickets[i]) continue;
             s = bt_wait(S, tickets[i], 600000, &results[i]);
-            if (s != BT_OK) rs = s;
+            if (s != BT_OK && rs == BT_OK) {
+                rs = s;
+                r_idx = i;
+                r_msg = bt_last_error(ctx);
+            }
         }
         std::unordered_map<uint64_t, clk::time_point> done;
         {
@@ -697,7 +709,7 @@ extern "C" bt_status bt_serve_replay(bt_ctx *ctx, const bt_server_cfg *cfg, cons
             for (auto &d : S->done_log) done[d.first] = d.second;
         }
         bt_server_stop(S);
-        if (rs != BT_OK) return rs;
+        if (rs != BT_OK) return bt_fail(rs, "bt_serve_replay: request %d: %s", r_idx, r_msg.c_str());
         for (int i = 0; i < n; ++i) {
             auto it = done.find(tickets[i]);
             latency_ms[i] = it == done.end() ? -1.0 : ms_between(at(i), it->second);
