@@ -351,7 +351,7 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
 # ---------------------------------------------------------------------------
 # Greeks: one derivative pass over the N=28 Greeks workload
 # ---------------------------------------------------------------------------
-def greeks_bench(bt, W, ctx, reps=3, with_cpu=True):
+def greeks_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
     import numpy as np
     opts = W.greeks_workload(28, 1, 256)
     cpu = {}
@@ -372,6 +372,8 @@ def greeks_bench(bt, W, ctx, reps=3, with_cpu=True):
     return {"workload": "value and dV/d(S0, sigma, rate, K), 256 sets (seed 1) x {arithmetic Asian call, "
                         "fixed-strike lookback call}, N=28, FP32_COMP, host arrays in and out",
             "ms": 1e3 * t, "options_per_s": len(opts) / t, "payoff_paths_per_s": paths / t,
+            # value (affine FMA, max, accumulate), in-the-money count, df/du accumulate
+            "ops_per_payoff_path": 5, "frac_of_issue_peak": 5 * paths / t / (sms * 128 * fmax * 1e6),
             "finite": bool(np.all(np.isfinite(grad))), **cpu}
 
 
@@ -640,7 +642,7 @@ def main():
     if world == 1 and not args.no_mc:
         mc = mc_bench(bt, W, ctx, sms, fmax, with_cpu=not args.no_cpu_baseline)
     if world == 1 and not args.no_greeks:
-        greeks = greeks_bench(bt, W, ctx, with_cpu=not args.no_cpu_baseline)
+        greeks = greeks_bench(bt, W, ctx, sms, fmax, with_cpu=not args.no_cpu_baseline)
     if world == 1 and not args.no_extras:
         extras = extras_bench(bt, W, ctx, sms, fmax, with_cpu=not args.no_cpu_baseline)
     if world == 1 and not args.no_serving:
