@@ -339,8 +339,25 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
         dt = time.perf_counter() - t0
         cpu = {"samples_per_s": (1 << mb_c) * R_c / dt, "cores": 1, "kind": "oracle",
                "sample": "2^%d strata x %d samples of the same option, one thread" % (mb_c, R_c)}
+    # the other stratifications of the MC workload: N = 64 and 252, m = 10, 12, 16
+    sweep = []
+    for Ns in (64, 252):
+        os_ = W.opt(Ns, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
+        for ms, Rs in ((10, 1 << 14), (12, 1 << 12), (16, 1 << 10)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rs = bt.bt_price_mc(ctx.h, [os_], ms, Rs, 20 + ms, stream)[0]
+            e1.record(stream)
+            e1.synchronize()
+            ns = float(Rs) * (1 << ms)
+            ps = bt.bt_price_mc(ctx.h, [os_], 0, int(ns), 40 + ms, stream)[0]
+            sweep.append({"N": Ns, "m": ms, "R": Rs, "samples_per_s": ns / (e0.elapsed_time(e1) / 1e3),
+                          "value": float(rs["value"]), "stderr": float(rs["stderr_mc"]),
+                          "plain_stderr_same_draws": float(ps["stderr_mc"]),
+                          "variance_ratio": float((ps["stderr_mc"] / rs["stderr_mc"]) ** 2)})
     return {"workload": "Partitioned MC, arithmetic Asian call, N=%d, S0=K=100, rate 0.05, sigma 0.2, T=1, "
-                        "2^%d strata x %d samples" % (N, mb, R), "cpu_baseline": cpu,
+                        "2^%d strata x %d samples" % (N, mb, R), "cpu_baseline": cpu, "strata_sweep": sweep,
             "samples_per_s": samples / t, "steps_per_s": steps / t, "ms": 1e3 * t,
             "value": float(r[0]["value"]), "stderr": float(r[0]["stderr_mc"]),
             "plain_mc_same_draws": {"value": float(plain["value"]), "stderr": float(plain["stderr_mc"]),
