@@ -28,7 +28,7 @@ def ctx(bt):
     c.close()
 
 
-@pytest.mark.parametrize("b,N", [(3, 1), (3, 6), (3, 10), (4, 6), (5, 5)])
+@pytest.mark.parametrize("b,N", [(3, 1), (3, 6), (3, 10), (4, 6), (5, 5), (6, 4), (7, 4), (8, 4)])
 def test_builtin_payoffs_against_the_oracle(bt, ctx, oracle, b, N):
     opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for pay in range(8) for K in (95.0, 103.0)]
     moves = [W.branch_moves(7 * N + i + b, N, b) for i in range(len(opts))]
@@ -111,7 +111,7 @@ def _tol(prec, paths):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("b,N", [(3, 1), (3, 9), (3, 13), (4, 8), (5, 7)])
+@pytest.mark.parametrize("b,N", [(3, 1), (3, 9), (3, 13), (4, 8), (5, 7), (6, 4), (7, 4), (8, 5)])
 def test_affine_moves_pass_against_the_oracle(bt, ctx, oracle, prec, b, N):
     """bt_price_exact_moves (the prefix/suffix tables and per-suffix weights of
     the time-varying pass, in base b) on non-recombining trees."""
@@ -122,6 +122,27 @@ def test_affine_moves_pass_against_the_oracle(bt, ctx, oracle, prec, b, N):
         ref = oracle.branch_price(o, m, b, 8)
         assert abs(g["value"] - ref) <= _tol(prec, b ** N) * abs(ref) + 1e-12 * o["S0"], (prec, o, g["value"], ref)
         assert g["paths"] == b ** N
+
+
+def test_affine_moves_probability_floor(bt, ctx, oracle):
+    """FP32_COMP refuses a branch probability in (0, 0.004) (its weights would
+    leave the FP32 pair range); FP64 takes it, and a zero probability (a
+    branch that never happens) is taken by both."""
+    o = W.opt(6, 100.0, 100.0, 0.02, 0.2, 1.0, W.ASIAN_ARITH_CALL)
+    mv = W.branch_moves(5, 6, 3)
+    rare = mv.copy()
+    rare[3, 3:] = [0.001, 0.5, 0.499]
+    with pytest.raises(bt.BtError) as e:
+        bt.bt_price_exact_moves(ctx.h, [o], 3, [rare], bt.BT_PREC_FP32_COMP)
+    assert e.value.status == bt.BT_EUNSUPPORTED
+    got = bt.bt_price_exact_moves(ctx.h, [o], 3, [rare], bt.BT_PREC_FP64)[0]["value"]
+    assert abs(got - oracle.branch_price(o, rare, 3, 8)) <= 1e-12 * abs(got)
+    never = mv.copy()
+    never[2, 3:] = [0.0, 0.5, 0.5]
+    ref = oracle.branch_price(o, never, 3, 8)
+    for prec in (bt.BT_PREC_FP64, bt.BT_PREC_FP32_COMP):
+        got = bt.bt_price_exact_moves(ctx.h, [o], 3, [never], prec)[0]["value"]
+        assert abs(got - ref) <= _tol(prec, 3 ** 6) * abs(ref) + 1e-12 * o["S0"], (prec, got, ref)
 
 
 def test_affine_moves_large_trinomial_fp32_against_fp64(bt, ctx):
