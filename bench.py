@@ -567,7 +567,9 @@ def main():
         torch.cuda.synchronize()
 
     ctx = bt.Context(local_rank)
-    opts = W.batched_exact_workload(args.N, 0, args.sets)
+    # weak scaling: every rank prices its own batch of option sets (seed = rank;
+    # rank 0's is the one-GPU workload), no data crosses between ranks
+    opts = W.batched_exact_workload(args.N, rank, args.sets)
     plan = bt.bt_exact_plan_create(ctx.h, opts, bt.BT_PREC_FP32_COMP)
     info = bt.bt_exact_plan_info_get(plan)
     step_paths = info["payoff_paths"]
@@ -676,8 +678,9 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(args, {"parallelism": "replicas" if world > 1 else "single GPU",
-                                             "wall_s_timed": t_wall}),
+            "config": workload_config(args, {"parallelism": ("dp%d: one batch of option sets per rank (seed = rank), "
+                                                             "no collective on the data path" % world)
+                                             if world > 1 else "single GPU", "wall_s_timed": t_wall}),
             "fp32_peak_frac": roof["frac"], "clocks": clocks, "e2e": e2e,
             # per step: k_params, k_tables, k_class_tables, k_exact32, k_finalize
             "gpu_launches": 5 * args.steps, "roofline": roof, "cpu_baseline": cpu,
