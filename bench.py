@@ -128,6 +128,32 @@ def cpu_oracle_sample(opts, seconds, threads):
     return paths / dt, sample
 
 
+def _mc_oracle_strata(job):
+    """Worker of the all-cores MC baseline: the oracle's draws for some strata."""
+    o, mb, strata, R, seed = job
+    from oracle import py_oracle as O
+    for z in strata:
+        O.mc_stratum(o, mb, z, R, seed)
+    return len(strata) * R
+
+
+def mc_oracle_all_cores(o, mb, R, seed, threads, strata_per_worker=4):
+    """The oracle's Partitioned MC over all host cores: one spawned process per
+    core, each drawing whole strata (the paper's strata-to-process mapping);
+    returns (samples/s, sample description)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(threads, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_mc_oracle_strata, [(o, mb, [w], 4, seed) for w in range(threads)]))  # start, load
+        jobs = [(o, mb, list(range(w * strata_per_worker, (w + 1) * strata_per_worker)), R, seed)
+                for w in range(threads)]
+        t0 = time.perf_counter()
+        n = sum(ex.map(_mc_oracle_strata, jobs))
+        dt = time.perf_counter() - t0
+    return n / dt, "%d strata x %d samples (strata 0..%d of 2^%d), %d processes" % (
+        threads * strata_per_worker, R, threads * strata_per_worker - 1, mb, threads)
+
+
 def cpu_model():
     try:
         for ln in open("/proc/cpuinfo"):
@@ -340,6 +366,9 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
         dt = time.perf_counter() - t0
         cpu = {"samples_per_s": (1 << mb_c) * R_c / dt, "cores": 1, "kind": "oracle",
                "sample": "2^%d strata x %d samples of the same option, one thread" % (mb_c, R_c)}
+        threads = cpu_threads()
+        v_all, s_all = mc_oracle_all_cores(o, mb, R, 1, threads, strata_per_worker=32)
+        cpu["all_cores"] = {"samples_per_s": v_all, "cores": threads, "kind": "oracle", "sample": s_all}
     # the other stratifications of the MC workload: N = 64 and 252, m = 10, 12, 16
     sweep = []
     for Ns in (64, 252):
