@@ -70,7 +70,7 @@ struct bt_pow {               // u^e for some exponent e, in FP64 and as an FP32
     float hi, lo;
 };
 
-// Numeric parameters of a job, computed on the device from the option (a1).
+// Numeric parameters of a job, computed on the device from the option.
 struct bt_jparams {
     double u, d, p, disc, lnu;
     double S0, K;

@@ -44,7 +44,7 @@
 #include "exact_common.cuh"
 
 // ---------------------------------------------------------------------------
-// a1: tree parameters (Section 2, A1-A3) on the device
+// Tree parameters (Section 2, A1-A3) on the device
 // ---------------------------------------------------------------------------
 __device__ static int dev_tree(const bt_option &o, double *u, double *d, double *p) {
     double dt = o.T / (double)o.N;
@@ -149,7 +149,7 @@ __global__ void k_params(const bt_option *opts, const bt_job *jobs, bt_jparams *
 }
 
 // ---------------------------------------------------------------------------
-// a2/a3: suffix table (sorted by up-count, groups padded with NaN) and the
+// Suffix table (sorted by up-count, groups padded with NaN) and the
 // two-level prefix tables, in FP64
 // ---------------------------------------------------------------------------
 __device__ static int binom_small(int n, int k) {
@@ -361,7 +361,7 @@ __global__ void k_class_tables(const bt_job *jobs, const bt_jparams *prm, float2
 }
 
 // ---------------------------------------------------------------------------
-// a3 (per prefix) and a4: the path sums
+// Prefix states and the path sums
 // ---------------------------------------------------------------------------
 template <int MODE>
 __device__ __forceinline__ void tree8(const float4 *f4, float B, float Ah, float nAl, float &tc, float &tp) {
@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_exact64(bt_exact_args a) {
 }
 
 // ---------------------------------------------------------------------------
-// a5: per-option reduction of the block partials in a fixed order (eq. f15)
+// Per-option reduction of the block partials in a fixed order (eq. f15)
 // ---------------------------------------------------------------------------
 struct neu {
     double s, c;

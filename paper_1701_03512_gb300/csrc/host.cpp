@@ -117,7 +117,7 @@ void ctx_free(bt_ctx *c, void *p, size_t bytes) {
 cudaStream_t ctx_stream(bt_ctx *c, void *s) { return s ? (cudaStream_t)s : c->stream; }
 
 // ---------------------------------------------------------------------------
-// a1 on the host (validation) -- Section 2, A1-A3
+// Tree parameters on the host (validation) -- Section 2, A1-A3
 // ---------------------------------------------------------------------------
 static bool finite_all(const bt_option &o) {
     return std::isfinite(o.S0) && std::isfinite(o.K) && std::isfinite(o.rate) && std::isfinite(o.sigma) &&

@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_mc_warp(bt_mc_args a) {
     }
 }
 
-// a8 (first half): one warp per stratum combines the stratum's work items
+// Combination, first half: one warp per stratum combines the stratum's work items
 // (Chan et al.'s update, fixed lane order and a fixed shuffle tree).
 __global__ void k_mc_strata(const bt_mc_job *jobs, int n_jobs, const double4 *item_stats, int64_t n_strata,
                             double4 *strata_nmq /* per stratum (n, mean, M2, prob) */) {
@@ -444,7 +444,7 @@ __global__ void k_mc_strata(const bt_mc_job *jobs, int n_jobs, const double4 *it
     if (lane == 0) strata_nmq[g] = make_double4(n, mu, Q, J.shared ? 1.0 : stratum_state(J, (uint64_t)mg).prob);
 }
 
-// a8 (second half): across strata, eq. mc12 and Var = sum_m P(D_m)^2 s_m^2 / R_m
+// Combination, second half: across strata, eq. mc12 and Var = sum_m P(D_m)^2 s_m^2 / R_m
 // (unbiased s_m^2); also the variance of one draw by the law of total variance
 // (eq. mc14), for plain-MC comparisons. One block per option.
 __global__ void k_mc_finalize(const bt_mc_job *jobs, int n_jobs, const double4 *strata_nmq, bt_result *out,

@@ -93,7 +93,7 @@ __device__ static double suffix_f(int field, const sblock &b, int N) {
     }
 }
 
-// a1 for move-by-move jobs: scalars and the suffix f range (every f_s is
+// Parameters of move-by-move jobs: scalars and the suffix f range (every f_s is
 // non-decreasing in each step's factor, so the smallest and the largest
 // factors of every step bound it).
 __global__ void k_steps_params(const bt_option *opts, const bt_job *jobs, const double *steps, bt_jparams *prm,
@@ -149,7 +149,7 @@ __device__ static bt_spentry make_spentry(const sblock &b, double e) {
     return r;
 }
 
-// a2/a3 for time-varying jobs: suffix entries (f, w) and the two prefix
+// Tables of move-by-move jobs: suffix entries (f, w) and the two prefix
 // tables. The geometric factor of a prefix block folds in the later steps
 // that inherit its end price: e_h = exp((lg_h + (M + L) ln rho_h)/N) for the
 // first block, e_m = exp((lg_m + L ln rho_m)/N) for the second.
