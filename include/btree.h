@@ -84,8 +84,13 @@ typedef struct {
 
 typedef struct {
     double value;       /* discounted value V                                    */
-    double err_est;     /* exact sums: a-priori bound on |V - V_exact| from
-                           rounding; MC: 0                                       */
+    double err_est;     /* exact sums: stated bound on |V - V_exact| from
+                           rounding, rel |V|: rel = 1e-12 in FP64; in FP32_COMP
+                           the band for the depth (1e-9 from N = 28, 3e-9 from
+                           20, 2e-8 from 12, 1e-7 below; 1e-9 for every N for
+                           the class-sum payoffs) plus, for the arithmetic
+                           Asian, 6e-8 max(p, 1-p)^N (one FP32 rounding of the
+                           heaviest path's share); MC: 0                     */
     double stderr_mc;   /* MC: standard error of `value`; exact sums: 0          */
     double var_plain;   /* MC: estimated variance of one undiscounted draw
                            V(X) (for plain-MC comparisons); exact sums: 0        */

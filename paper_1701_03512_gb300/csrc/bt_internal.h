@@ -6,7 +6,8 @@
 #include "../../include/btree.h"
 
 #define BT_MAX_N_EXACT 40
-#define BT_MAX_L 12            // suffix steps held in a shared-memory table
+#define BT_MAX_L 13            // suffix steps held in a shared-memory table (lattice passes)
+#define BT_STEPS_MAX_L 12      // b^L <= 2^12 suffixes for trees given move by move (16-byte entries)
 #define BT_LOW_BITS 10         // a work item covers 2^10 consecutive prefixes
 #define BT_THREADS 256         // threads per block of the path-sum kernels
 #define BT_PT 4                // prefixes per thread (FP32 kernel): 256 * 4 = 2^10
@@ -76,6 +77,7 @@ struct bt_jparams {
     double S0, K;
     double NKoS0, KoS0, S0oN;
     double fmin, fmax;
+    double wmax;                     // probability of the likeliest path
     double W[BT_MAX_L + 1];          // suffix-group weights p^k (1-p)^{L-k}
     double wl[BT_LOW_BITS + 1];      // p^c (1-p)^{Plo-c}, Plo = min(P, BT_LOW_BITS)
     double wh[BT_MAX_N_EXACT + 1];   // p^c (1-p)^{Phi-c}, Phi = P - Plo

@@ -83,6 +83,7 @@ __global__ void k_params(const bt_option *opts, const bt_job *jobs, bt_jparams *
     memset(&P, 0, sizeof(P));
     P.ok = dev_tree(o, &P.u, &P.d, &P.p);
     P.disc = exp(-o.rate * o.T);
+    P.wmax = pow(fmax(P.p, 1.0 - P.p), (double)J.N);
     P.lnu = log(P.u);
     P.S0 = o.S0;
     P.K = o.K;
@@ -763,8 +764,21 @@ __global__ void k_finalize(const bt_job *jobs, const bt_jparams *prm, int n_jobs
         p.c += pc;
     }
     if (lane == 0) {
-        const double disc = prm[J.prm_off].disc;
-        const double rel = prec == BT_PREC_FP64 ? 1e-13 : 1e-9;
+        const bt_jparams &P = prm[J.prm_off];
+        const double disc = P.disc;
+        // stated error: FP64 1e-12; FP32 the accuracy contract by the number
+        // of paths (class sums carry no per-path rounding: 1e-9), plus one
+        // FP32 rounding (2^-24) of the likeliest path's share, which no
+        // averaging removes when the tree's mass sits on a few paths
+        double rel = 1e-12;
+        if (prec != BT_PREC_FP64 && J.cls) {
+            rel = 1e-9;
+        } else if (prec != BT_PREC_FP64) {  // one FP32 rounding per path: the band by log2(paths)
+            const bool wide = J.branches > 2;
+            const double bits = wide ? (double)J.N * log2((double)J.branches) : (double)J.N;
+            rel = bits >= 28 ? 1e-9 : bits >= 20 ? 3e-9 : bits >= 12 ? (wide ? 5e-8 : 2e-8) : (wide ? 3e-7 : 1e-7);
+            rel += 6.0e-8 * P.wmax;
+        }
         const int64_t paths = 1ll << J.N;
         if (J.out_call >= 0) {
             bt_result r;

@@ -216,8 +216,8 @@ int exact_split_L(int N) { return std::max(1, std::min(BT_MAX_L, N - BT_LOW_BITS
 // payoffs the suffix factor f_s depends on the suffix only through one
 // integer key (level sum, end level, max or min level), so within an up-count
 // group (same weight) the suffixes fall into a few classes of equal f_s: at
-// L = 12, 13 (European), <= 91 (lookback) or 299 (geometric) classes instead
-// of 4096 suffixes. The FP32 pass then sums multiplicity x payoff over the
+// L = 13, 14 (European), 62 (lookback) or 378 (geometric) classes instead
+// of 8192 suffixes. The FP32 pass then sums multiplicity x payoff over the
 // classes in pair arithmetic. The key, its definition and the ordering
 // (groups by up-count, keys ascending) are shared with k_class_tables.
 static int suffix_key(int field, unsigned s, int L) {

@@ -112,6 +112,13 @@ __global__ void k_steps_params(const bt_option *opts, const bt_job *jobs, const 
     P.KoS0 = o.K / o.S0;
     P.S0oN = o.S0 / (double)J.N;
     const int b = J.branches;
+    P.wmax = 1.0;  // the likeliest path: the likeliest move of every step
+    for (int t = 0; t < J.N; ++t) {
+        const double *m = steps + 2 * b * (J.off_pow + t) + b;
+        double q = 0.0;
+        for (int k = 0; k < b; ++k) q = fmax(q, m[k]);
+        P.wmax *= q;
+    }
     const double *st = steps + 2 * b * (J.off_pow + J.P);
     P.fmin = suffix_f(J.field, walk_steps(0, J.L, b, st, -1), J.N);
     P.fmax = suffix_f(J.field, walk_steps(0, J.L, b, st, +1), J.N);
@@ -436,7 +443,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_steps64(bt_exact_args a, cons
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-#define BT_STEPS_SMEM ((size_t)(1 << BT_MAX_L) * 16)
+#define BT_STEPS_SMEM ((size_t)(1 << BT_STEPS_MAX_L) * 16)
 
 extern "C" int bt_launch_steps_params(const bt_option *d_opts, const bt_job *d_jobs, const double *d_steps,
                                       bt_jparams *d_prm, int n_jobs, void *stream) {

@@ -67,7 +67,7 @@ static bt_status price_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int 
         // suffix steps: b^L <= 2^12 entries in shared memory (binomial: the lattice pass's split)
         int L = 0;
         int64_t nsuf = 1;
-        while (L < J.N && nsuf * b <= (1 << BT_MAX_L) && (b > 2 || L < exact_split_L(J.N))) {
+        while (L < J.N && nsuf * b <= (1 << BT_STEPS_MAX_L) && (b > 2 || L < exact_split_L(J.N))) {
             nsuf *= b;
             ++L;
         }

@@ -32,7 +32,7 @@ def exact_items(o):
     """Work items of the exhaustive pass: item i covers prefixes
     [i 2^10, (i+1) 2^10) of 2^P, all 2^L suffixes each, prefix bits first."""
     N = o["N"]
-    L = max(1, min(12, N - 10))
+    L = max(1, min(13, N - 10))   # the library's split: L = clamp(N - 10, 1, 13)
     P = N - L
     n_items = max(1, -(-(1 << P) // (1 << 10)))
     span = 1 << (10 + L)

@@ -121,6 +121,7 @@ def test_affine_moves_pass_against_the_oracle(bt, ctx, oracle, prec, b, N):
     for o, m, g in zip(opts, moves, got):
         ref = oracle.branch_price(o, m, b, 8)
         assert abs(g["value"] - ref) <= _tol(prec, b ** N) * abs(ref) + 1e-12 * o["S0"], (prec, o, g["value"], ref)
+        assert abs(g["value"] - ref) <= g["err_est"] + 1e-12 * o["S0"], (prec, o, g["err_est"])   # stated error
         assert g["paths"] == b ** N
 
 

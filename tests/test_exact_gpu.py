@@ -117,9 +117,9 @@ def test_paper_exact_values(bt, ctx, golden_dir):
     assert abs(got[1] - g["values"]["lookback_fixed_put"]) <= 5e-4
 
 
-@pytest.mark.parametrize("N", [11, 12, 22, 23, 24, 26])
+@pytest.mark.parametrize("N", [11, 12, 22, 23, 24, 25, 26])
 def test_split_boundaries(bt, ctx, oracle, N):
-    """Around the prefix/suffix split changes (L grows until 12, P crosses 11)."""
+    """Around the prefix/suffix split changes (L = N - 10 grows until 13 at N = 23, then P grows)."""
     opts = W.batch(N, W.option_sets(N, 2), list(range(8)))
     ref = [oracle.exact(o) if N > 18 else oracle.price_exhaustive(o, 8) for o in opts]
     for prec in (0, 1):
@@ -305,17 +305,35 @@ def test_empty_and_single_step(bt, ctx, oracle):
             assert abs(got - ref) <= tol(prec, 1, pay) * abs(ref) + 1e-12 * 100.0, (pay, prec, got, ref)
 
 
+@pytest.mark.parametrize("N", [9, 16, 22, 26])
+def test_stated_error_covers_the_difference_to_the_oracle(bt, ctx, oracle, N):
+    """err_est of every result (the accuracy contract for its depth, payoff
+    and precision) bounds its distance to the oracle."""
+    opts = W.batch(N, W.option_sets(70 + N, 3), list(range(8)))
+    ref = np.array([oracle.exact(o) if N > 18 else oracle.price_exhaustive(o, 8) for o in opts])
+    s0 = np.array([o["S0"] for o in opts])
+    for prec in (0, 1):
+        r = ctx.price_exact(opts, prec)
+        assert np.all(np.abs(r["value"] - ref) <= r["err_est"] + 1e-12 * s0), (prec, N)
+        assert np.all(r["err_est"] <= np.array([tol(prec, N, o["payoff"]) for o in opts]) * np.abs(r["value"]) * 1.01)
+
+
 def test_probability_limit_of_the_fp32_path(bt, ctx, oracle):
-    """min(p, 1-p) >= 0.004 is accepted in FP32 and matches the oracle; below
-    it FP32 is refused and FP64 still prices."""
+    """min(p, 1-p) >= 0.004 is accepted in FP32 and matches the oracle within
+    the stated error; below it FP32 is refused and FP64 still prices. At
+    p = 0.996 the all-up path carries 0.996^24 = 91 % of the value, so its one
+    FP32 rounding (up to 2^-24) does not average out: the stated error adds
+    6e-8 max(p, 1-p)^N to the contract's band, 5.8e-8 relative here."""
     u = 1.05
     d = 1 / u
     for p, ok in ((0.004, True), (0.996, True), (0.0039, False)):
         o = W.opt(24, 100.0, 100.0, 0.0, 0.2, 1.0, W.ASIAN_ARITH_CALL, W.TREE_EXPLICIT, u=u, d=d, p=p)
         if ok:
-            got = ctx.price_exact([o], 1)["value"][0]
+            r = ctx.price_exact([o], 1)[0]
             ref = oracle.exact(o)
-            assert abs(got - ref) <= tol(1, 24) * abs(ref) + 1e-12 * 100.0
+            stated = tol(1, 24) + 6e-8 * max(p, 1 - p) ** 24
+            assert r["err_est"] == pytest.approx(stated * abs(r["value"]), rel=1e-12)
+            assert abs(r["value"] - ref) <= r["err_est"] + 1e-12 * 100.0
         else:
             with pytest.raises(bt.BtError) as e:
                 ctx.price_exact([o], 1)

@@ -68,16 +68,18 @@ def test_admission_by_memory(bt, ctx):
     """A pool that holds only a few requests' partials at a time still
     completes every request, admitting as memory frees up."""
     opts = [W.opt(38, 100.0, 90.0 + 2 * i, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL) for i in range(8)]
-    # N = 38: 2^16 work items x 16 B of partials = 1 MiB per request, plus
-    # 2 x 2^13 prefix entries x 32 B and the suffix table: about 1.55 MiB
-    srv = bt.bt_server_start(ctx.h, max_active=64, n_streams=2, device_budget_bytes=(3 << 20) + (512 << 10))
+    # N = 38 (13 suffix steps, 25 prefix steps): 2^15 work items x 16 B of
+    # partials = 512 KiB per request, plus 2^12 + 2^13 prefix entries x 32 B
+    # and the 65 KiB suffix table: about 0.94 MiB; the pool holds two
+    budget = (2 << 20) + (512 << 10)
+    srv = bt.bt_server_start(ctx.h, max_active=64, n_streams=2, device_budget_bytes=budget)
     try:
         tickets = [bt.bt_submit(srv, o) for o in opts]
         got = [bt.bt_wait(srv, t, 120000) for t in tickets]
         st = bt.bt_server_stats(srv)
     finally:
         bt.bt_server_stop(srv)
-    assert st["pool_bytes"] < (3 << 20) + (512 << 10)
+    assert st["pool_bytes"] < budget
     assert 1 <= st["peak_active"] <= 2, st
     assert st["completed"] == len(opts)
     for o, g in zip(opts, got):

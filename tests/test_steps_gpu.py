@@ -44,6 +44,8 @@ def test_all_payoffs_against_the_oracle(bt, ctx, oracle, prec, N):
     got = bt.bt_price_exact_steps(ctx.h, opts, steps, prec)
     ref = [oracle.steps_price(o, s, 8) for o, s in zip(opts, steps)]
     _check(got["value"], ref, opts, prec, "N=%d" % N)
+    s0 = np.array([o["S0"] for o in opts])
+    assert np.all(np.abs(got["value"] - np.array(ref)) <= got["err_est"] + 1e-12 * s0)   # the stated error
     assert np.all(got["paths"] == 2 ** N)
 
 
