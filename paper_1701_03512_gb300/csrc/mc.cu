@@ -138,43 +138,42 @@ struct walker {
     }
 };
 
-// Simulates the suffixes of samples ia and ib together (two independent Philox
-// streams per thread for instruction-level parallelism).
-template <int FIELD>
-__device__ __forceinline__ void simulate_two(const bt_mc_job &J, unsigned ia, unsigned ib, unsigned c2, float &fa,
-                                             float &fb) {
+// Simulates the suffixes of W samples together (W independent Philox streams
+// per thread, for instruction-level parallelism).
+template <int FIELD, int W>
+__device__ __forceinline__ void simulate_w(const bt_mc_job &J, const unsigned (&idx)[W], unsigned c2, float (&f)[W]) {
     const int L = J.N - J.mb;
     const uint2 key = make_uint2(J.key_lo, J.key_hi);
-    walker<FIELD> A, B;
+    walker<FIELD> A[W];
     const int L4 = L & ~3;
     int j0 = 0;
     for (; j0 < L4; j0 += 4) {  // whole blocks of four steps, no per-step bound test
-        const uint4 ra = philox4x32_10(make_uint4((unsigned)(j0 >> 2), ia, c2, J.stream), key);
-        const uint4 rb = philox4x32_10(make_uint4((unsigned)(j0 >> 2), ib, c2, J.stream), key);
-        const unsigned wa[4] = {ra.x, ra.y, ra.z, ra.w};
-        const unsigned wb[4] = {rb.x, rb.y, rb.z, rb.w};
+        uint4 r[W];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            A.step(wa[q] < J.thr, J.uf, J.df);
-            B.step(wb[q] < J.thr, J.uf, J.df);
+        for (int w = 0; w < W; ++w) r[w] = philox4x32_10(make_uint4((unsigned)(j0 >> 2), idx[w], c2, J.stream), key);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            A[w].step(r[w].x < J.thr, J.uf, J.df);
+            A[w].step(r[w].y < J.thr, J.uf, J.df);
+            A[w].step(r[w].z < J.thr, J.uf, J.df);
+            A[w].step(r[w].w < J.thr, J.uf, J.df);
         }
     }
     if (j0 < L) {  // the last one to three steps: words 0..L-j0-1 of the final block
-        const uint4 ra = philox4x32_10(make_uint4((unsigned)(j0 >> 2), ia, c2, J.stream), key);
-        const uint4 rb = philox4x32_10(make_uint4((unsigned)(j0 >> 2), ib, c2, J.stream), key);
-        const unsigned wa[3] = {ra.x, ra.y, ra.z};
-        const unsigned wb[3] = {rb.x, rb.y, rb.z};
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            if (j0 + q < L) {
-                A.step(wa[q] < J.thr, J.uf, J.df);
-                B.step(wb[q] < J.thr, J.uf, J.df);
-            }
+        for (int w = 0; w < W; ++w) {
+            const uint4 r = philox4x32_10(make_uint4((unsigned)(j0 >> 2), idx[w], c2, J.stream), key);
+            const unsigned wd[3] = {r.x, r.y, r.z};
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (j0 + q < L) A[w].step(wd[q] < J.thr, J.uf, J.df);
         }
     }
-    fa = A.value(J, L);
-    fb = B.value(J, L);
+#pragma unroll
+    for (int w = 0; w < W; ++w) f[w] = A[w].value(J, L);
 }
+
+#define BT_MC_WALKERS 4   // samples per thread at once in the Partitioned kernel (measured: 2 < 8 < 4)
 
 __device__ __forceinline__ float payoff_of(const bt_mc_job &J, float tau, float beta, float C, float f) {
     const float y = tau + f;
@@ -219,8 +218,9 @@ __device__ void mc_item(const bt_mc_args &a, const bt_mc_job &J, int64_t item_lo
         const int64_t ia = i0 + threadIdx.x + (int64_t)k * BT_THREADS;
         const int64_t ib = ia + BT_THREADS;
         if (ia >= J.R) break;
+        const unsigned idx[2] = {(unsigned)ia, (unsigned)ib};
         float f2[2];
-        simulate_two<FIELD>(J, (unsigned)ia, (unsigned)ib, SHARED ? 0u : (unsigned)m, f2[0], f2[1]);
+        simulate_w<FIELD, 2>(J, idx, SHARED ? 0u : (unsigned)m, f2);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (h == 1 && ib >= J.R) break;
@@ -337,17 +337,21 @@ __device__ __forceinline__ void mc_warp_item(const bt_mc_args &a, const bt_mc_jo
     const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
     const int64_t i0 = (item_local % chunks) * BT_MC_ITEM;
     float n = 0.0f, mean = 0.0f, M2 = 0.0f;
+    constexpr int W = BT_MC_WALKERS;
+    static_assert((BT_MC_ITEM / 32) % W == 0, "walkers must divide a lane's samples per item");
 #pragma unroll 1
-    for (int k = 0; k < BT_MC_ITEM / 32; k += 2) {
+    for (int k = 0; k < BT_MC_ITEM / 32; k += W) {
         const int64_t ia = i0 + lane + (int64_t)k * 32;
-        const int64_t ib = ia + 32;
         if (ia >= J.R) break;
-        float f2[2];
-        simulate_two<FIELD>(J, (unsigned)ia, (unsigned)ib, (unsigned)m, f2[0], f2[1]);
+        unsigned idx[W];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (h == 1 && ib >= J.R) break;
-            const float v = payoff_of(J, tau, beta, C, f2[h]);
+        for (int w = 0; w < W; ++w) idx[w] = (unsigned)(ia + 32 * w);
+        float fw[W];
+        simulate_w<FIELD, W>(J, idx, (unsigned)m, fw);
+#pragma unroll
+        for (int h = 0; h < W; ++h) {
+            if (h > 0 && ia + 32 * h >= J.R) break;
+            const float v = payoff_of(J, tau, beta, C, fw[h]);
             n += 1.0f;
             const float delta = v - mean;
             mean += delta / n;
