@@ -64,7 +64,7 @@ static bt_status price_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int 
         J.out_put = mode == BT_MODE_PUT ? i : -1;
         J.N = opts[i].N;
         J.branches = b;
-        // suffix steps: b^L <= 2^12 entries in shared memory (binomial: the lattice pass's split)
+        // suffix steps: b^L <= 2^12 entries in shared memory (binomial: N - 10 steps, at most 12)
         int L = 0;
         int64_t nsuf = 1;
         while (L < J.N && nsuf * b <= (1 << BT_STEPS_MAX_L) && (b > 2 || L < exact_split_L(J.N))) {
