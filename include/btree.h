@@ -175,6 +175,16 @@ bt_status bt_exact_plan_partials(bt_exact_plan *plan, double *partials, int32_t 
 bt_status bt_exact_plan_job(const bt_exact_plan *plan, int32_t j, int32_t *opt_call, int32_t *opt_put,
                             int32_t *P, int32_t *L, int32_t *prefixes_per_item);
 bt_status bt_exact_plan_info_get(const bt_exact_plan *plan, bt_exact_plan_info *info);
+/* The split the exhaustive pass uses for one option priced alone at `prec`,
+ * computed on the host (no device, no context): P prefix steps and L suffix
+ * steps (P + L = N; Section 3's rank bits are the prefix), work items of
+ * prefixes_per_item consecutive prefixes, n_items = ceil(2^P /
+ * prefixes_per_item). Work item i covers the path indices [i ppi 2^L,
+ * (i + 1) ppi 2^L) (first step most significant). For ranks that compute
+ * their share of the items some other way than through a plan. Errors: as
+ * bt_price_exact's validation. Any pointer may be NULL. */
+bt_status bt_exact_split(const bt_option *opt, bt_precision prec, int32_t *P, int32_t *L, int32_t *prefixes_per_item,
+                         int64_t *n_items);
 /* Duration in milliseconds of the path-sum kernel of the most recent run,
  * measured with CUDA events recorded on that run's stream just before and
  * after the kernel launch. Synchronises on the end event. BT_EINVAL before

@@ -107,6 +107,8 @@ def lib():
         _proto(L, "bt_exact_plan_job", [_vp, _i32, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32),
                                         C.POINTER(_i32), C.POINTER(_i32)])
         _proto(L, "bt_exact_plan_info_get", [_vp, C.POINTER(bt_exact_plan_info)])
+        _proto(L, "bt_exact_split", [_vp, C.c_int, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32),
+                                     C.POINTER(C.c_int64)])
         _proto(L, "bt_exact_plan_destroy", [_vp], None)
         _proto(L, "bt_exact_plan_kernel_ms", [_vp, C.POINTER(C.c_float)])
         _proto(L, "bt_price_exact_noalloc", [_vp, _i32, C.c_int, _vp, _vp])
@@ -236,6 +238,14 @@ def bt_exact_plan_job(plan, j):
     _check(lib().bt_exact_plan_job(plan, j, *[C.byref(v) for v in vals]))
     keys = ("opt_call", "opt_put", "P", "L", "prefixes_per_item")
     return {k: v.value for k, v in zip(keys, vals)}
+
+
+def bt_exact_split(opt, prec=BT_PREC_FP32_COMP):
+    """The pass's split for one option priced alone (host only, no device)."""
+    a = options_array([opt])
+    P, L, ppi, n = _i32(), _i32(), _i32(), C.c_int64()
+    _check(lib().bt_exact_split(a.ctypes.data, prec, C.byref(P), C.byref(L), C.byref(ppi), C.byref(n)))
+    return {"P": P.value, "L": L.value, "prefixes_per_item": ppi.value, "n_items": n.value}
 
 
 def bt_exact_plan_kernel_ms(plan) -> float:

@@ -8,6 +8,8 @@
 #define BT_MAX_N_EXACT 40
 #define BT_MAX_L 13            // suffix steps held in a shared-memory table (lattice passes)
 #define BT_STEPS_MAX_L 12      // b^L <= 2^12 suffixes for trees given move by move (16-byte entries)
+#define BT_ARITH_CLS_MAX_N 27  // FP32 arithmetic-Asian jobs up to this depth sum each suffix as a class
+#define BT_ARITH_CLS_MAX_L 12  // ... with at most 2^12 classes of 16 bytes in shared memory
 #define BT_LOW_BITS 10         // a work item covers 2^10 consecutive prefixes
 #define BT_THREADS 256         // threads per block of the path-sum kernels
 #define BT_PT 4                // prefixes per thread (FP32 kernel): 256 * 4 = 2^10

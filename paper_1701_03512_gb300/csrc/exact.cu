@@ -22,7 +22,10 @@
 // The European, geometric and lookback payoffs take a table of recombined
 // suffix classes instead (k_class_tables, item32_cls): within an up-count
 // group their f_s depends on one integer key, so each class is evaluated once
-// per prefix in FP32-pair arithmetic and weighted by its multiplicity.
+// per prefix in FP32-pair arithmetic and weighted by its multiplicity. The
+// arithmetic Asian below 2^28 paths (N <= 27) takes the same pass with every
+// suffix its own class (k_tables writes that table): with fewer paths the
+// per-path roundings would not average below 1e-9.
 //
 // Rounding design of the FP32 path. The per-prefix scale lambda = 2^-e
 // (256 - h)/256, with 2^e bounding |tau + f| over the suffix range and h a
@@ -209,8 +212,11 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
     const bt_job J = jobs[j];
     const bt_jparams &Pj = prm[J.prm_off];
     const double u = Pj.u, d = Pj.d, lnu = Pj.lnu;
-    // class jobs get their suffix table from k_class_tables
-    const int64_t nsuf = J.cls ? 0 : 1ll << J.L, nsl = J.cls ? 0 : J.suf_len;
+    // class jobs get their suffix table from k_class_tables, except the
+    // arithmetic Asian's: its classes are its suffixes, one path each
+    const bool acls = J.cls && J.field == BT_F_ARITH;
+    const int64_t nsuf = (J.cls && !acls) ? 0 : 1ll << J.L;
+    const int64_t nsl = (J.cls && !acls) ? 0 : acls ? J.suf_len / 2 : J.suf_len;
     const int64_t nh = 1ll << J.H, nm = 1ll << J.M;
     const int64_t npow = 2 * J.N + 3;
     const int64_t total = nsuf + nsl + nh + nm + npow + J.geo_len;
@@ -241,6 +247,16 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
             default: v = exp((double)mn * lnu); break;
             }
             int pos = J.goff[k] + colex_rank(s);
+            if (acls) {  // class entry (f_hi, f_lo), (multiplicity 1, 0); with sufd, df/du as a pair
+                suf32[J.off_suf + 2 * pos] = split2(v);
+                suf32[J.off_suf + 2 * pos + 1] = make_float2(1.0f, 0.0f);
+                if (sufd) {
+                    const float2 dd = split2(fl / u);
+                    sufd[J.off_suf + 2 * pos] = dd.x;
+                    sufd[J.off_suf + 2 * pos + 1] = dd.y;
+                }
+                continue;
+            }
             if (sufd) {  // df_s/du
                 double dv;
                 switch (J.field) {
@@ -266,7 +282,11 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
         if (i < nsl) {  // padding slots of each up-count group
             int pos = (int)i, k = 0;
             while (k < J.L && pos >= J.goff[k + 1]) ++k;
-            if (pos - J.goff[k] >= binom_small(J.L, k)) {
+            if (pos - J.goff[k] >= binom_small(J.L, k) && acls) {  // zero-multiplicity classes
+                suf32[J.off_suf + 2 * pos] = make_float2(0.0f, 0.0f);
+                suf32[J.off_suf + 2 * pos + 1] = make_float2(0.0f, 0.0f);
+                if (sufd) sufd[J.off_suf + 2 * pos] = sufd[J.off_suf + 2 * pos + 1] = 0.0f;
+            } else if (pos - J.goff[k] >= binom_small(J.L, k)) {
                 if (prec == BT_PREC_FP64) suf64[J.off_suf + pos] = nan("");
                 else suf32[J.off_suf + pos] = make_float2(__int_as_float(0x7fc00000), 0.0f);
                 if (sufd) sufd[J.off_suf + pos] = 0.0f;
@@ -315,7 +335,7 @@ __global__ void k_tables(const bt_job *jobs, const bt_jparams *prm, int prec, fl
 #define BT_KEY_RANGE (2 * BT_KEY_SPAN + 1)
 __global__ void k_class_tables(const bt_job *jobs, const bt_jparams *prm, float2 *suf32, float *sufd) {
     const bt_job J = jobs[blockIdx.x];
-    if (!J.cls) return;
+    if (!J.cls || J.field == BT_F_ARITH) return;  // the arithmetic Asian's classes come from k_tables
     __shared__ int hist[(BT_MAX_L + 1) * BT_KEY_RANGE];
     for (int i = threadIdx.x; i < (J.L + 1) * BT_KEY_RANGE; i += blockDim.x) hist[i] = 0;
     __syncthreads();

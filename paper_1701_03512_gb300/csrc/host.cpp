@@ -261,8 +261,13 @@ static const int *class_counts(int field, int L) {
 }
 
 void fill_job_shape(bt_job &J, int N, int field, int mode, int prec) {
+    // Below 2^28 paths the per-path FP32 rounding of the arithmetic Asian
+    // averages over too few paths for 1e-9, so those jobs take the pair-sum
+    // class pass with every suffix its own class (multiplicity 1).
+    const bool arith_cls = prec == BT_PREC_FP32_COMP && field == BT_F_ARITH && N <= BT_ARITH_CLS_MAX_N;
     J.N = N;
     J.L = exact_split_L(N);
+    if (arith_cls) J.L = std::min(J.L, BT_ARITH_CLS_MAX_L);
     J.P = N - J.L;
     J.M = (J.P + 1) / 2;
     J.H = J.P - J.M;
@@ -277,13 +282,14 @@ void fill_job_shape(bt_job &J, int N, int field, int mode, int prec) {
     for (int k = J.L + 1; k < BT_MAX_L + 2; ++k) J.goff[k] = off;
     J.suf_len = off;
     J.cls = 0;
-    if (prec == BT_PREC_FP32_COMP && field_has_classes(field)) {
+    if (prec == BT_PREC_FP32_COMP && (field_has_classes(field) || arith_cls)) {
         // class table: goff in class units, two float2 slots per class
-        const int *cnt = class_counts(field, J.L);
+        const int *cnt = arith_cls ? nullptr : class_counts(field, J.L);
         off = 0;
         for (int k = 0; k <= J.L; ++k) {
             J.goff[k] = off;
-            off += (cnt[k] + BT_CLS_UNROLL - 1) / BT_CLS_UNROLL * BT_CLS_UNROLL;
+            const int c = arith_cls ? binom_host(J.L, k) : cnt[k];
+            off += (c + BT_CLS_UNROLL - 1) / BT_CLS_UNROLL * BT_CLS_UNROLL;
         }
         for (int k = J.L + 1; k < BT_MAX_L + 2; ++k) J.goff[k] = off;
         J.suf_len = 2 * off;
@@ -603,6 +609,24 @@ extern "C" bt_status bt_exact_plan_job(const bt_exact_plan *pl, int32_t j, int32
     if (P) *P = J.P;
     if (L) *L = J.L;
     if (ppi) *ppi = 1 << BT_LOW_BITS;
+    return BT_OK;
+}
+
+extern "C" bt_status bt_exact_split(const bt_option *opt, bt_precision prec, int32_t *P, int32_t *L, int32_t *ppi,
+                                    int64_t *n_items) {
+    if (!opt) return bt_fail(BT_EINVAL, "bt_exact_split: NULL option");
+    if (prec != BT_PREC_FP64 && prec != BT_PREC_FP32_COMP) return bt_fail(BT_EINVAL, "bad precision %d", (int)prec);
+    bt_status s = validate_option(opt, 0, BT_MAX_N_EXACT);
+    if (s != BT_OK) return s;
+    int field, mode;
+    payoff_field(opt->payoff, &field, &mode);
+    bt_job J;
+    memset(&J, 0, sizeof(J));
+    fill_job_shape(J, opt->N, field, mode, prec);
+    if (P) *P = J.P;
+    if (L) *L = J.L;
+    if (ppi) *ppi = 1 << BT_LOW_BITS;
+    if (n_items) *n_items = J.n_items;
     return BT_OK;
 }
 

@@ -29,14 +29,15 @@ MC_BITS, MC_R, MC_SEED = 4, 512, 7
 
 
 def exact_items(o):
-    """Work items of the exhaustive pass: item i covers prefixes
-    [i 2^10, (i+1) 2^10) of 2^P, all 2^L suffixes each, prefix bits first."""
-    N = o["N"]
-    L = max(1, min(13, N - 10))   # the library's split: L = clamp(N - 10, 1, 13)
-    P = N - L
-    n_items = max(1, -(-(1 << P) // (1 << 10)))
-    span = 1 << (10 + L)
-    return [(i * span, min((i + 1) * span, 1 << N)) for i in range(n_items)]
+    """Work items of the exhaustive pass (FP32_COMP), as the library splits
+    them (bt_exact_split, host only): item i covers the path indices
+    [i ppi 2^L, (i+1) ppi 2^L), prefix bits first."""
+    from paper_1701_03512_gb300 import build as b
+    b.build()
+    from paper_1701_03512_gb300 import btree as bt
+    sp = bt.bt_exact_split(o, bt.BT_PREC_FP32_COMP)
+    span = sp["prefixes_per_item"] << sp["L"]
+    return [(i * span, min((i + 1) * span, 1 << o["N"])) for i in range(sp["n_items"])]
 
 
 def oracle_exact_part(rank, world):

@@ -103,3 +103,25 @@ def test_options_array_roundtrip(bt):
     assert a.shape == (8,) and a["N"].tolist() == [32] * 8
     assert a["payoff"].tolist() == [2, 3] * 4
     assert np.allclose(a["S0"][::2], W.option_sets(0, 4)["S0"])
+
+
+def test_exact_split_needs_no_device(bt):
+    """The pass's prefix/suffix split (Section 3's rank bits as the prefix),
+    queried on the host: L = N - 10 up to 13 suffix steps; FP32 arithmetic
+    Asians up to N = 27 sum each suffix as a class, with at most 12."""
+    cases = [  # (N, payoff, precision) -> (P, L)
+        ((36, W.ASIAN_ARITH_CALL, bt.BT_PREC_FP32_COMP), (23, 13)),
+        ((27, W.ASIAN_ARITH_PUT, bt.BT_PREC_FP32_COMP), (15, 12)),
+        ((27, W.ASIAN_ARITH_PUT, bt.BT_PREC_FP64), (14, 13)),
+        ((27, W.ASIAN_GEO_CALL, bt.BT_PREC_FP32_COMP), (14, 13)),
+        ((20, W.ASIAN_ARITH_CALL, bt.BT_PREC_FP32_COMP), (10, 10)),
+        ((5, W.EURO_PUT, bt.BT_PREC_FP64), (4, 1)),
+    ]
+    for (N, pay, prec), (P, L) in cases:
+        sp = bt.bt_exact_split(W.opt(N, 100.0, 100.0, 0.05, 0.2, 1.0, pay), prec)
+        assert (sp["P"], sp["L"]) == (P, L), (N, pay, prec, sp)
+        assert sp["prefixes_per_item"] == 1024
+        assert sp["n_items"] == max(1, (1 << P) // 1024)
+    with pytest.raises(bt.BtError) as e:
+        bt.bt_exact_split(W.opt(41, 100.0, 100.0, 0.05, 0.2, 1.0, W.EURO_CALL))
+    assert e.value.status == bt.BT_EINVAL

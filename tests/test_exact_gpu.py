@@ -3,13 +3,12 @@
 Tolerances (relative, plus an absolute floor of 1e-12 * S0 for values that are
 (nearly) zero, where a relative bound has no meaning):
   FP64 kernel: 1e-12.
-  FP32_COMP kernel, arithmetic Asian: 1e-9 for N >= 28. Every path's payoff
-  is one correctly rounded FP32 value (relative error <= 2^-24); those errors
-  average out over many paths, so smaller trees get wider bands: 3e-9 for
-  N >= 20, 2e-8 for N >= 12, 1e-7 below.
-  FP32_COMP kernel, European, geometric and lookback payoffs: these are
-  summed over recombined suffix classes in FP32-pair arithmetic with no
-  per-path FP32 rounding, so 1e-9 holds at every N.
+  FP32_COMP kernel: 1e-9 at every N. From 2^28 paths the arithmetic Asian's
+  per-path pass rounds each path's payoff once in FP32 (relative error <=
+  2^-24) and those errors average out over the many paths; below 2^28 paths
+  it takes the class pass with each suffix its own class. The European,
+  geometric and lookback payoffs are summed over recombined suffix classes in
+  FP32-pair arithmetic with no per-path FP32 rounding.
 All calls go through the C ABI.
 """
 import math
@@ -25,15 +24,10 @@ TOL = {0: 1e-12, 1: 1e-9}   # BT_PREC_FP64, BT_PREC_FP32_COMP at N >= 28
 
 
 def tol(prec, N, payoff=2):
-    if prec == 0:
-        return 1e-12
-    if N >= 28 or payoff not in (2, 3):
-        return 1e-9
-    if N >= 20:
-        return 3e-9
-    if N >= 12:
-        return 2e-8
-    return 1e-7
+    """The accuracy contract: FP64 1e-12; FP32_COMP 1e-9 at every N (the
+    arithmetic Asian below 2^28 paths sums each suffix as a class in FP32
+    pairs, like the other payoffs)."""
+    return 1e-12 if prec == 0 else 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -321,17 +315,18 @@ def test_stated_error_covers_the_difference_to_the_oracle(bt, ctx, oracle, N):
 def test_probability_limit_of_the_fp32_path(bt, ctx, oracle):
     """min(p, 1-p) >= 0.004 is accepted in FP32 and matches the oracle within
     the stated error; below it FP32 is refused and FP64 still prices. At
-    p = 0.996 the all-up path carries 0.996^24 = 91 % of the value, so its one
-    FP32 rounding (up to 2^-24) does not average out: the stated error adds
-    6e-8 max(p, 1-p)^N to the contract's band, 5.8e-8 relative here."""
+    p = 0.996 the all-up path carries 0.996^28 = 89 % of the value, so its one
+    FP32 rounding (up to 2^-24) does not average out: the stated error of the
+    per-path pass adds 6e-8 max(p, 1-p)^N to the 1e-9 band, 5.5e-8 relative
+    here."""
     u = 1.05
     d = 1 / u
     for p, ok in ((0.004, True), (0.996, True), (0.0039, False)):
-        o = W.opt(24, 100.0, 100.0, 0.0, 0.2, 1.0, W.ASIAN_ARITH_CALL, W.TREE_EXPLICIT, u=u, d=d, p=p)
+        o = W.opt(28, 100.0, 100.0, 0.0, 0.2, 1.0, W.ASIAN_ARITH_CALL, W.TREE_EXPLICIT, u=u, d=d, p=p)
         if ok:
             r = ctx.price_exact([o], 1)[0]
             ref = oracle.exact(o)
-            stated = tol(1, 24) + 6e-8 * max(p, 1 - p) ** 24
+            stated = tol(1, 28) + 6e-8 * max(p, 1 - p) ** 28
             assert r["err_est"] == pytest.approx(stated * abs(r["value"]), rel=1e-12)
             assert abs(r["value"] - ref) <= r["err_est"] + 1e-12 * 100.0
         else:

@@ -59,7 +59,7 @@ def test_matches_oracle_pathwise_gradient(bt, ctx, oracle, payoff):
     val, grad = bt.bt_greeks_exact(ctx.h, opts)
     for i, o in enumerate(opts):
         v_ref, g_ref = oracle.greeks_crr(o)
-        assert abs(val[i] - v_ref) <= 3e-9 * abs(v_ref) + 1e-12 * o["S0"]
+        assert abs(val[i] - v_ref) <= 1e-9 * abs(v_ref) + 1e-12 * o["S0"]
         _close(grad[i], g_ref, 1e-6, (payoff, i))
 
 

@@ -19,9 +19,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _tol(prec, N):
-    if prec == 0:
-        return 1e-12
-    return 1e-9 if N >= 28 else 3e-9 if N >= 20 else 2e-8 if N >= 12 else 1e-7
+    return 1e-12 if prec == 0 else 1e-9
 
 
 @pytest.fixture(scope="module")
