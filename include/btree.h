@@ -68,7 +68,8 @@ typedef enum {
     BT_PREC_FP64 = 0,       /* every path in FP64                                    */
     BT_PREC_FP32_COMP = 1   /* path arithmetic in FP32 on coefficients carried as
                                FP32 pairs, group sums folded with error-free
-                               transformations, FP64 across blocks                 */
+                               transformations, FP64 across blocks; 1e-9
+                               relative for the exhaustive lattice sums          */
 } bt_precision;
 
 /* One pricing problem. 80 bytes, naturally aligned. */
@@ -86,11 +87,12 @@ typedef struct {
     double value;       /* discounted value V                                    */
     double err_est;     /* exact sums: stated bound on |V - V_exact| from
                            rounding, rel |V|: rel = 1e-12 in FP64; in FP32_COMP
-                           the band for the depth (1e-9 from N = 28, 3e-9 from
-                           20, 2e-8 from 12, 1e-7 below; 1e-9 for every N for
-                           the class-sum payoffs) plus, for the arithmetic
-                           Asian, 6e-8 max(p, 1-p)^N (one FP32 rounding of the
-                           heaviest path's share); MC: 0                     */
+                           1e-9 for the lattice passes at every N, and for the
+                           move-by-move passes the band by the number of paths
+                           (1e-9 from 2^28, 3e-9 from 2^20, 2e-8 binomial or
+                           5e-8 wider from 2^12, 1e-7 or 3e-7 below); plus,
+                           where each path is rounded once in FP32, 6e-8 times
+                           the likeliest path's probability; MC: 0           */
     double stderr_mc;   /* MC: standard error of `value`; exact sums: 0          */
     double var_plain;   /* MC: estimated variance of one undiscounted draw
                            V(X) (for plain-MC comparisons); exact sums: 0        */
