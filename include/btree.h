@@ -203,24 +203,27 @@ void bt_exact_plan_destroy(bt_exact_plan *plan);
  * N (<= 40), payoff, S0, K, rate and T (discount e^{-rate T}) are used;
  * tree_kind, sigma, u, d, p are ignored. The tree need not recombine: every
  * path is evaluated, with weight prod_t p_t^{x_t} (1 - p_t)^{1 - x_t}.
- * Requires 0 < d_t < u_t and 0 < p_t < 1 (BT_EINVAL), and for FP32_COMP
- * min(p_t, 1 - p_t) >= 0.004 (BT_EUNSUPPORTED). Every option is its own pass
- * (no call/put fusion). Results as bt_price_exact; synchronous on `stream`. */
+ * Requires 0 < d_t < u_t and 0 < p_t < 1 (BT_EINVAL), and for FP32_COMP on
+ * trees of 2^28 paths or more min(p_t, 1 - p_t) >= 0.004 (BT_EUNSUPPORTED).
+ * Every option is its own pass (no call/put fusion). Accuracy, results and
+ * errors as bt_price_exact_moves with b = 2; synchronous on `stream`. */
 bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, int32_t n, const double *steps,
                                bt_precision prec, bt_result *out, void *stream);
 /* The same affine passes (FP32_COMP or FP64) for trees with b = branches
  * (2..8) branches per node (the end of Section 3: trinomial and wider trees),
  * moves given as for bt_price_exact_branching: for each option's steps in
  * turn, b factors then b probabilities indexed by the digit (factors > 0,
- * probabilities in [0,1] summing to 1 within 1e-12: BT_EINVAL; FP32_COMP
- * needs every positive probability >= 0.004: BT_EUNSUPPORTED). b^N <= 2^42.
+ * probabilities in [0,1] summing to 1 within 1e-12: BT_EINVAL). b^N <= 2^42.
  * A path is N base-b digits, the first step most significant; paths = b^N.
  * The built-in payoffs only (for a plug-in, bt_price_exact_branching).
- * FP32_COMP relative accuracy by the b^N paths its per-path roundings
- * average over: 1e-9 from 2^28 paths, 3e-9 from 2^20, 5e-8 from 2^12, 3e-7
- * below (plus 1e-12 S0); a recombining tree (the same moves at every step) repeats equal
- * suffix values, which for the European, geometric and lookback payoffs can
- * correlate the per-path FP32 roundings: use FP64 there for 1e-9. */
+ * FP32_COMP: a tree of 2^28 paths or more runs the FP32 pass, which rounds
+ * every path once and needs every positive probability >= 0.004
+ * (BT_EUNSUPPORTED), 1e-9 relative (plus 1e-12 S0); smaller trees, whose
+ * roundings would not average under 1e-9, run the FP64 pass (err_est
+ * states 1e-12 for them). A recombining tree (the same moves at every step)
+ * repeats equal suffix values, which for the European, geometric and
+ * lookback payoffs can correlate the per-path FP32 roundings: use FP64 there
+ * for 1e-9 on large trees. */
 bt_status bt_price_exact_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t branches,
                                const double *moves, bt_precision prec, bt_result *out, void *stream);
 

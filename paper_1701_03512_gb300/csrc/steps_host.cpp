@@ -172,11 +172,56 @@ static bt_status price_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int 
     return rs;
 }
 
+// FP32_COMP rounds every path once (a tree given move by move has no classes),
+// and below 2^28 paths those roundings do not average under 1e-9: such
+// options are priced by the FP64 pass instead, which is cheap at that size.
+static bool fp32_pass_suffices(const bt_option &o, int b) { return (double)o.N * std::log2((double)b) >= 28.0 - 1e-9; }
+
+static bt_status price_moves_routed(bt_ctx *ctx, const bt_option *opts, int32_t n, int b, const double *moves,
+                                    bt_precision prec, bt_result *out, void *stream) {
+    if (prec != BT_PREC_FP32_COMP) return price_moves(ctx, opts, n, b, moves, prec, out, stream);
+    std::vector<int> grp[2];  // [0] FP64 (small trees), [1] FP32_COMP
+    std::vector<int64_t> first(n);
+    int64_t t = 0;
+    for (int i = 0; i < n; ++i) {
+        if (opts[i].N < 1 || opts[i].N > BT_MAX_N_EXACT)
+            return bt_fail(BT_EINVAL, "option %d: N=%d outside 1..%d", i, opts[i].N, BT_MAX_N_EXACT);
+        first[i] = t;
+        t += opts[i].N;
+        grp[fp32_pass_suffices(opts[i], b) ? 1 : 0].push_back(i);
+    }
+    for (int i = 0; i < n; ++i) {  // validation with the batch's own option indices
+        bt_status s = validate_scalars(opts[i], i);
+        if (s == BT_OK && (double)opts[i].N * std::log2((double)b) > 42.0 + 1e-9)
+            s = bt_fail(BT_EUNSUPPORTED, "option %d: %d^%d paths exceed 2^42", i, b, opts[i].N);
+        if (s == BT_OK)
+            s = validate_moves(moves + 2 * b * first[i], opts[i].N, b, i,
+                               fp32_pass_suffices(opts[i], b) ? prec : BT_PREC_FP64);
+        if (s != BT_OK) return s;
+    }
+    if (grp[0].empty()) return price_moves(ctx, opts, n, b, moves, prec, out, stream);
+    if (grp[1].empty()) return price_moves(ctx, opts, n, b, moves, BT_PREC_FP64, out, stream);
+    for (int g = 0; g < 2; ++g) {
+        std::vector<bt_option> o;
+        std::vector<double> mv;
+        for (int i : grp[g]) {
+            o.push_back(opts[i]);
+            mv.insert(mv.end(), moves + 2 * b * first[i], moves + 2 * b * (first[i] + opts[i].N));
+        }
+        std::vector<bt_result> r(o.size());
+        bt_status s = price_moves(ctx, o.data(), (int32_t)o.size(), b, mv.data(), g ? prec : BT_PREC_FP64, r.data(),
+                                  stream);
+        if (s != BT_OK) return s;
+        for (size_t k = 0; k < r.size(); ++k) out[grp[g][k]] = r[k];
+    }
+    return BT_OK;
+}
+
 extern "C" bt_status bt_price_exact_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t branches,
                                           const double *moves, bt_precision prec, bt_result *out, void *stream) {
     if (!ctx || !opts || !moves || !out || n < 1) return bt_fail(BT_EINVAL, "bt_price_exact_moves: bad arguments");
     if (branches < 2 || branches > 8) return bt_fail(BT_EINVAL, "branches = %d outside 2..8", branches);
-    return price_moves(ctx, opts, n, branches, moves, prec, out, stream);
+    return price_moves_routed(ctx, opts, n, branches, moves, prec, out, stream);
 }
 
 extern "C" bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, int32_t n, const double *steps,
@@ -196,5 +241,5 @@ extern "C" bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, in
         }
         o += opts[i].N;
     }
-    return price_moves(ctx, opts, n, 2, mv.data(), prec, out, stream);
+    return price_moves_routed(ctx, opts, n, 2, mv.data(), prec, out, stream);
 }

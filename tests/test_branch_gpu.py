@@ -102,12 +102,10 @@ def test_invalid_moves(bt, ctx):
 
 
 def _tol(prec, paths):
-    """FP64 1e-12; FP32_COMP by the number of paths the per-path roundings
-    average over: 1e-9 from 2^28, 3e-9 from 2^20, 5e-8 from 2^12, 3e-7 below."""
-    if prec == 0:
-        return 1e-12
-    n = math.log2(paths)
-    return 1e-9 if n >= 28 else 3e-9 if n >= 20 else 5e-8 if n >= 12 else 3e-7
+    """FP64 1e-12; FP32_COMP 1e-9: from 2^28 paths the FP32 pass, whose
+    per-path roundings average out over that many paths; smaller trees are
+    priced by the FP64 pass under FP32_COMP."""
+    return 1e-12 if prec == 0 else 1e-9
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -126,35 +124,48 @@ def test_affine_moves_pass_against_the_oracle(bt, ctx, oracle, prec, b, N):
 
 
 def test_affine_moves_probability_floor(bt, ctx, oracle):
-    """FP32_COMP refuses a branch probability in (0, 0.004) (its weights would
-    leave the FP32 pair range); FP64 takes it, and a zero probability (a
-    branch that never happens) is taken by both."""
+    """From 2^28 paths FP32_COMP runs the FP32 pass, which refuses a branch
+    probability in (0, 0.004) (its weights would leave the FP32 pair range);
+    FP64 takes it. A smaller tree runs the FP64 pass under FP32_COMP too, so
+    there the rare probability is taken. A zero probability (a branch that
+    never happens) is taken by the FP32 pass as well."""
     o = W.opt(6, 100.0, 100.0, 0.02, 0.2, 1.0, W.ASIAN_ARITH_CALL)
-    mv = W.branch_moves(5, 6, 3)
-    rare = mv.copy()
+    rare = W.branch_moves(5, 6, 3)
     rare[3, 3:] = [0.001, 0.5, 0.499]
+    r = bt.bt_price_exact_moves(ctx.h, [o], 3, [rare], bt.BT_PREC_FP32_COMP)[0]
+    assert abs(r["value"] - oracle.branch_price(o, rare, 3, 8)) <= 1e-12 * abs(r["value"])
+    assert r["err_est"] == pytest.approx(1e-12 * abs(r["value"]))      # priced by the FP64 pass
+    ob = W.opt(18, 100.0, 100.0, 0.02, 0.2, 1.0, W.ASIAN_ARITH_CALL)   # 3^18 = 3.9e8 paths
+    mvb = W.branch_moves(6, 18, 3)
+    rareb = mvb.copy()
+    rareb[9, 3:] = [0.001, 0.5, 0.499]
     with pytest.raises(bt.BtError) as e:
-        bt.bt_price_exact_moves(ctx.h, [o], 3, [rare], bt.BT_PREC_FP32_COMP)
+        bt.bt_price_exact_moves(ctx.h, [ob], 3, [rareb], bt.BT_PREC_FP32_COMP)
     assert e.value.status == bt.BT_EUNSUPPORTED
-    got = bt.bt_price_exact_moves(ctx.h, [o], 3, [rare], bt.BT_PREC_FP64)[0]["value"]
-    assert abs(got - oracle.branch_price(o, rare, 3, 8)) <= 1e-12 * abs(got)
-    never = mv.copy()
-    never[2, 3:] = [0.0, 0.5, 0.5]
-    ref = oracle.branch_price(o, never, 3, 8)
-    for prec in (bt.BT_PREC_FP64, bt.BT_PREC_FP32_COMP):
-        got = bt.bt_price_exact_moves(ctx.h, [o], 3, [never], prec)[0]["value"]
-        assert abs(got - ref) <= _tol(prec, 3 ** 6) * abs(ref) + 1e-12 * o["S0"], (prec, got, ref)
+    assert bt.bt_price_exact_moves(ctx.h, [ob], 3, [rareb], bt.BT_PREC_FP64)[0]["value"] > 0.0
+    never = mvb.copy()
+    never[9, 3:] = [0.0, 0.5, 0.5]
+    v64 = bt.bt_price_exact_moves(ctx.h, [ob], 3, [never], bt.BT_PREC_FP64)[0]["value"]
+    v32 = bt.bt_price_exact_moves(ctx.h, [ob], 3, [never], bt.BT_PREC_FP32_COMP)[0]["value"]
+    assert abs(v32 - v64) <= 1e-9 * abs(v64) + 1e-12 * ob["S0"], (v32, v64)
 
 
-def test_affine_moves_large_trinomial_fp32_against_fp64(bt, ctx):
-    """3^20 paths (3.5e9): the FP32 pass against the FP64 pass, and the
-    recombining-lattice European in FP64 against backward induction."""
-    N = 20
-    opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for pay in (2, 3) for K in (95.0, 105.0)]
-    moves = [W.branch_moves(700 + i, N, 3, 0.01, 0.05) for i in range(len(opts))]
-    v32 = bt.bt_price_exact_moves(ctx.h, opts, 3, moves, 1)["value"]
-    v64 = bt.bt_price_exact_moves(ctx.h, opts, 3, moves, 0)["value"]
-    assert np.all(np.abs(v32 - v64) <= 3e-9 * np.abs(v64))
+@pytest.mark.parametrize("b,N", [(3, 20), (4, 14), (8, 10)])   # 3.5e9, 2.7e8, 1.1e9 paths
+def test_affine_moves_large_trees_fp32_against_fp64(bt, ctx, b, N):
+    """From 2^28 paths FP32_COMP runs the FP32 pass: every payoff against
+    the FP64 pass (which the oracle pins on smaller trees) at the 1e-9
+    contract."""
+    opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for pay in range(8) for K in (95.0, 105.0)]
+    moves = [W.branch_moves(700 + 10 * b + i, N, b, 0.01, 0.05) for i in range(len(opts))]
+    ok = [not np.any((m[:, b:] > 0) & (m[:, b:] < 0.004)) for m in moves]   # the FP32 pass's floor
+    opts = [o for o, k in zip(opts, ok) if k]
+    moves = [m for m, k in zip(moves, ok) if k]
+    assert len(opts) >= 10
+    v32 = bt.bt_price_exact_moves(ctx.h, opts, b, moves, 1)
+    v64 = bt.bt_price_exact_moves(ctx.h, opts, b, moves, 0)["value"]
+    s0 = np.array([o["S0"] for o in opts])
+    assert np.all(np.abs(v32["value"] - v64) <= 1e-9 * np.abs(v64) + 1e-12 * s0)
+    assert np.all(np.abs(v32["value"] - v64) <= v32["err_est"] + 1e-12 * s0)
 
 
 def test_affine_moves_recombining_trinomial_fp64(bt, ctx, oracle):

@@ -11,9 +11,9 @@ pytestmark = pytest.mark.gpu
 
 
 def tol(prec, N):
-    if prec == 0:
-        return 1e-12
-    return 1e-9 if N >= 28 else 3e-9 if N >= 20 else 2e-8 if N >= 12 else 1e-7
+    """FP64 1e-12; FP32_COMP 1e-9 (trees below 2^28 paths are priced by the
+    FP64 pass under FP32_COMP, larger ones by the FP32 pass)."""
+    return 1e-12 if prec == 0 else 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -64,7 +64,7 @@ def test_fp32_against_fp64_at_large_n(bt, ctx):
     """N = 30 and 34 non-recombining trees (beyond the oracle's reach in a
     test): the FP32 pass against the FP64 pass, which the oracle pins below."""
     for N in (30, 34):
-        opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for pay in (2, 3, 4, 6, 7) for K in (95.0, 110.0)]
+        opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for pay in range(8) for K in (95.0, 110.0)]
         steps = [W.step_factors(500 + N + i, N, 0.01, 0.05) for i in range(len(opts))]
         v32 = bt.bt_price_exact_steps(ctx.h, opts, steps, 1)["value"]
         v64 = bt.bt_price_exact_steps(ctx.h, opts, steps, 0)["value"]
@@ -90,9 +90,15 @@ def test_invalid_steps(bt, ctx):
         assert e.value.status == bt.BT_EINVAL
     st = good.copy()
     st[1, 2] = 0.001
-    bt.bt_price_exact_steps(ctx.h, [o], [st], 0)          # FP64 takes it
+    v64 = bt.bt_price_exact_steps(ctx.h, [o], [st], 0)["value"][0]   # FP64 takes it
+    # so does FP32_COMP below 2^28 paths (it runs the FP64 pass there) ...
+    assert bt.bt_price_exact_steps(ctx.h, [o], [st], 1)["value"][0] == v64
+    # ... while the FP32 pass (2^28 paths and more) refuses p_t < 0.004
+    o28 = dict(o, N=28)
+    st28 = W.step_factors(2, 28)
+    st28[5, 2] = 0.001
     with pytest.raises(bt.BtError) as e:
-        bt.bt_price_exact_steps(ctx.h, [o], [st], 1)
+        bt.bt_price_exact_steps(ctx.h, [o28], [st28], 1)
     assert e.value.status == bt.BT_EUNSUPPORTED
     with pytest.raises(ValueError):
         bt.bt_price_exact_steps(ctx.h, [o], [good[:5]], 0)
