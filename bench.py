@@ -511,6 +511,17 @@ def extras_bench(bt, W, ctx, sms, fmax, with_cpu=True):
         out["generic_trinomial"]["cpu_baseline"] = _oracle_rate(
             lambda: O.branch_price(o3c, mv3c, 3, 1), 3.0 ** 13,
             "the arithmetic Asian call on a trinomial tree at N=13 (3^13 paths), one thread")
+    # the plain single-option case: arithmetic Asian call, N=20 (2^20 paths), FP64, one call with
+    # host arrays (its parity against the oracle, <= 1e-12, is asserted by the tests)
+    o1 = W.single_asian_n20()
+    t1 = _timed(lambda: bt.bt_price_exact(ctx.h, [o1], bt.BT_PREC_FP64), reps=5)
+    v1 = float(bt.bt_price_exact(ctx.h, [o1], bt.BT_PREC_FP64)[0]["value"])
+    out["single_asian_n20_fp64"] = {
+        "workload": "arithmetic Asian call, N=20, S0=K=100, rate 0.05, sigma 0.2, T=1, CRR, FP64, one option, "
+                    "host arrays in and out", "ms": 1e3 * t1, "value": v1, "paths_per_s": 2.0 ** 20 / t1}
+    if with_cpu:
+        out["single_asian_n20_fp64"]["cpu_baseline"] = _oracle_rate(
+            lambda: O.price_exhaustive(o1, 1), 2.0 ** 20, "the same option, all 2^20 paths, one thread")
     # the batched workload at N=32 in the all-FP64 kernel (the accuracy reference) beside FP32_COMP
     o32 = W.batched_exact_workload(32, 0, 64)
     t64 = _timed(lambda: bt.bt_price_exact(ctx.h, o32, bt.BT_PREC_FP64), reps=1)
