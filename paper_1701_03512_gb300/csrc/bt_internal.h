@@ -11,6 +11,7 @@
 #define BT_ARITH_CLS_MAX_N 27  // FP32 arithmetic-Asian jobs up to this depth sum each suffix as a class
 #define BT_ARITH_CLS_MAX_L 12  // ... with at most 2^12 classes of 16 bytes in shared memory
 #define BT_LOW_BITS 10         // a work item covers 2^10 consecutive prefixes
+#define BT_MIN_ITEM_BITS 5     // the split keeps >= 2^5 work items per option where it can
 #define BT_THREADS 256         // threads per block of the path-sum kernels
 #define BT_PT 4                // prefixes per thread (FP32 kernel): 256 * 4 = 2^10
 #define BT_PT64 4              // prefixes per thread (FP64 kernel)

@@ -210,7 +210,10 @@ void payoff_field(int payoff, int *field, int *mode) {
     }
 }
 
-int exact_split_L(int N) { return std::max(1, std::min(BT_MAX_L, N - BT_LOW_BITS)); }
+// L = clamp(N - 15, 1, 13): as many suffix steps as shared memory holds,
+// leaving at least 2^15 prefixes (32 work items) where the tree has them, so
+// that even one small option spreads over the SMs.
+int exact_split_L(int N) { return std::max(1, std::min(BT_MAX_L, N - BT_LOW_BITS - BT_MIN_ITEM_BITS)); }
 
 // Recombined suffix classes. For the geometric, European and lookback
 // payoffs the suffix factor f_s depends on the suffix only through one

@@ -64,10 +64,17 @@ static bt_status price_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int 
         J.out_put = mode == BT_MODE_PUT ? i : -1;
         J.N = opts[i].N;
         J.branches = b;
-        // suffix steps: b^L <= 2^12 entries in shared memory (binomial: N - 10 steps, at most 12)
+        // suffix steps: b^L <= 2^12 entries in shared memory, leaving at least
+        // 2^15 prefixes where the tree has them (binomial: the lattice split)
         int L = 0;
         int64_t nsuf = 1;
-        while (L < J.N && nsuf * b <= (1 << BT_STEPS_MAX_L) && (b > 2 || L < exact_split_L(J.N))) {
+        auto prefixes_after = [&](int l) {  // b^(N - l), saturated
+            double x = std::pow((double)b, (double)(J.N - l));
+            return x;
+        };
+        while (L < J.N && nsuf * b <= (1 << BT_STEPS_MAX_L) &&
+               (L == 0 || (b == 2 ? L < exact_split_L(J.N)
+                                  : prefixes_after(L + 1) >= (double)(1 << (BT_LOW_BITS + BT_MIN_ITEM_BITS))))) {
             nsuf *= b;
             ++L;
         }

@@ -107,14 +107,16 @@ def test_options_array_roundtrip(bt):
 
 def test_exact_split_needs_no_device(bt):
     """The pass's prefix/suffix split (Section 3's rank bits as the prefix),
-    queried on the host: L = N - 10 up to 13 suffix steps; FP32 arithmetic
-    Asians up to N = 27 sum each suffix as a class, with at most 12."""
+    queried on the host: L = N - 15 (at least 1, at most 13) suffix steps, so
+    an option keeps 2^5 work items of 2^10 prefixes where it can; FP32
+    arithmetic Asians up to N = 27 sum each suffix as a class, with at most 12."""
     cases = [  # (N, payoff, precision) -> (P, L)
         ((36, W.ASIAN_ARITH_CALL, bt.BT_PREC_FP32_COMP), (23, 13)),
+        ((28, W.ASIAN_ARITH_PUT, bt.BT_PREC_FP32_COMP), (15, 13)),
         ((27, W.ASIAN_ARITH_PUT, bt.BT_PREC_FP32_COMP), (15, 12)),
-        ((27, W.ASIAN_ARITH_PUT, bt.BT_PREC_FP64), (14, 13)),
-        ((27, W.ASIAN_GEO_CALL, bt.BT_PREC_FP32_COMP), (14, 13)),
-        ((20, W.ASIAN_ARITH_CALL, bt.BT_PREC_FP32_COMP), (10, 10)),
+        ((26, W.ASIAN_ARITH_PUT, bt.BT_PREC_FP64), (15, 11)),
+        ((30, W.ASIAN_GEO_CALL, bt.BT_PREC_FP32_COMP), (17, 13)),
+        ((20, W.ASIAN_ARITH_CALL, bt.BT_PREC_FP64), (15, 5)),
         ((5, W.EURO_PUT, bt.BT_PREC_FP64), (4, 1)),
     ]
     for (N, pay, prec), (P, L) in cases:

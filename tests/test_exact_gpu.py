@@ -111,9 +111,10 @@ def test_paper_exact_values(bt, ctx, golden_dir):
     assert abs(got[1] - g["values"]["lookback_fixed_put"]) <= 5e-4
 
 
-@pytest.mark.parametrize("N", [11, 12, 22, 23, 24, 25, 26])
+@pytest.mark.parametrize("N", [11, 12, 15, 16, 17, 22, 27, 28, 29])
 def test_split_boundaries(bt, ctx, oracle, N):
-    """Around the prefix/suffix split changes (L = N - 10 grows until 13 at N = 23, then P grows)."""
+    """Around the prefix/suffix split changes (L = N - 15 from N = 16, 13 from N = 28; the class pass
+    of the FP32 arithmetic Asian up to N = 27)."""
     opts = W.batch(N, W.option_sets(N, 2), list(range(8)))
     ref = [oracle.exact(o) if N > 18 else oracle.price_exhaustive(o, 8) for o in opts]
     for prec in (0, 1):
