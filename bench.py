@@ -522,6 +522,20 @@ def extras_bench(bt, W, ctx, sms, fmax, with_cpu=True):
     if with_cpu:
         out["single_asian_n20_fp64"]["cpu_baseline"] = _oracle_rate(
             lambda: O.price_exhaustive(o1, 1), 2.0 ** 20, "the same option, all 2^20 paths, one thread")
+    # the class pass: recombined classes (geometric, lookback, European) at N=36, and the small
+    # arithmetic Asians (N <= 27) whose every suffix is a class
+    oc = W.batch(36, W.option_sets(0, 64), (W.ASIAN_GEO_CALL, W.LOOKBACK_FIXED_CALL, W.EURO_PUT))
+    tc = _timed(lambda: bt.bt_price_exact(ctx.h, oc, bt.BT_PREC_FP32_COMP), reps=2)
+    out["class_payoffs_n36"] = {
+        "workload": "64 sets (seed 0) x {geometric Asian call, fixed-strike lookback call, European put}, N=36, "
+                    "FP32_COMP (recombined suffix classes), host arrays in and out",
+        "ms": 1e3 * tc, "payoff_paths_per_s": len(oc) * 2.0 ** 36 / tc}
+    oa = W.batched_exact_workload(24, 0, 64)
+    ta = _timed(lambda: bt.bt_price_exact(ctx.h, oa, bt.BT_PREC_FP32_COMP), reps=3)
+    out["small_arith_n24_class_pass"] = {
+        "workload": "64 sets (seed 0) x arithmetic Asian call+put, N=24, FP32_COMP (each suffix a class), "
+                    "host arrays in and out",
+        "ms": 1e3 * ta, "payoff_paths_per_s": len(oa) * 2.0 ** 24 / ta}
     # the batched workload at N=32 in the all-FP64 kernel (the accuracy reference) beside FP32_COMP
     o32 = W.batched_exact_workload(32, 0, 64)
     t64 = _timed(lambda: bt.bt_price_exact(ctx.h, o32, bt.BT_PREC_FP64), reps=1)
