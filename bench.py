@@ -286,7 +286,7 @@ def profiled_traffic(N):
 # ---------------------------------------------------------------------------
 # Serving: continuous batching vs plain pricing on one arrival stream
 # ---------------------------------------------------------------------------
-SERVING_CFG = dict(max_active=256, n_streams=3, max_items_per_launch=1216, device_budget_bytes=8 << 30)
+SERVING_CFG = dict(max_active=1024, n_streams=6, max_items_per_launch=4864, device_budget_bytes=8 << 30)
 
 
 def _lat(lat):

@@ -338,9 +338,9 @@ bt_status bt_philox4x32_10(bt_ctx *ctx, const uint32_t *ctr, const uint32_t *key
  * bt_price_exact, so each result is identical alone and in the mix. */
 typedef struct bt_server bt_server;
 typedef struct {
-    int32_t max_active;            /* requests admitted at once (slots); 0 = 256           */
-    int32_t n_streams;             /* path-sum launches in flight; 0 = 3                    */
-    int32_t max_items_per_launch;  /* 2^10-prefix work items per launch; 0 = 1216           */
+    int32_t max_active;            /* requests admitted at once (slots); 0 = 1024          */
+    int32_t n_streams;             /* path-sum launches in flight; 0 = 6                    */
+    int32_t max_items_per_launch;  /* 2^10-prefix work items per launch; 0 = 4864           */
     int32_t use_fp64;              /* precision bt_serve_replay submits with: 0 = FP32_COMP, 1 = FP64 */
     size_t device_budget_bytes;    /* device memory for slots, tables, partials; 0 = 8 GiB */
 } bt_server_cfg;

@@ -161,9 +161,9 @@ extern "C" bt_status bt_server_start(bt_ctx *ctx, const bt_server_cfg *cfg_in, b
     bt_server_cfg cfg;
     if (cfg_in) cfg = *cfg_in;
     else memset(&cfg, 0, sizeof(cfg));
-    if (cfg.max_active <= 0) cfg.max_active = 256;
-    if (cfg.n_streams <= 0) cfg.n_streams = 3;
-    if (cfg.max_items_per_launch <= 0) cfg.max_items_per_launch = 1216;
+    if (cfg.max_active <= 0) cfg.max_active = 1024;
+    if (cfg.n_streams <= 0) cfg.n_streams = 6;
+    if (cfg.max_items_per_launch <= 0) cfg.max_items_per_launch = 4864;  // 16 waves of 304 blocks
     if (cfg.device_budget_bytes == 0) cfg.device_budget_bytes = (size_t)8 << 30;
     if (cfg.use_fp64 != 0 && cfg.use_fp64 != 1) return bt_fail(BT_EINVAL, "bt_server_start: use_fp64 must be 0 or 1");
     if (cfg.max_active > 65536 || cfg.n_streams > 16)
