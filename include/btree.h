@@ -86,13 +86,11 @@ typedef struct {
 typedef struct {
     double value;       /* discounted value V                                    */
     double err_est;     /* exact sums: stated bound on |V - V_exact| from
-                           rounding, rel |V|: rel = 1e-12 in FP64; in FP32_COMP
-                           1e-9 for the lattice passes at every N, and for the
-                           move-by-move passes the band by the number of paths
-                           (1e-9 from 2^28, 3e-9 from 2^20, 2e-8 binomial or
-                           5e-8 wider from 2^12, 1e-7 or 3e-7 below); plus,
-                           where each path is rounded once in FP32, 6e-8 times
-                           the likeliest path's probability; MC: 0           */
+                           rounding, rel |V|: rel = 1e-12 in FP64 (and for the
+                           small move-by-move trees FP32_COMP prices in FP64);
+                           1e-9 in FP32_COMP, plus, where each path is rounded
+                           once in FP32, 6e-8 times the likeliest path's
+                           probability; MC: 0                                */
     double stderr_mc;   /* MC: standard error of `value`; exact sums: 0          */
     double var_plain;   /* MC: estimated variance of one undiscounted draw
                            V(X) (for plain-MC comparisons); exact sums: 0        */
