@@ -127,3 +127,22 @@ def test_exact_split_needs_no_device(bt):
     with pytest.raises(bt.BtError) as e:
         bt.bt_exact_split(W.opt(41, 100.0, 100.0, 0.05, 0.2, 1.0, W.EURO_CALL))
     assert e.value.status == bt.BT_EINVAL
+
+
+def test_plain_c_client(bt, tmp_path):
+    """tests/abi_client.c built with gcc against include/btree.h and linked
+    to lib/libbtree.so: the boundary from C, no Python in between."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(bt.LIB_PATH)
+    exe = str(tmp_path / "abi_client")
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                    os.path.join(root, "tests", "abi_client.c"), "-L", libdir, "-lbtree",
+                    "-Wl,-rpath," + libdir, "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert "split P=15 L=5" in r.stdout
