@@ -164,24 +164,29 @@ def options_array(opts) -> np.ndarray:
 
 # --- same names as the C ABI -------------------------------------------------
 def bt_version() -> str:
+    """Library version string (names the GPU architecture it was built for)."""
     return lib().bt_version().decode()
 
 
 def bt_create(device: int = 0, device_budget_bytes: int = 0):
+    """A context on CUDA device `device` (handle); raises BtError(BT_ECUDA) without a usable GPU."""
     h = _vp()
     _check(lib().bt_create(device, device_budget_bytes, C.byref(h)))
     return h
 
 
 def bt_destroy(ctx):
+    """Frees a context and everything it holds."""
     lib().bt_destroy(ctx)
 
 
 def bt_device_bytes(ctx) -> int:
+    """Device bytes the context holds right now."""
     return lib().bt_device_bytes(ctx)
 
 
 def bt_tree_params(opt):
+    """(u, d, p) of the option's tree (CRR, Seydel or explicit), computed on the host."""
     a = options_array(opt)
     u, d, p = C.c_double(), C.c_double(), C.c_double()
     _check(lib().bt_tree_params(a.ctypes.data, C.byref(u), C.byref(d), C.byref(p)))
@@ -189,6 +194,7 @@ def bt_tree_params(opt):
 
 
 def bt_price_exact(ctx, opts, prec=BT_PREC_FP32_COMP, stream=None) -> np.ndarray:
+    """Exact expected values over all 2^N paths; returns a RESULT_DTYPE array in option order."""
     a = options_array(opts)
     out = np.zeros(len(a), dtype=RESULT_DTYPE)
     _check(lib().bt_price_exact(ctx, a.ctypes.data, len(a), prec, out.ctypes.data, _stream(stream)))
@@ -196,6 +202,7 @@ def bt_price_exact(ctx, opts, prec=BT_PREC_FP32_COMP, stream=None) -> np.ndarray
 
 
 def bt_exact_plan_create(ctx, opts, prec=BT_PREC_FP32_COMP):
+    """Plans the exhaustive pass for a batch with the options resident on the device (handle)."""
     a = options_array(opts)
     h = _vp()
     _check(lib().bt_exact_plan_create(ctx, a.ctypes.data, len(a), prec, C.byref(h)))
@@ -203,20 +210,24 @@ def bt_exact_plan_create(ctx, opts, prec=BT_PREC_FP32_COMP):
 
 
 def bt_exact_plan_run(plan, stream=None):
+    """Enqueues one full pass of the plan on `stream` (asynchronous)."""
     _check(lib().bt_exact_plan_run(plan, _stream(stream)))
 
 
 def bt_exact_plan_run_shard(plan, shard, n_shards, stream=None):
+    """Enqueues the work items i with i % n_shards == shard (numbered across the batch)."""
     _check(lib().bt_exact_plan_run_shard(plan, shard, n_shards, _stream(stream)))
 
 
 def bt_exact_plan_info_get(plan) -> dict:
+    """Sizes of the plan: options, jobs, work items, payoff-paths, device and copy bytes."""
     i = bt_exact_plan_info()
     _check(lib().bt_exact_plan_info_get(plan, C.byref(i)))
     return {k: getattr(i, k) for k, _ in bt_exact_plan_info._fields_}
 
 
 def bt_exact_plan_read(plan, stream=None) -> np.ndarray:
+    """Synchronises and returns the plan's results (RESULT_DTYPE, option order)."""
     n = bt_exact_plan_info_get(plan)["n_options"]
     out = np.zeros(n, dtype=RESULT_DTYPE)
     _check(lib().bt_exact_plan_read(plan, out.ctypes.data, _stream(stream)))
@@ -224,6 +235,7 @@ def bt_exact_plan_read(plan, stream=None) -> np.ndarray:
 
 
 def bt_exact_plan_partials(plan, stream=None):
+    """Per-work-item undiscounted (call, put) partial sums, with each item's job and first prefix."""
     n = bt_exact_plan_info_get(plan)["n_items"]
     part = np.zeros((n, 2))
     job = np.zeros(n, dtype=np.int32)
@@ -234,6 +246,7 @@ def bt_exact_plan_partials(plan, stream=None):
 
 
 def bt_exact_plan_job(plan, j):
+    """Job j's option slots and split: opt_call, opt_put, P, L, prefixes_per_item."""
     vals = [_i32() for _ in range(5)]
     _check(lib().bt_exact_plan_job(plan, j, *[C.byref(v) for v in vals]))
     keys = ("opt_call", "opt_put", "P", "L", "prefixes_per_item")
@@ -249,12 +262,14 @@ def bt_exact_split(opt, prec=BT_PREC_FP32_COMP):
 
 
 def bt_exact_plan_kernel_ms(plan) -> float:
+    """Duration of the last run's path-sum kernel (CUDA events on its stream)."""
     ms = C.c_float()
     _check(lib().bt_exact_plan_kernel_ms(plan, C.byref(ms)))
     return ms.value
 
 
 def bt_exact_plan_destroy(plan):
+    """Frees a plan."""
     lib().bt_exact_plan_destroy(plan)
 
 
@@ -262,6 +277,7 @@ BT_MC_PARTITIONED, BT_MC_SHARED = 0, 1
 
 
 def bt_price_mc(ctx, opts, strata_bits, samples_per_stratum, seed, stream=None) -> np.ndarray:
+    """Partitioned Monte Carlo with 2^strata_bits strata (0: plain MC); value and standard error per option."""
     a = options_array(opts)
     out = np.zeros(len(a), dtype=RESULT_DTYPE)
     _check(lib().bt_price_mc(ctx, a.ctypes.data, len(a), strata_bits, samples_per_stratum, seed,
@@ -271,6 +287,8 @@ def bt_price_mc(ctx, opts, strata_bits, samples_per_stratum, seed, stream=None) 
 
 def bt_price_mc_ex(ctx, opts, strata_bits, samples_per_stratum, seed, kind=BT_MC_PARTITIONED,
                    with_strata=False, stream=None):
+    """bt_price_mc with the estimator kind (Partitioned or Shared-Sample) and optionally the
+    per-stratum (mean, variance, probability) statistics."""
     a = options_array(opts)
     out = np.zeros(len(a), dtype=RESULT_DTYPE)
     per = 1 if kind == BT_MC_SHARED else (1 << strata_bits)
@@ -307,10 +325,13 @@ def bt_plugin_compile(ctx, source: str):
 
 
 def bt_plugin_destroy(plugin):
+    """Frees a compiled plug-in."""
     lib().bt_plugin_destroy(plugin)
 
 
 def bt_price_exact_plugin(ctx, plugin, opts, steps=None, params=None, stream=None) -> np.ndarray:
+    """Every path through the plug-in's state machine (FP64); steps as bt_price_exact_steps or None
+    for each option's own tree, params [n][<= 8] handed to the plug-in."""
     a = options_array(opts)
     st = None
     if steps is not None:
@@ -381,6 +402,7 @@ def bt_price_mc_shard(ctx, opts, strata_bits, samples_per_stratum, seed, shard, 
 
 
 def bt_philox4x32_10(ctx, ctr, key) -> np.ndarray:
+    """Philox-4x32-10 on the device: counters [n][4] and keys [n][2] (uint32) -> words [n][4]."""
     c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
     k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
     out = np.zeros_like(c)
@@ -403,6 +425,8 @@ def _cfg(max_active=0, n_streams=0, max_items_per_launch=0, use_fp64=0, device_b
 
 
 def bt_server_start(ctx, **cfg):
+    """Starts a continuous-batching server (max_active, n_streams, max_items_per_launch, use_fp64,
+    device_budget_bytes; 0 = the defaults); returns its handle."""
     h = _vp()
     c = _cfg(**cfg)
     _check(lib().bt_server_start(ctx, C.byref(c), C.byref(h)))
@@ -410,6 +434,7 @@ def bt_server_start(ctx, **cfg):
 
 
 def bt_submit(srv, opt, prec=BT_PREC_FP32_COMP) -> int:
+    """Queues one option at precision `prec`; returns its ticket at once."""
     a = options_array(opt)
     t = C.c_uint64()
     _check(lib().bt_submit(srv, a.ctypes.data, prec, C.byref(t)))
@@ -417,12 +442,14 @@ def bt_submit(srv, opt, prec=BT_PREC_FP32_COMP) -> int:
 
 
 def bt_wait(srv, ticket, timeout_ms=60000) -> np.ndarray:
+    """Waits up to timeout_ms for the ticket's result and collects it (BtError(BT_ETIMEOUT) on expiry)."""
     out = np.zeros(1, dtype=RESULT_DTYPE)
     _check(lib().bt_wait(srv, ticket, timeout_ms, out.ctypes.data))
     return out[0]
 
 
 def bt_poll(srv, ticket):
+    """The ticket's result if it is done (collecting it), else None."""
     out = np.zeros(1, dtype=RESULT_DTYPE)
     done = _i32()
     _check(lib().bt_poll(srv, ticket, out.ctypes.data, C.byref(done)))
@@ -430,12 +457,14 @@ def bt_poll(srv, ticket):
 
 
 def bt_server_stats(srv) -> dict:
+    """Counts, p50/p99/mean/max latency, throughput and pool figures of the server so far."""
     st = bt_server_stats_t()
     _check(lib().bt_server_stats(srv, C.byref(st)))
     return {k: getattr(st, k) for k, _ in bt_server_stats_t._fields_}
 
 
 def bt_server_stop(srv):
+    """Finishes the queued requests and stops the server (no other call on it may run or follow)."""
     _check(lib().bt_server_stop(srv))
 
 
