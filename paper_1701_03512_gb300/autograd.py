@@ -8,7 +8,6 @@ rate, K)); the backward multiplies those derivatives by the upstream gradient.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import btree as bt
@@ -35,6 +34,7 @@ class ExactPrice(torch.autograd.Function):
 
 
 def exact_price(params: torch.Tensor, template, ctx_handle, prec=bt.BT_PREC_FP32_COMP) -> torch.Tensor:
+    """Values of the options (differentiable in params [n, 4] = S0, sigma, rate, K)."""
     if params.ndim != 2 or params.shape[1] != 4 or params.shape[0] != len(template):
         raise ValueError("params must be [n, 4] = (S0, sigma, rate, K) per option")
     return ExactPrice.apply(params, list(template), ctx_handle, prec)
