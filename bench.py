@@ -377,6 +377,28 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
         threads = cpu_threads()
         v_all, s_all = mc_oracle_all_cores(o, mb, R, 1, threads, strata_per_worker=32)
         cpu["all_cores"] = {"samples_per_s": v_all, "cores": threads, "kind": "oracle", "sample": s_all}
+    # the Shared-Sample estimator (the Remark of Section 4): the same R suffixes under every one
+    # of the 2^m prefixes, beside the Partitioned estimator with R suffixes per stratum
+    shared = None
+    try:
+        osh = W.opt(64, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
+        msh, rsh = 10, 1 << 14
+        bt.bt_price_mc_ex(ctx.h, [osh], msh, 1024, 3, bt.BT_MC_SHARED, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rs = bt.bt_price_mc_ex(ctx.h, [osh], msh, rsh, 4, bt.BT_MC_SHARED, stream=stream)[0]
+        e1.record(stream)
+        e1.synchronize()
+        tsh = e0.elapsed_time(e1) / 1e3
+        rpart = bt.bt_price_mc_ex(ctx.h, [osh], msh, rsh, 4, bt.BT_MC_PARTITIONED, stream=stream)[0]
+        shared = {"workload": "Shared-Sample MC, arithmetic Asian call, N=64, 2^10 prefixes x 2^14 shared suffixes",
+                  "ms": 1e3 * tsh, "suffixes_per_s": rsh / tsh, "prefix_suffix_pairs_per_s": (rsh << msh) / tsh,
+                  "value": float(rs["value"]), "stderr": float(rs["stderr_mc"]),
+                  "partitioned_same_R_per_stratum": {"value": float(rpart["value"]),
+                                                     "stderr": float(rpart["stderr_mc"])}}
+    except Exception as exc:  # keep the rest of the line if this extra entry fails
+        shared = {"error": str(exc)}
     # the other stratifications of the MC workload: N = 64 and 252, m = 10, 12, 16
     sweep = []
     for Ns in (64, 252):
@@ -396,6 +418,7 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
                           "variance_ratio": float((ps["stderr_mc"] / rs["stderr_mc"]) ** 2)})
     return {"workload": "Partitioned MC, arithmetic Asian call, N=%d, S0=K=100, rate 0.05, sigma 0.2, T=1, "
                         "2^%d strata x %d samples" % (N, mb, R), "cpu_baseline": cpu, "strata_sweep": sweep,
+            "shared_sample": shared,
             "samples_per_s": samples / t, "steps_per_s": steps / t, "ms": 1e3 * t,
             "value": float(r[0]["value"]), "stderr": float(r[0]["stderr_mc"]),
             "plain_mc_same_draws": {"value": float(plain["value"]), "stderr": float(plain["stderr_mc"]),
