@@ -696,31 +696,170 @@ double orc_greeks_crr(int N, int payoff, double S0, double K, double rate, doubl
 }
 
 /* ------------------------------------------------------------------------ */
-/* Time-varying trees: eq. f13 with per-step u_t, d_t, p_t                   */
+/* Trees given move by move: time-varying binomial trees (eq. f13 with       */
+/* per-step u_t, d_t, p_t) and trees with b branches per node (end of        */
+/* Section 3). One walk per path gives every payoff's quantity.              */
 /* ------------------------------------------------------------------------ */
-/* The payoff's quantity along path b: S_t = S_{t-1} * (x_t ? u_t : d_t). */
-static double steps_quantity(const orc_steps_model *m, uint64_t b) {
-    int N = m->N;
-    double sum = 0.0, lsum = 0.0, mx = -INFINITY, mn = INFINITY, St = m->S0;
-    for (int t = 1; t <= N; ++t) {
-        int x = (int)((b >> (N - t)) & 1u);
-        St = St * (x ? m->u[t - 1] : m->d[t - 1]);
-        sum += St;
-        lsum += log(St);
-        if (St > mx) mx = St;
-        if (St < mn) mn = St;
-    }
-    switch (m->payoff) {
-    case ORC_EURO_CALL: case ORC_EURO_PUT: return St;
-    case ORC_ARITH_CALL: case ORC_ARITH_PUT: return sum / (double)N;
-    case ORC_GEO_CALL: case ORC_GEO_PUT: return exp(lsum / (double)N);
-    case ORC_LOOK_CALL: return mx;
-    default: return mn;
+typedef struct { double SN, sum, lsum, mx, mn; } price_summary;
+
+/* The payoff's underlying quantity from a path's prices (the definitions of
+ * path_quantity above: S_N, the average, the geometric average, max, min over
+ * t = 1..N). */
+static double summary_quantity(int payoff, int N, const price_summary *s) {
+    switch (payoff) {
+    case ORC_EURO_CALL: case ORC_EURO_PUT: return s->SN;
+    case ORC_ARITH_CALL: case ORC_ARITH_PUT: return s->sum / (double)N;
+    case ORC_GEO_CALL: case ORC_GEO_PUT: return exp(s->lsum / (double)N);
+    case ORC_LOOK_CALL: return s->mx;
+    default: return s->mn;
     }
 }
 
+/* Walks one path: x[t-1] is the digit taken at step t, fac[(t-1) b + k] and
+ * lnf[(t-1) b + k] the factor of digit k at step t and its logarithm,
+ * prob[(t-1) b + k] its probability. S_t = S_{t-1} fac, ln S_t = ln S_{t-1} +
+ * ln fac (so sum_t ln S_t needs no logarithm per step), and the path's
+ * probability is the product of the probabilities of its moves. */
+static double walk_moves(int N, int b, double S0, const double *fac, const double *lnf, const double *prob,
+                         const int *x, price_summary *s) {
+    double St = S0, lS = log(S0), w = 1.0;
+    s->sum = 0.0; s->lsum = 0.0; s->mx = -INFINITY; s->mn = INFINITY;
+    for (int t = 1; t <= N; ++t) {
+        const int k = (t - 1) * b + x[t - 1];
+        St = St * fac[k];
+        lS = lS + lnf[k];
+        w = w * prob[k];
+        s->sum += St;
+        s->lsum += lS;
+        if (St > s->mx) s->mx = St;
+        if (St < s->mn) s->mn = St;
+    }
+    s->SN = St;
+    return w;
+}
+
+/* Digits of path index idx, the first step most significant (Section 3's rank
+ * digits come first): x[t-1] = digit of step t in base b. */
+static void path_digits(uint64_t idx, int N, int b, int *x) {
+    for (int t = N; t >= 1; --t) {
+        x[t - 1] = (int)(idx % (uint64_t)b);
+        idx /= (uint64_t)b;
+    }
+}
+
+/* A tree given move by move in one layout: b factors and b probabilities per
+ * step, with the logarithms of the factors. */
+typedef struct {
+    int N, b;
+    double S0;
+    double *fac, *lnf, *prob;
+} moves_t;
+
+static int moves_from_steps(const orc_steps_model *m, moves_t *mv) {
+    mv->N = m->N; mv->b = 2; mv->S0 = m->S0;
+    mv->fac = (double *)malloc(sizeof(double) * 2 * (size_t)m->N);
+    mv->lnf = (double *)malloc(sizeof(double) * 2 * (size_t)m->N);
+    mv->prob = (double *)malloc(sizeof(double) * 2 * (size_t)m->N);
+    if (!mv->fac || !mv->lnf || !mv->prob) return -1;
+    for (int t = 0; t < m->N; ++t) {   /* digit 0 = down, digit 1 = up */
+        mv->fac[2 * t] = m->d[t]; mv->fac[2 * t + 1] = m->u[t];
+        mv->prob[2 * t] = 1.0 - m->p[t]; mv->prob[2 * t + 1] = m->p[t];
+        mv->lnf[2 * t] = log(m->d[t]); mv->lnf[2 * t + 1] = log(m->u[t]);
+    }
+    return 0;
+}
+
+static int moves_from_branch(const orc_branch_model *m, moves_t *mv) {
+    const size_t n = (size_t)m->N * (size_t)m->b;
+    mv->N = m->N; mv->b = m->b; mv->S0 = m->S0;
+    mv->fac = (double *)malloc(sizeof(double) * n);
+    mv->lnf = (double *)malloc(sizeof(double) * n);
+    mv->prob = (double *)malloc(sizeof(double) * n);
+    if (!mv->fac || !mv->lnf || !mv->prob) return -1;
+    for (size_t i = 0; i < n; ++i) {
+        mv->fac[i] = m->f[i];
+        mv->prob[i] = m->q[i];
+        mv->lnf[i] = log(m->f[i]);
+    }
+    return 0;
+}
+
+static void moves_free(moves_t *mv) { free(mv->fac); free(mv->lnf); free(mv->prob); }
+
+/* eq. f14 (undiscounted) for several payoffs at once: for every path index in
+ * [lo, hi), in order, rebuild the path, cost it in O(N) (Listing 1's loop) and
+ * add p(x) V_j(x) to accumulator j, V_j the payoff pay[j] with strike K[j]. */
+static void moves_sum(const moves_t *mv, int n, const int32_t *pay, const double *K, uint64_t lo, uint64_t hi,
+                      nsum *acc) {
+    int x[64];
+    price_summary s;
+    double X[8];
+    if (lo >= hi) return;
+    path_digits(lo, mv->N, mv->b, x);
+    for (uint64_t idx = lo; idx < hi; ++idx) {
+        const double w = walk_moves(mv->N, mv->b, mv->S0, mv->fac, mv->lnf, mv->prob, x, &s);
+        for (int k = 0; k < 8; ++k) X[k] = NAN;   /* each payoff kind's quantity, once per path */
+        for (int j = 0; j < n; ++j) {
+            if (isnan(X[pay[j]])) X[pay[j]] = summary_quantity(pay[j], mv->N, &s);
+            nsum_add(&acc[j], w * payoff_of(pay[j], K[j], X[pay[j]]));
+        }
+        /* the next path index: add one in base b (the last step least significant) */
+        for (int t = mv->N - 1; t >= 0 && ++x[t] == mv->b; --t) x[t] = 0;
+    }
+}
+
+typedef struct {
+    const moves_t *mv; int n; const int32_t *pay; const double *K;
+    uint64_t lo, hi; nsum *acc;
+} moves_worker_t;
+
+static void *moves_worker_run(void *arg) {
+    moves_worker_t *w = (moves_worker_t *)arg;
+    for (int j = 0; j < w->n; ++j) { w->acc[j].s = 0.0; w->acc[j].c = 0.0; }
+    moves_sum(w->mv, w->n, w->pay, w->K, w->lo, w->hi, w->acc);
+    return NULL;
+}
+
+/* Section 3's partition: the b^N path indices split into M contiguous ranges
+ * (for M a power of b, rank m owns the paths whose leading digits are m's),
+ * partial sums added in rank order (eq. f15). out[j] = disc * sum for payoff j. */
+static void moves_price(const moves_t *mv, double disc, int n, const int32_t *pay, const double *K, int M,
+                        double *out) {
+    uint64_t total = 1;
+    for (int t = 0; t < mv->N; ++t) total *= (uint64_t)mv->b;
+    if (M < 1) M = 1;
+    if ((uint64_t)M > total) M = (int)total;
+    moves_worker_t *ws = (moves_worker_t *)calloc((size_t)M, sizeof(moves_worker_t));
+    nsum *accs = (nsum *)calloc((size_t)M * (size_t)n, sizeof(nsum));
+    pthread_t *th = (pthread_t *)calloc((size_t)M, sizeof(pthread_t));
+    int *started = (int *)calloc((size_t)M, sizeof(int));
+    for (int k = 0; k < M; ++k) {
+        ws[k].mv = mv; ws[k].n = n; ws[k].pay = pay; ws[k].K = K; ws[k].acc = accs + (size_t)k * n;
+        ws[k].lo = (uint64_t)(((unsigned __int128)total * (unsigned)k) / (unsigned)M);
+        ws[k].hi = (uint64_t)(((unsigned __int128)total * (unsigned)(k + 1)) / (unsigned)M);
+        started[k] = (M > 1) && pthread_create(&th[k], NULL, moves_worker_run, &ws[k]) == 0;
+        if (!started[k]) moves_worker_run(&ws[k]);
+    }
+    for (int k = 0; k < M; ++k)
+        if (started[k]) pthread_join(th[k], NULL);
+    for (int j = 0; j < n; ++j) {
+        nsum tot = {0.0, 0.0};
+        for (int k = 0; k < M; ++k) {      /* eq. f15 in rank order */
+            nsum_add(&tot, accs[(size_t)k * n + j].s);
+            nsum_add(&tot, accs[(size_t)k * n + j].c);
+        }
+        out[j] = disc * nsum_get(&tot);
+    }
+    free(ws); free(accs); free(th); free(started);
+}
+
 double orc_steps_path_payoff(const orc_steps_model *m, uint64_t b) {
-    return payoff_of(m->payoff, m->K, steps_quantity(m, b));
+    moves_t mv; int x[64]; price_summary s;
+    if (m->N < 1 || m->N > 62 || moves_from_steps(m, &mv)) return NAN;
+    path_digits(b, m->N, 2, x);
+    walk_moves(m->N, 2, m->S0, mv.fac, mv.lnf, mv.prob, x, &s);
+    moves_free(&mv);
+    return payoff_of(m->payoff, m->K, summary_quantity(m->payoff, m->N, &s));
 }
 
 double orc_steps_path_prob(const orc_steps_model *m, uint64_t b) {
@@ -733,130 +872,128 @@ double orc_steps_path_prob(const orc_steps_model *m, uint64_t b) {
     return w;
 }
 
-static void steps_sum(const orc_steps_model *m, uint64_t lo, uint64_t hi, nsum *acc) {
-    for (uint64_t b = lo; b < hi; ++b)
-        nsum_add(acc, orc_steps_path_prob(m, b) * orc_steps_path_payoff(m, b));
-}
-
 void orc_steps_sum_range(const orc_steps_model *m, uint64_t lo, uint64_t hi, double *sum, double *comp) {
-    nsum acc = {0.0, 0.0};
-    if (m->N > 62) { *sum = NAN; *comp = 0.0; return; }
-    steps_sum(m, lo, hi, &acc);
+    moves_t mv; nsum acc = {0.0, 0.0};
+    const int32_t pay = m->payoff;
+    if (m->N < 1 || m->N > 62 || moves_from_steps(m, &mv)) { *sum = NAN; *comp = 0.0; return; }
+    moves_sum(&mv, 1, &pay, &m->K, lo, hi, &acc);
+    moves_free(&mv);
     *sum = acc.s; *comp = acc.c;
 }
 
-typedef struct { const orc_steps_model *m; uint64_t lo, hi; nsum acc; } steps_worker_t;
+/* Section 3: M = 2^r workers (nthreads rounded down to a power of two), worker
+ * m owns B_m^N, the paths whose first r steps are m's bits. */
+static int pow2_workers(int N, int nthreads) {
+    int r = 0;
+    while ((2 << r) <= nthreads && r + 1 <= N) ++r;
+    return nthreads < 2 ? 1 : 1 << r;
+}
 
-static void *steps_worker_run(void *arg) {
-    steps_worker_t *w = (steps_worker_t *)arg;
-    w->acc.s = 0.0; w->acc.c = 0.0;
-    steps_sum(w->m, w->lo, w->hi, &w->acc);
-    return NULL;
+void orc_steps_price_multi(const orc_steps_model *m, int n, const int32_t *pay, const double *K, int nthreads,
+                           double *out) {
+    moves_t mv;
+    if (m->N < 1 || m->N > 62 || n < 1 || moves_from_steps(m, &mv)) {
+        for (int j = 0; j < n; ++j) out[j] = NAN;
+        return;
+    }
+    moves_price(&mv, m->disc, n, pay, K, pow2_workers(m->N, nthreads), out);
+    moves_free(&mv);
 }
 
 double orc_steps_price(const orc_steps_model *m, int nthreads) {
-    if (m->N < 1 || m->N > 62) return NAN;
-    int r = 0;
-    while ((2 << r) <= nthreads && r + 1 <= m->N) ++r;
-    if (nthreads < 2) r = 0;
-    const int M = 1 << r;
-    const uint64_t per = ((uint64_t)1 << m->N) >> r;   /* process m owns B_m^N (Section 3) */
-    steps_worker_t *ws = (steps_worker_t *)calloc((size_t)M, sizeof(steps_worker_t));
-    pthread_t *th = (pthread_t *)calloc((size_t)M, sizeof(pthread_t));
-    int *started = (int *)calloc((size_t)M, sizeof(int));
-    for (int k = 0; k < M; ++k) {
-        ws[k].m = m; ws[k].lo = (uint64_t)k * per; ws[k].hi = (uint64_t)(k + 1) * per;
-        started[k] = (M > 1) && pthread_create(&th[k], NULL, steps_worker_run, &ws[k]) == 0;
-        if (!started[k]) steps_worker_run(&ws[k]);
-    }
-    nsum tot = {0.0, 0.0};
-    for (int k = 0; k < M; ++k) {          /* eq. f15 in rank order */
-        if (started[k]) pthread_join(th[k], NULL);
-        nsum_add(&tot, ws[k].acc.s);
-        nsum_add(&tot, ws[k].acc.c);
-    }
-    free(ws); free(th); free(started);
-    return m->disc * nsum_get(&tot);
+    const int32_t pay = m->payoff;
+    double v;
+    orc_steps_price_multi(m, 1, &pay, &m->K, nthreads, &v);
+    return v;
 }
 
 /* ------------------------------------------------------------------------ */
 /* b-ary trees (end of Section 3)                                            */
 /* ------------------------------------------------------------------------ */
-static int branch_digit(const orc_branch_model *m, uint64_t idx, int t) {
-    /* digit of step t (1-based), the first step most significant */
-    uint64_t v = idx;
-    for (int k = m->N; k > t; --k) v /= (uint64_t)m->b;
-    return (int)(v % (uint64_t)m->b);
-}
-
-static double branch_quantity(const orc_branch_model *m, uint64_t idx) {
-    int N = m->N;
-    double sum = 0.0, lsum = 0.0, mx = -INFINITY, mn = INFINITY, St = m->S0;
-    for (int t = 1; t <= N; ++t) {
-        int x = branch_digit(m, idx, t);
-        St = St * m->f[(t - 1) * m->b + x];
-        sum += St;
-        lsum += log(St);
-        if (St > mx) mx = St;
-        if (St < mn) mn = St;
+static int branch_paths_ok(const orc_branch_model *m) {
+    if (m->N < 1 || m->N > 62 || m->b < 2) return 0;
+    uint64_t total = 1;
+    for (int t = 0; t < m->N; ++t) {
+        if (total > ((uint64_t)1 << 62) / (uint64_t)m->b) return 0;
+        total *= (uint64_t)m->b;
     }
-    switch (m->payoff) {
-    case ORC_EURO_CALL: case ORC_EURO_PUT: return St;
-    case ORC_ARITH_CALL: case ORC_ARITH_PUT: return sum / (double)N;
-    case ORC_GEO_CALL: case ORC_GEO_PUT: return exp(lsum / (double)N);
-    case ORC_LOOK_CALL: return mx;
-    default: return mn;
-    }
+    return 1;
 }
 
 double orc_branch_path_payoff(const orc_branch_model *m, uint64_t idx) {
-    return payoff_of(m->payoff, m->K, branch_quantity(m, idx));
+    moves_t mv; int x[64]; price_summary s;
+    if (!branch_paths_ok(m) || moves_from_branch(m, &mv)) return NAN;
+    path_digits(idx, m->N, m->b, x);
+    walk_moves(m->N, m->b, m->S0, mv.fac, mv.lnf, mv.prob, x, &s);
+    moves_free(&mv);
+    return payoff_of(m->payoff, m->K, summary_quantity(m->payoff, m->N, &s));
 }
 
 double orc_branch_path_prob(const orc_branch_model *m, uint64_t idx) {
+    int x[64];
+    if (!branch_paths_ok(m)) return NAN;
+    path_digits(idx, m->N, m->b, x);
     double w = 1.0;
-    for (int t = 1; t <= m->N; ++t) w *= m->q[(t - 1) * m->b + branch_digit(m, idx, t)];
+    for (int t = 1; t <= m->N; ++t) w *= m->q[(t - 1) * m->b + x[t - 1]];
     return w;
 }
 
-typedef struct { const orc_branch_model *m; uint64_t lo, hi; nsum acc; } branch_worker_t;
-
-static void *branch_worker_run(void *arg) {
-    branch_worker_t *w = (branch_worker_t *)arg;
-    w->acc.s = 0.0; w->acc.c = 0.0;
-    for (uint64_t i = w->lo; i < w->hi; ++i)
-        nsum_add(&w->acc, orc_branch_path_prob(w->m, i) * orc_branch_path_payoff(w->m, i));
-    return NULL;
+void orc_branch_price_multi(const orc_branch_model *m, int n, const int32_t *pay, const double *K, int nthreads,
+                            double *out) {
+    moves_t mv;
+    if (!branch_paths_ok(m) || n < 1 || moves_from_branch(m, &mv)) {
+        for (int j = 0; j < n; ++j) out[j] = NAN;
+        return;
+    }
+    moves_price(&mv, m->disc, n, pay, K, nthreads, out);
+    moves_free(&mv);
 }
 
 double orc_branch_price(const orc_branch_model *m, int nthreads) {
-    if (m->N < 1 || m->b < 2) return NAN;
+    const int32_t pay = m->payoff;
+    double v;
+    orc_branch_price_multi(m, 1, &pay, &m->K, nthreads, &v);
+    return v;
+}
+
+/* eq. expval: E[V(x)] = sum_x p(x) V(x) for any function V of the whole path,
+ * on a tree given move by move. Paths are visited in index order (Listing 1's
+ * loop); their prices and digits are handed to `fn` in blocks, and p(x) V(x)
+ * is added in path order with Neumaier compensation. One thread (the
+ * callback may not be reentrant). */
+#define ORC_FN_BLOCK 2048
+double orc_functional_price(const orc_branch_model *m, orc_payoff_fn fn, void *user) {
+    moves_t mv;
+    if (!branch_paths_ok(m) || !fn || moves_from_branch(m, &mv)) return NAN;
+    const int N = m->N, b = m->b;
     uint64_t total = 1;
-    for (int t = 0; t < m->N; ++t) {
-        if (total > ((uint64_t)1 << 62) / (uint64_t)m->b) return NAN;
-        total *= (uint64_t)m->b;
+    for (int t = 0; t < N; ++t) total *= (uint64_t)b;
+    double *S = (double *)malloc(sizeof(double) * ORC_FN_BLOCK * (size_t)N);
+    int32_t *X = (int32_t *)malloc(sizeof(int32_t) * ORC_FN_BLOCK * (size_t)N);
+    double *w = (double *)malloc(sizeof(double) * ORC_FN_BLOCK);
+    double *v = (double *)malloc(sizeof(double) * ORC_FN_BLOCK);
+    nsum acc = {0.0, 0.0};
+    int x[64];
+    for (uint64_t lo = 0; lo < total; lo += ORC_FN_BLOCK) {
+        const int cnt = (int)((total - lo) < ORC_FN_BLOCK ? (total - lo) : ORC_FN_BLOCK);
+        for (int i = 0; i < cnt; ++i) {
+            path_digits(lo + (uint64_t)i, N, b, x);   /* path index lo + i, first step most significant */
+            double St = m->S0, wi = 1.0;
+            for (int t = 1; t <= N; ++t) {
+                const int k = (t - 1) * b + x[t - 1];
+                St = St * mv.fac[k];
+                wi = wi * mv.prob[k];
+                S[(size_t)i * N + t - 1] = St;
+                X[(size_t)i * N + t - 1] = x[t - 1];
+            }
+            w[i] = wi;
+        }
+        fn(user, cnt, N, S, X, v);
+        for (int i = 0; i < cnt; ++i) nsum_add(&acc, w[i] * v[i]);
     }
-    int M = nthreads < 1 ? 1 : nthreads;
-    if ((uint64_t)M > total) M = (int)total;
-    branch_worker_t *ws = (branch_worker_t *)calloc((size_t)M, sizeof(branch_worker_t));
-    pthread_t *th = (pthread_t *)calloc((size_t)M, sizeof(pthread_t));
-    int *started = (int *)calloc((size_t)M, sizeof(int));
-    for (int k = 0; k < M; ++k) {
-        ws[k].m = m;
-        ws[k].lo = total / (uint64_t)M * (uint64_t)k + (k < (int)(total % (uint64_t)M) ? (uint64_t)k : total % (uint64_t)M);
-        ws[k].hi = total / (uint64_t)M * (uint64_t)(k + 1) +
-                   (k + 1 < (int)(total % (uint64_t)M) ? (uint64_t)(k + 1) : total % (uint64_t)M);
-        started[k] = (M > 1) && pthread_create(&th[k], NULL, branch_worker_run, &ws[k]) == 0;
-        if (!started[k]) branch_worker_run(&ws[k]);
-    }
-    nsum tot = {0.0, 0.0};
-    for (int k = 0; k < M; ++k) {
-        if (started[k]) pthread_join(th[k], NULL);
-        nsum_add(&tot, ws[k].acc.s);
-        nsum_add(&tot, ws[k].acc.c);
-    }
-    free(ws); free(th); free(started);
-    return m->disc * nsum_get(&tot);
+    free(S); free(X); free(w); free(v);
+    moves_free(&mv);
+    return m->disc * nsum_get(&acc);
 }
 
 double orc_branch_european_backward(const orc_branch_model *m) {

@@ -140,6 +140,13 @@ void orc_steps_sum_range(const orc_steps_model *m, uint64_t lo, uint64_t hi, dou
  * down to a power of two), partials added in rank order (eq. f14, f15). */
 double orc_steps_price(const orc_steps_model *m, int nthreads);
 
+/* Several payoffs of one time-varying tree in one enumeration: out[j] is the
+ * discounted value of payoff pay[j] with strike K[j] (the model's own payoff
+ * and K are not used), each path walked once for all of them; same partition
+ * and reduction order as orc_steps_price. */
+void orc_steps_price_multi(const orc_steps_model *m, int n, const int32_t *pay, const double *K, int nthreads,
+                           double *out);
+
 /* Trees with b branches per node (the end of Section 3: the partition of the
  * paths applies to trees with more than two branches, e.g. trinomial trees).
  * A path is N digits x_t in 0..b-1, the first step the most significant digit
@@ -160,6 +167,19 @@ double orc_branch_path_prob(const orc_branch_model *m, uint64_t idx);
  * (Section 3's partition by leading digits when nthreads is a power of b),
  * partials added in rank order. Needs b^N < 2^63. */
 double orc_branch_price(const orc_branch_model *m, int nthreads);
+/* As orc_steps_price_multi for a b-ary tree: out[j] for payoff pay[j], strike K[j]. */
+void orc_branch_price_multi(const orc_branch_model *m, int n, const int32_t *pay, const double *K, int nthreads,
+                            double *out);
+/* eq. expval for a payoff given as a function of the whole path: the value
+ * e^{-qT} sum_x p(x) V(x) on the tree m (a time-varying binomial tree is b = 2
+ * with factors (d_t, u_t) and probabilities (1 - p_t, p_t); m->payoff and m->K
+ * are not used). Paths are visited in index order and passed to fn in blocks:
+ * fn(user, count, N, S, x, v) receives S[i N + t - 1] = S_t and x[i N + t - 1]
+ * = the digit of step t of the block's path i, and writes its payoff to v[i].
+ * Single-threaded. */
+typedef void (*orc_payoff_fn)(void *user, int32_t count, int32_t N, const double *S, const int32_t *x, double *v);
+double orc_functional_price(const orc_branch_model *m, orc_payoff_fn fn, void *user);
+
 /* European value by backward induction on a recombining b-ary lattice with
  * the same moves at every step (f[0], q[0] used for all steps; f_k = u^{k - c}
  * with c = (b-1)/2 so that node (t, j) has price S0 u^{j - c t}). */

@@ -50,6 +50,11 @@ class BranchModel(C.Structure):
                 ("f", C.POINTER(C.c_double)), ("q", C.POINTER(C.c_double))]
 
 
+# fn(user, count, N, S, x, v) of orc_functional_price
+PAYOFF_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                        C.POINTER(C.c_double))
+
+
 def lib():
     global _lib
     with _lock:
@@ -89,6 +94,11 @@ def lib():
             L.orc_branch_path_prob.argtypes = [pb, u64]; L.orc_branch_path_prob.restype = d
             L.orc_branch_price.argtypes = [pb, C.c_int]; L.orc_branch_price.restype = d
             L.orc_branch_european_backward.argtypes = [pb]; L.orc_branch_european_backward.restype = d
+            pi32 = C.POINTER(C.c_int32)
+            L.orc_steps_price_multi.argtypes = [ps, C.c_int, pi32, pd, C.c_int, pd]
+            L.orc_branch_price_multi.argtypes = [pb, C.c_int, pi32, pd, C.c_int, pd]
+            L.orc_functional_price.argtypes = [pb, PAYOFF_FN, C.c_void_p]
+            L.orc_functional_price.restype = d
             _lib = L
     return _lib
 
@@ -293,3 +303,61 @@ def mc_stratum(o: dict, mb: int, z: int, Rm: int, seed: int, stream: int = 0):
     a, b, c = C.c_double(), C.c_double(), C.c_double()
     lib().orc_mc_stratum(C.byref(model(o)), mb, z, Rm, seed, stream, C.byref(a), C.byref(b), C.byref(c))
     return a.value, b.value, c.value
+
+
+def _pay_strikes(pays_ks):
+    pays = np.ascontiguousarray([int(p) for p, _ in pays_ks], dtype=np.int32)
+    ks = np.ascontiguousarray([float(k) for _, k in pays_ks], dtype=np.float64)
+    return pays, ks
+
+
+def steps_price_multi(o: dict, steps, pays_ks, nthreads: int = 8) -> np.ndarray:
+    """Discounted values of every (payoff, K) in pays_ks on one time-varying
+    tree (o's S0, rate, T, N), each path walked once for all of them."""
+    m, keep = steps_model(o, steps)
+    pays, ks = _pay_strikes(pays_ks)
+    out = np.zeros(len(pays))
+    lib().orc_steps_price_multi(C.byref(m), len(pays), pays.ctypes.data_as(C.POINTER(C.c_int32)),
+                                ks.ctypes.data_as(C.POINTER(C.c_double)), nthreads,
+                                out.ctypes.data_as(C.POINTER(C.c_double)))
+    return out
+
+
+def branch_price_multi(o: dict, moves, b: int, pays_ks, nthreads: int = 8) -> np.ndarray:
+    m, keep = branch_model(o, moves, b)
+    pays, ks = _pay_strikes(pays_ks)
+    out = np.zeros(len(pays))
+    lib().orc_branch_price_multi(C.byref(m), len(pays), pays.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 ks.ctypes.data_as(C.POINTER(C.c_double)), nthreads,
+                                 out.ctypes.data_as(C.POINTER(C.c_double)))
+    return out
+
+
+def functional_price(o: dict, moves, b: int, V) -> float:
+    """eq. expval for a payoff V given as a Python function of whole paths:
+    V(S, x) receives S[count, N] (S_1..S_N) and x[count, N] (the digits) of a
+    block of consecutive paths and returns their payoffs. moves as for
+    branch_price (for a time-varying binomial tree: (d_t, u_t, 1-p_t, p_t))."""
+    m, keep = branch_model(o, moves, b)
+    err = []
+
+    def cb(user, count, N, S, x, v):
+        try:
+            s = np.ctypeslib.as_array(S, shape=(count, N))
+            xs = np.ctypeslib.as_array(x, shape=(count, N))
+            np.ctypeslib.as_array(v, shape=(count,))[:] = np.asarray(V(s, xs), dtype=np.float64)
+        except Exception as e:  # surfaced after the call
+            err.append(e)
+            np.ctypeslib.as_array(v, shape=(count,))[:] = np.nan
+
+    fn = PAYOFF_FN(cb)
+    r = lib().orc_functional_price(C.byref(m), fn, None)
+    if err:
+        raise err[0]
+    return r
+
+
+def steps_as_moves(steps) -> np.ndarray:
+    """(u_t, d_t, p_t) rows as binomial moves (d_t, u_t, 1 - p_t, p_t): digit 1 = up."""
+    st = np.asarray(steps, dtype=np.float64)
+    return np.stack([st[:, 1], st[:, 0], 1.0 - st[:, 2], st[:, 2]], axis=1)

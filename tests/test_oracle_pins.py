@@ -516,3 +516,104 @@ def test_paper_table5_variances_loosely(oracle, golden_dir):
             assert abs(v - 82.115) <= 4 * math.sqrt(se2), (kind, M, v, se2)
             ref = g[kind]["var"][i]
             assert 0.5 * ref <= se2 <= 2.0 * ref, (kind, M, se2, ref)
+
+
+# ---------------------------------------------------------------------------
+# Several payoffs per enumeration, and payoffs given as functions of the path
+# ---------------------------------------------------------------------------
+ALL_PAYOFF_STRIKES = [(pay, K) for pay in range(8) for K in (92.0, 106.0)]
+
+
+def test_steps_multi_matches_numpy_brute_force(oracle):
+    """Every payoff and two strikes from one walk of the time-varying tree,
+    each against the independent numpy enumeration."""
+    N = 11
+    steps = W.step_factors(31, N)
+    o = W.opt(N, 100.0, 100.0, 0.04, 0.2, 1.3, W.EURO_CALL)
+    got = oracle.steps_price_multi(o, steps, ALL_PAYOFF_STRIKES, 4)
+    for (pay, K), g in zip(ALL_PAYOFF_STRIKES, got):
+        ref = _numpy_steps(dict(o, payoff=pay, K=K), steps)
+        assert g == pytest.approx(ref, rel=1e-13, abs=1e-13), (pay, K)
+
+
+@pytest.mark.parametrize("b,N", [(3, 8), (4, 6)])
+def test_branch_multi_matches_numpy_brute_force(oracle, b, N):
+    moves = W.branch_moves(40 + b, N, b)
+    o = W.opt(N, 100.0, 100.0, 0.03, 0.2, 1.0, W.EURO_CALL)
+    got = oracle.branch_price_multi(o, moves, b, ALL_PAYOFF_STRIKES, 3)
+    for (pay, K), g in zip(ALL_PAYOFF_STRIKES, got):
+        ref = _numpy_branch(dict(o, payoff=pay, K=K), moves, b)
+        assert g == pytest.approx(ref, rel=1e-13, abs=1e-13), (b, pay, K)
+
+
+def test_multi_partition_does_not_change_the_sum(oracle):
+    """The rank partition (1, 2, 4, 8 workers) changes only the rounding order."""
+    N = 14
+    steps = W.step_factors(12, N)
+    o = W.opt(N, 100.0, 100.0, 0.04, 0.2, 1.0, W.EURO_CALL)
+    ref = oracle.steps_price_multi(o, steps, ALL_PAYOFF_STRIKES, 1)
+    for M in (2, 4, 8):
+        assert np.allclose(oracle.steps_price_multi(o, steps, ALL_PAYOFF_STRIKES, M), ref, rtol=1e-14, atol=1e-14)
+
+
+def test_functional_constant_and_end_price_closed_forms(oracle):
+    """V = 1 sums the path probabilities (to e^{-qT}); V = S_N gives
+    e^{-qT} S0 prod_t g_t with g_t = sum_k f_tk q_tk (independent steps)."""
+    for b, N, moves in ((2, 10, oracle.steps_as_moves(W.step_factors(6, 10))), (3, 7, W.branch_moves(8, 7, 3))):
+        o = W.opt(N, 100.0, 0.0, 0.05, 0.2, 1.2, W.EURO_CALL)
+        disc = math.exp(-0.05 * 1.2)
+        one = oracle.functional_price(o, moves, b, lambda S, x: np.ones(len(S)))
+        assert one == pytest.approx(disc, rel=1e-14)
+        g = np.sum(moves[:, :b] * moves[:, b:], axis=1)
+        end = oracle.functional_price(o, moves, b, lambda S, x: S[:, -1])
+        assert end == pytest.approx(disc * 100.0 * np.prod(g), rel=1e-13)
+
+
+def test_functional_digits_and_prices_agree(oracle):
+    """The digits handed to the payoff are the path index's base-b digits
+    (first step most significant) and the prices their running products."""
+    b, N = 3, 5
+    moves = W.branch_moves(9, N, b)
+    seen = []
+
+    def V(S, x):
+        seen.append((S.copy(), x.copy()))
+        return np.zeros(len(S))
+    oracle.functional_price(W.opt(N, 100.0, 0.0, 0.0, 0.2, 1.0, W.EURO_CALL), moves, b, V)
+    S = np.concatenate([s for s, _ in seen])
+    x = np.concatenate([d for _, d in seen])
+    idx = np.arange(b ** N)
+    want = (idx[:, None] // (b ** (N - 1 - np.arange(N)))[None, :]) % b
+    assert np.array_equal(x, want)
+    f = moves[:, :b][np.arange(N)[None, :], want]
+    assert np.allclose(S, 100.0 * np.cumprod(f, axis=1), rtol=1e-15)
+
+
+@pytest.mark.parametrize("payoff", [W.ASIAN_ARITH_CALL, W.LOOKBACK_FIXED_PUT, W.ASIAN_GEO_PUT, W.EURO_CALL])
+def test_functional_restated_payoffs_match_numpy_brute_force(oracle, payoff):
+    """Built-in payoffs written as path functions agree with the independent
+    numpy enumeration (and so with the walk oracle)."""
+    N, K = 12, 101.0
+    steps = W.step_factors(17, N)
+    o = W.opt(N, 100.0, K, 0.04, 0.2, 1.0, payoff)
+    V = {W.ASIAN_ARITH_CALL: lambda S, x: np.maximum(S.mean(axis=1) - K, 0.0),
+         W.LOOKBACK_FIXED_PUT: lambda S, x: np.maximum(K - S.min(axis=1), 0.0),
+         W.ASIAN_GEO_PUT: lambda S, x: np.maximum(K - np.exp(np.log(S).mean(axis=1)), 0.0),
+         W.EURO_CALL: lambda S, x: np.maximum(S[:, -1] - K, 0.0)}[payoff]
+    got = oracle.functional_price(o, oracle.steps_as_moves(steps), 2, V)
+    assert got == pytest.approx(_numpy_steps(o, steps), rel=1e-13, abs=1e-13)
+
+
+def test_functional_barrier_against_numpy_brute_force(oracle):
+    """A path-dependent payoff outside the built-ins: an up-and-out call."""
+    N, K, B = 12, 98.0, 112.0
+    steps = W.step_factors(23, N)
+    o = W.opt(N, 100.0, K, 0.04, 0.3, 1.0, W.EURO_CALL)
+    got = oracle.functional_price(o, oracle.steps_as_moves(steps), 2,
+                                  lambda S, x: np.where(S.max(axis=1) >= B, 0.0, np.maximum(S[:, -1] - K, 0.0)))
+    bb = np.arange(1 << N, dtype=np.int64)
+    xx = ((bb[:, None] >> (N - 1 - np.arange(N))[None, :]) & 1).astype(bool)
+    S = 100.0 * np.cumprod(np.where(xx, steps[:, 0], steps[:, 1]), axis=1)
+    w = np.prod(np.where(xx, steps[:, 2], 1.0 - steps[:, 2]), axis=1)
+    v = np.where(S.max(axis=1) >= B, 0.0, np.maximum(S[:, -1] - K, 0.0))
+    assert got == pytest.approx(math.exp(-0.04) * math.fsum(w * v), rel=1e-13)
