@@ -85,12 +85,14 @@ typedef struct {
 
 typedef struct {
     double value;       /* discounted value V                                    */
-    double err_est;     /* exact sums: stated bound on |V - V_exact| from
-                           rounding, rel |V|: rel = 1e-12 in FP64 (and for the
-                           small move-by-move trees FP32_COMP prices in FP64);
-                           1e-9 in FP32_COMP, plus, where each path is rounded
-                           once in FP32, 6e-8 times the likeliest path's
-                           probability; MC: 0                                */
+    double err_est;     /* exact sums: the stated error of V from rounding,
+                           rel |V|: rel = 1e-12 in FP64 (and for the
+                           move-by-move trees FP32_COMP prices in FP64);
+                           1e-9 in FP32_COMP. Values below 1e-3 S0 carry
+                           1e-12 S0 absolute as well. For the FP32 passes
+                           that round each path once this is the measured
+                           envelope of averaged roundings, not a bound;
+                           MC: 0                                              */
     double stderr_mc;   /* MC: standard error of `value`; exact sums: 0          */
     double var_plain;   /* MC: estimated variance of one undiscounted draw
                            V(X) (for plain-MC comparisons); exact sums: 0        */
@@ -128,7 +130,12 @@ bt_status bt_tree_params(const bt_option *opt, double *u, double *d, double *p);
  * fixed order (eq. f15). An arithmetic or geometric Asian or a European call
  * immediately followed by the put of identical parameters (or the reverse) is
  * evaluated in one pass over the paths; each still counts its own 2^N paths.
- * out[0..n) receives the results in input order. Synchronous on `stream`.
+ * FP32_COMP rounds each path once in FP32 only for the arithmetic Asian on
+ * trees of 2^28 paths or more with at least 2^27 effective paths,
+ * 1 / sum_x p(x)^2 = (p^2 + (1-p)^2)^-N; every other option (and the other
+ * payoffs always) is summed over suffix classes in FP32 pairs with no
+ * per-path rounding. out[0..n) receives the results in input order.
+ * Synchronous on `stream`.
  * Errors: BT_EINVAL (bad option, message names the index: N < 1 or N > 40,
  * S0 <= 0, K < 0, T <= 0, sigma <= 0, p outside (0,1), u <= d, a non-finite
  * value), BT_EUNSUPPORTED (FP32_COMP with min(p,1-p) < 0.004, whose weights
@@ -201,10 +208,12 @@ void bt_exact_plan_destroy(bt_exact_plan *plan);
  * N (<= 40), payoff, S0, K, rate and T (discount e^{-rate T}) are used;
  * tree_kind, sigma, u, d, p are ignored. The tree need not recombine: every
  * path is evaluated, with weight prod_t p_t^{x_t} (1 - p_t)^{1 - x_t}.
- * Requires 0 < d_t < u_t and 0 < p_t < 1 (BT_EINVAL), and for FP32_COMP on
- * trees of 2^28 paths or more min(p_t, 1 - p_t) >= 0.004 (BT_EUNSUPPORTED).
- * Every option is its own pass (no call/put fusion). Accuracy, results and
- * errors as bt_price_exact_moves with b = 2; synchronous on `stream`. */
+ * Requires 0 < d_t < u_t and 0 < p_t < 1 (BT_EINVAL), and for the FP32
+ * pass (see bt_price_exact_moves) min(p_t, 1 - p_t) >= 0.004
+ * (BT_EUNSUPPORTED). A call immediately followed by the put of the same
+ * field, tree (identical steps) and strike, or the reverse, is one pass.
+ * Accuracy, results and errors as bt_price_exact_moves with b = 2;
+ * synchronous on `stream`. */
 bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, int32_t n, const double *steps,
                                bt_precision prec, bt_result *out, void *stream);
 /* The same affine passes (FP32_COMP or FP64) for trees with b = branches
@@ -214,14 +223,15 @@ bt_status bt_price_exact_steps(bt_ctx *ctx, const bt_option *opts, int32_t n, co
  * probabilities in [0,1] summing to 1 within 1e-12: BT_EINVAL). b^N <= 2^42.
  * A path is N base-b digits, the first step most significant; paths = b^N.
  * The built-in payoffs only (for a plug-in, bt_price_exact_branching).
- * FP32_COMP: a tree of 2^28 paths or more runs the FP32 pass, which rounds
- * every path once and needs every positive probability >= 0.004
- * (BT_EUNSUPPORTED), 1e-9 relative (plus 1e-12 S0); smaller trees, whose
- * roundings would not average under 1e-9, run the FP64 pass (err_est
- * states 1e-12 for them). A recombining tree (the same moves at every step)
- * repeats equal suffix values, which for the European, geometric and
- * lookback payoffs can correlate the per-path FP32 roundings: use FP64 there
- * for 1e-9 on large trees. */
+ * A call immediately followed by the put of the same field, moves and
+ * strike (or the reverse) is one pass. FP32_COMP: the FP32 pass, which
+ * rounds every path once, runs a tree of 2^28 paths or more with at least
+ * 2^27 effective paths (1 / sum_x p(x)^2 = prod_t 1 / sum_k q_tk^2) whose
+ * suffix values do not repeat (on average at most eight suffixes per
+ * distinct value: a recombining tree repeats end prices, level sums and
+ * extremes); it needs every positive probability >= 0.004 (BT_EUNSUPPORTED)
+ * and meets 1e-9 relative (plus 1e-12 S0). Every other option runs the FP64
+ * pass (err_est then states 1e-12). */
 bt_status bt_price_exact_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t branches,
                                const double *moves, bt_precision prec, bt_result *out, void *stream);
 

@@ -9,6 +9,16 @@
 #define BT_MAX_L 13            // suffix steps held in a shared-memory table (lattice passes)
 #define BT_STEPS_MAX_L 12      // b^L <= 2^12 suffixes for trees given move by move (16-byte entries)
 #define BT_ARITH_CLS_MAX_N 27  // FP32 arithmetic-Asian jobs up to this depth sum each suffix as a class
+// The FP32 passes that round every path once average those roundings over
+// the tree's effective number of paths, n_eff = 1 / sum_x p(x)^2 (2^N for a
+// balanced binomial tree, (p^2 + (1-p)^2)^-N for the lattice, prod_t 1 /
+// sum_k q_tk^2 for a tree given move by move). They are used only where
+// log2(n_eff) reaches this bound; other trees take a pass that rounds no
+// single path (the pair-sum class pass of the lattice, or FP64 for trees
+// given move by move).
+#ifndef BT_PER_PATH_MIN_NEFF_LOG2
+#define BT_PER_PATH_MIN_NEFF_LOG2 27.0
+#endif
 #define BT_ARITH_CLS_MAX_L 12  // ... with at most 2^12 classes of 16 bytes in shared memory
 #define BT_LOW_BITS 10         // a work item covers 2^10 consecutive prefixes
 #define BT_MIN_ITEM_BITS 5     // the split keeps >= 2^5 work items per option where it can

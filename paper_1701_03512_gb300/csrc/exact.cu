@@ -786,19 +786,12 @@ __global__ void k_finalize(const bt_job *jobs, const bt_jparams *prm, int n_jobs
     if (lane == 0) {
         const bt_jparams &P = prm[J.prm_off];
         const double disc = P.disc;
-        // stated error: FP64 1e-12; FP32 the accuracy contract by the number
-        // of paths (class sums carry no per-path rounding: 1e-9), plus one
-        // FP32 rounding (2^-24) of the likeliest path's share, which no
-        // averaging removes when the tree's mass sits on a few paths
-        double rel = 1e-12;
-        if (prec != BT_PREC_FP64 && J.cls) {
-            rel = 1e-9;
-        } else if (prec != BT_PREC_FP64) {  // one FP32 rounding per path: the band by log2(paths)
-            const bool wide = J.branches > 2;
-            const double bits = wide ? (double)J.N * log2((double)J.branches) : (double)J.N;
-            rel = bits >= 28 ? 1e-9 : bits >= 20 ? 3e-9 : bits >= 12 ? (wide ? 5e-8 : 2e-8) : (wide ? 3e-7 : 1e-7);
-            rel += 6.0e-8 * P.wmax;
-        }
+        // stated error: FP64 1e-12; FP32_COMP 1e-9. The host gives the FP32
+        // passes that round paths one by one only trees of 2^28 paths or
+        // more with at least 2^BT_PER_PATH_MIN_NEFF_LOG2 effective paths
+        // (the others go to passes without per-path rounding), where the
+        // roundings average under 1e-9; class sums round no single path.
+        const double rel = prec == BT_PREC_FP64 ? 1e-12 : 1e-9;
         const int64_t paths = 1ll << J.N;
         if (J.out_call >= 0) {
             bt_result r;
@@ -863,17 +856,17 @@ static size_t exact_smem(int prec) {
     return prec == BT_PREC_FP64 ? (size_t)BT_SUF_MAX * sizeof(double) : (size_t)BT_SUF_MAX * sizeof(float2);
 }
 
+// Persistent grid of the path-sum kernel: SMs x resident blocks. Returns the
+// negated cudaError_t if a query fails (the global error state is not read,
+// so an earlier error of the caller's own is neither reported nor cleared).
 extern "C" int bt_exact_grid_size(int prec, int device) {
     int sms = 0, per = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    size_t sm = exact_smem(prec);
-    if (prec == BT_PREC_FP64) {
-        cudaFuncSetAttribute(k_exact64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_exact64, BT_THREADS, sm);
-    } else {
-        cudaFuncSetAttribute(k_exact32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_exact32, BT_THREADS, sm);
-    }
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const size_t sm = exact_smem(prec);
+    const void *k = prec == BT_PREC_FP64 ? (const void *)k_exact64 : (const void *)k_exact32;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BT_THREADS, sm);
+    if (e != cudaSuccess) return -(int)e;
     if (per < 1) per = 1;
     if (sms < 1) sms = 1;
     return sms * per;

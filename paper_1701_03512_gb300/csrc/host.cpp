@@ -70,10 +70,11 @@ extern "C" bt_status bt_create(int device, size_t budget, bt_ctx **out) {
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
     c->grid32 = bt_exact_grid_size(BT_PREC_FP32_COMP, device);
     c->grid64 = bt_exact_grid_size(BT_PREC_FP64, device);
-    if ((e = cudaGetLastError()) != cudaSuccess) {
+    if (c->grid32 < 0 || c->grid64 < 0) {
+        const int err = c->grid32 < 0 ? -c->grid32 : -c->grid64;
         cudaStreamDestroy(c->stream);
         delete c;
-        return bt_cuda_fail(e, "bt_create: kernel attributes");
+        return bt_cuda_fail(err, "bt_create: kernel attributes");
     }
     *out = c;
     return BT_OK;
@@ -263,11 +264,21 @@ static const int *class_counts(int field, int L) {
     return table[field][L];
 }
 
-void fill_job_shape(bt_job &J, int N, int field, int mode, int prec) {
+bool tree_skewed(const bt_option &o) {
+    double u, d, p;
+    if (host_tree(&o, &u, &d, &p) != BT_OK) return false;
+    const double neff_log2 = -(double)o.N * std::log2(p * p + (1.0 - p) * (1.0 - p));
+    return neff_log2 < BT_PER_PATH_MIN_NEFF_LOG2;
+}
+
+void fill_job_shape(bt_job &J, int N, int field, int mode, int prec, bool skewed) {
     // Below 2^28 paths the per-path FP32 rounding of the arithmetic Asian
-    // averages over too few paths for 1e-9, so those jobs take the pair-sum
-    // class pass with every suffix its own class (multiplicity 1).
-    const bool arith_cls = prec == BT_PREC_FP32_COMP && field == BT_F_ARITH && N <= BT_ARITH_CLS_MAX_N;
+    // averages over too few paths for 1e-9, and so it does on a skewed tree
+    // (fewer than 2^BT_PER_PATH_MIN_NEFF_LOG2 effective paths): those jobs
+    // take the pair-sum class pass with every suffix its own class
+    // (multiplicity 1), which rounds no single path.
+    const bool arith_cls =
+        prec == BT_PREC_FP32_COMP && field == BT_F_ARITH && (N <= BT_ARITH_CLS_MAX_N || skewed);
     J.N = N;
     J.L = exact_split_L(N);
     if (arith_cls) J.L = std::min(J.L, BT_ARITH_CLS_MAX_L);
@@ -330,7 +341,7 @@ void plan_one_job(const bt_option *opts, int n, int i, bt_job *J, int *step, int
             *step = 2;
         }
     }
-    fill_job_shape(*J, opts[i].N, field, mode, prec);
+    fill_job_shape(*J, opts[i].N, field, mode, prec, tree_skewed(opts[i]));
 }
 
 struct bt_exact_plan {
@@ -399,7 +410,7 @@ bt_status plan_jobs(const bt_option *opts, int n, int prec, std::vector<bt_job> 
                 step = 2;
             }
         }
-        fill_job_shape(J, opts[i].N, field, mode, prec);
+        fill_job_shape(J, opts[i].N, field, mode, prec, tree_skewed(opts[i]));
         J.item_begin = items;
         J.item_offset = 0;
         J.part_off = items;
@@ -625,7 +636,7 @@ extern "C" bt_status bt_exact_split(const bt_option *opt, bt_precision prec, int
     payoff_field(opt->payoff, &field, &mode);
     bt_job J;
     memset(&J, 0, sizeof(J));
-    fill_job_shape(J, opt->N, field, mode, prec);
+    fill_job_shape(J, opt->N, field, mode, prec, tree_skewed(*opt));
     if (P) *P = J.P;
     if (L) *L = J.L;
     if (ppi) *ppi = 1 << BT_LOW_BITS;

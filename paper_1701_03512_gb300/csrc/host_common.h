@@ -31,7 +31,11 @@ bt_status host_tree(const bt_option *o, double *u, double *d, double *p);
 bt_status validate_option(const bt_option *o, int idx, int max_n);
 int exact_split_L(int N);
 void payoff_field(int payoff, int *field, int *mode);
-void fill_job_shape(bt_job &J, int N, int field, int mode, int prec);
+// true if the tree has fewer than 2^BT_PER_PATH_MIN_NEFF_LOG2 effective
+// paths (the per-path FP32 pass then does not meet 1e-9; the option takes a
+// pass that rounds no single path). Needs a validated option.
+bool tree_skewed(const bt_option &o);
+void fill_job_shape(bt_job &J, int N, int field, int mode, int prec, bool skewed);
 bt_status plan_jobs(const bt_option *opts, int n, int prec, std::vector<bt_job> &jobs, int64_t *n_items,
                     int64_t *payoff_paths, int64_t *path_evals, int max_n);
 void plan_one_job(const bt_option *opts, int n, int i, bt_job *J, int *step, int prec);

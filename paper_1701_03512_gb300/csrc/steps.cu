@@ -12,15 +12,24 @@
 // (geometric), rho_L (European), max_j or min_j rho_j (lookback). What
 // changes is the weight: w(x) = w_q w_s with w_s the product over the suffix
 // of p_t or 1 - p_t, a different number for every suffix. So each path's
-// payoff is multiplied by its suffix weight (one more multiply-add per path)
-// instead of summing an up-count group before one multiplication.
+// payoff is multiplied by its suffix weight and accumulated in one FMA
+// instead of summing an up-count group before one multiplication. A call and
+// a put of the same tree and strike share the pass (and the two FMAs of the
+// affine form).
 //
 // Prefix states come from two-level tables over the steps 1..H and H+1..P
 // (end factor and its inverse, backward-relative partial sum, extreme
 // relative prices, geometric factor and its inverse, weight; FP64 and as FP32
 // pairs), composed per prefix in pair arithmetic. The FP32 path keeps the
 // rounding design of exact.cu (scaled affine form, exact lambda f_hi + A_hi,
-// one rounding per payoff); the weight enters as w_hi z + w_lo z.
+// one rounding per payoff). The weight enters as one FP32 number per suffix,
+// rounded from FP64 by error diffusion along ascending f_s (k_steps_weights):
+// the rounding residuals r_s = w_s - w32_s then have every partial sum over
+// a run of consecutive f_s bounded by one FP32 ulp of the largest weight, and
+// because a payoff is max(+-(tau + f_s), 0) -- an integral over thresholds of
+// the indicator of f_s above (below) the threshold -- sum_s r_s payoff_s is
+// bounded by that ulp times the payoff range (summation by parts) instead
+// of growing with the number of suffixes.
 //
 // A job reuses bt_job: off_pow is the index of its first step in the move
 // array (2b doubles per step: the b factors, then the b probabilities),
@@ -202,6 +211,72 @@ __global__ void k_steps_tables(const bt_job *jobs, const bt_jparams *prm, const 
     }
 }
 
+// FP32 suffix weights by error diffusion (one block per job, FP32 tables):
+// the entries (f_hi, -f_lo, w_hi, w_lo) written by k_steps_tables are sorted
+// by f = f_hi + f_lo (bitonic sort in shared memory, padding keys +inf), then
+// one thread walks them in ascending f carrying the rounding residual:
+// w32 = RN_f32(w + carry), carry = w + carry - w32, so that the residuals of
+// any run of consecutive f telescope to the difference of two carries, each
+// at most half an FP32 ulp. The entry keeps (f_hi, -f_lo, w32, 0).
+#define BT_SORT_N (1 << BT_STEPS_MAX_L)
+__global__ void __launch_bounds__(1024) k_steps_weights(const bt_job *jobs, float4 *suf32) {
+    const bt_job J = jobs[blockIdx.x];
+    __shared__ double key[BT_SORT_N];
+    __shared__ int16_t idx[BT_SORT_N];
+    const int n = (int)J.n_suffix;
+    int np = 1;
+    while (np < n) np <<= 1;
+    float4 *tab = suf32 + J.off_suf;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        if (i < n) {
+            const float4 e = tab[i];
+            key[i] = (double)e.x - (double)e.y;   // f_hi - (-f_lo), exact in FP64
+        } else {
+            key[i] = __longlong_as_double(0x7ff0000000000000ll);   // +inf after every suffix
+        }
+        idx[i] = (int16_t)i;
+    }
+    __syncthreads();
+    for (int k = 2; k <= np; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < np; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l <= i) continue;
+                const double a = key[i], c = key[l];
+                const bool asc = (i & k) == 0;
+                if (asc ? a > c : a < c) {
+                    key[i] = c;
+                    key[l] = a;
+                    const int16_t t = idx[i];
+                    idx[i] = idx[l];
+                    idx[l] = t;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {   // the weights in ascending f
+        const float4 e = tab[idx[r]];
+        key[r] = (double)e.z + (double)e.w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double carry = 0.0;
+        for (int r = 0; r < n; ++r) {
+            const double target = key[r] + carry;
+            const float w32 = __double2float_rn(target);
+            carry = target - (double)w32;
+            key[r] = (double)w32;
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        float4 &e = tab[idx[r]];
+        e.z = (float)key[r];
+        e.w = 0.0f;
+    }
+}
+
 // Per-prefix affine form and weight in FP32 pairs.
 struct sstate {
     df32 tau, beta, cst, w;
@@ -253,27 +328,22 @@ __device__ __forceinline__ sstate steps_state(const bt_job &J, const bt_jparams 
     return r;
 }
 
-// One work item, FP32: per path y = lambda f_hi + A_hi, c = lambda (-f_lo) - A_lo,
-// z = sat(+-(y - c)), weighted z w_hi + z w_lo, eight-wide tree, TwoSum into
-// the prefix's running sum; prefixes combined in pairs, the block in FP64.
-// Weighted payoffs/lambda of eight suffixes under one prefix, summed by an
-// eight-wide tree: y = lambda f_hi + A_hi, c = lambda (-f_lo) - A_lo,
-// z = sat(+-(y - c)), v = w_hi z + w_lo z.
+// Weighted payoffs/lambda of eight suffixes under one prefix: per suffix
+// y = lambda f_hi + A_hi (exact), c = lambda (-f_lo) - A_lo, z = sat(+-(y - c))
+// (call: y - c, put: c - y), accumulated as w32 z by a chain of FMAs; a
+// call and a put share y and c.
 template <int MODE>
-__device__ __forceinline__ float wtree8(const float4 *f4, float B, float Ah, float nAl) {
-    float v[BT_UNROLL];
+__device__ __forceinline__ void wchain8(const float4 *f4, float B, float Ah, float nAl, float &tc, float &tp) {
+    float ac = 0.0f, ap = 0.0f;
 #pragma unroll
     for (int i = 0; i < BT_UNROLL; ++i) {
         const float y = __fmaf_rn(B, f4[i].x, Ah);
         const float c = __fmaf_rn(B, f4[i].y, nAl);
-        const float z = (MODE & BT_MODE_CALL) ? __saturatef(__fsub_rn(y, c)) : __saturatef(__fsub_rn(c, y));
-        v[i] = __fmaf_rn(f4[i].z, z, __fmul_rn(f4[i].w, z));
+        if (MODE & BT_MODE_CALL) ac = __fmaf_rn(f4[i].z, __saturatef(__fsub_rn(y, c)), ac);
+        if (MODE & BT_MODE_PUT) ap = __fmaf_rn(f4[i].z, __saturatef(__fsub_rn(c, y)), ap);
     }
-#pragma unroll
-    for (int w = 1; w < BT_UNROLL; w *= 2)
-#pragma unroll
-        for (int i = 0; i < BT_UNROLL; i += 2 * w) v[i] = __fadd_rn(v[i], v[i + w]);
-    return v[0];
+    tc = ac;
+    tp = ap;
 }
 
 // g + t as (sum, compensation): Fast2Sum (|g| >= |t| after the first add).
@@ -283,9 +353,10 @@ __device__ __forceinline__ void fast_acc_s(float &g, float &e, float t) {
     g = sN;
 }
 
-// One work item, FP32: eight-wide trees of weighted payoffs, eight trees
-// added in turn per Fast2Sum into the prefix's running sum; prefixes combined
-// in pairs (w beta / lambda and C recomputed after the loop), the block in FP64.
+// One work item, FP32: eight-suffix FMA chains of weighted payoffs, eight
+// chains added in turn per Fast2Sum into the prefix's running sum; prefixes
+// combined in pairs (w beta / lambda and C recomputed after the loop), the
+// block in FP64.
 template <int MODE>
 __device__ __forceinline__ void item_steps32(const bt_exact_args &a, const smem_job &sj, const float4 *s_suf,
                                              const bt_spentry *tab, double2 *red) {
@@ -308,45 +379,61 @@ __device__ __forceinline__ void item_steps32(const bt_exact_args &a, const smem_
             Ah[j] = nAl[j] = __int_as_float(0x7fc00000);  // sat(NaN) = 0
         }
     }
-    float g[BT_PT], e[BT_PT];
+    float gc[BT_PT], ec[BT_PT], gp[BT_PT], ep[BT_PT];
 #pragma unroll
-    for (int j = 0; j < BT_PT; ++j) g[j] = e[j] = 0.0f;
+    for (int j = 0; j < BT_PT; ++j) gc[j] = ec[j] = gp[j] = ep[j] = 0.0f;
     int s = 0;
     for (; s + 8 * BT_UNROLL <= J.suf_len; s += 8 * BT_UNROLL) {
-        float t[BT_PT];
+        float tc[BT_PT], tp[BT_PT];
 #pragma unroll
-        for (int j = 0; j < BT_PT; ++j) t[j] = 0.0f;
+        for (int j = 0; j < BT_PT; ++j) tc[j] = tp[j] = 0.0f;
 #pragma unroll 2
         for (int r = 0; r < 8; ++r) {
             float4 f4[BT_UNROLL];
 #pragma unroll
             for (int i = 0; i < BT_UNROLL; ++i) f4[i] = s_suf[s + r * BT_UNROLL + i];
 #pragma unroll
-            for (int j = 0; j < BT_PT; ++j) t[j] = __fadd_rn(t[j], wtree8<MODE>(f4, B[j], Ah[j], nAl[j]));
+            for (int j = 0; j < BT_PT; ++j) {
+                float uc, up;
+                wchain8<MODE>(f4, B[j], Ah[j], nAl[j], uc, up);
+                if (MODE & BT_MODE_CALL) tc[j] = __fadd_rn(tc[j], uc);
+                if (MODE & BT_MODE_PUT) tp[j] = __fadd_rn(tp[j], up);
+            }
         }
 #pragma unroll
-        for (int j = 0; j < BT_PT; ++j) fast_acc_s(g[j], e[j], t[j]);
+        for (int j = 0; j < BT_PT; ++j) {
+            if (MODE & BT_MODE_CALL) fast_acc_s(gc[j], ec[j], tc[j]);
+            if (MODE & BT_MODE_PUT) fast_acc_s(gp[j], ep[j], tp[j]);
+        }
     }
     for (; s < J.suf_len; s += BT_UNROLL) {
         float4 f4[BT_UNROLL];
 #pragma unroll
         for (int i = 0; i < BT_UNROLL; ++i) f4[i] = s_suf[s + i];
 #pragma unroll
-        for (int j = 0; j < BT_PT; ++j) fast_acc_s(g[j], e[j], wtree8<MODE>(f4, B[j], Ah[j], nAl[j]));
+        for (int j = 0; j < BT_PT; ++j) {
+            float uc, up;
+            wchain8<MODE>(f4, B[j], Ah[j], nAl[j], uc, up);
+            if (MODE & BT_MODE_CALL) fast_acc_s(gc[j], ec[j], uc);
+            if (MODE & BT_MODE_PUT) fast_acc_s(gp[j], ep[j], up);
+        }
     }
-    df32 tot = df_make(0.0f, 0.0f), cst = df_make(0.0f, 0.0f);
+    df32 totC = df_make(0.0f, 0.0f), totP = df_make(0.0f, 0.0f), cst = df_make(0.0f, 0.0f);
 #pragma unroll
     for (int j = 0; j < BT_PT; ++j) {
         const int64_t q = qbase + threadIdx.x + j * BT_THREADS;
         if (q >= nP) continue;
         const sstate st = steps_state(J, P, tab, q);
         const scale32 sc = scale_prefix(st.tau, P, q);
-        tot = df_add_pos(tot, df_mul(df_mul(df_mul(st.w, st.beta), sc.rinv), fast_two_sum(g[j], e[j])));
+        const df32 om = df_mul(df_mul(st.w, st.beta), sc.rinv);
+        if (MODE & BT_MODE_CALL) totC = df_add_pos(totC, df_mul(om, fast_two_sum(gc[j], ec[j])));
+        if (MODE & BT_MODE_PUT) totP = df_add_pos(totP, df_mul(om, fast_two_sum(gp[j], ep[j])));
         cst = df_add_pos(cst, df_mul(st.w, st.cst));
     }
-    double v = df_to_double(tot);
-    if (J.field == BT_F_LOOKMAX || J.field == BT_F_LOOKMIN) v += df_to_double(cst);
-    const double2 sum = (MODE & BT_MODE_CALL) ? block_sum2(v, 0.0, red) : block_sum2(0.0, v, red);
+    double vc = df_to_double(totC), vp = df_to_double(totP);
+    if (J.field == BT_F_LOOKMAX) vc += df_to_double(cst);
+    if (J.field == BT_F_LOOKMIN) vp += df_to_double(cst);
+    const double2 sum = block_sum2(vc, vp, red);
     if (threadIdx.x == 0) a.partials[J.part_off + item_local] = sum;
 }
 
@@ -397,24 +484,28 @@ __device__ __forceinline__ void item_steps64(const bt_exact_args &a, const smem_
         om[j] = w * beta;
         cst += w * c;
     }
-    double acc[BT_PT64];
+    double accC[BT_PT64], accP[BT_PT64];
 #pragma unroll
-    for (int j = 0; j < BT_PT64; ++j) acc[j] = 0.0;
+    for (int j = 0; j < BT_PT64; ++j) accC[j] = accP[j] = 0.0;
     for (int s = 0; s < J.suf_len; ++s) {
         const double2 fw = s_suf[s];
 #pragma unroll
         for (int j = 0; j < BT_PT64; ++j) {
             const double y = tau[j] + fw.x;
             // NaN (a masked prefix) contributes nothing
-            const double z = (MODE & BT_MODE_CALL) ? (y > 0.0 ? y : 0.0) : (y < 0.0 ? -y : 0.0);
-            acc[j] = fma(fw.y, z, acc[j]);
+            if (MODE & BT_MODE_CALL) accC[j] = fma(fw.y, y > 0.0 ? y : 0.0, accC[j]);
+            if (MODE & BT_MODE_PUT) accP[j] = fma(fw.y, y < 0.0 ? -y : 0.0, accP[j]);
         }
     }
-    double v = 0.0;
+    double vc = 0.0, vp = 0.0;
 #pragma unroll
-    for (int j = 0; j < BT_PT64; ++j) v = fma(om[j], acc[j], v);
-    if (J.field == BT_F_LOOKMAX || J.field == BT_F_LOOKMIN) v += cst;
-    const double2 sum = (MODE & BT_MODE_CALL) ? block_sum2(v, 0.0, red) : block_sum2(0.0, v, red);
+    for (int j = 0; j < BT_PT64; ++j) {
+        vc = fma(om[j], accC[j], vc);
+        vp = fma(om[j], accP[j], vp);
+    }
+    if (J.field == BT_F_LOOKMAX) vc += cst;
+    if (J.field == BT_F_LOOKMIN) vp += cst;
+    const double2 sum = block_sum2(vc, vp, red);
     if (threadIdx.x == 0) a.partials[J.part_off + item_local] = sum;
 }
 
@@ -424,8 +515,11 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_steps32(bt_exact_args a, cons
     __shared__ double2 red[BT_THREADS / 32];
     int cur_job = -1;
     while (next_item<float4>(a, sj, s_suf4, reinterpret_cast<const float4 *>(a.suf32), cur_job)) {
-        if (sj.J.mode == BT_MODE_CALL) item_steps32<BT_MODE_CALL>(a, sj, s_suf4, tab, red);
-        else item_steps32<BT_MODE_PUT>(a, sj, s_suf4, tab, red);
+        switch (sj.J.mode) {
+        case BT_MODE_CALL: item_steps32<BT_MODE_CALL>(a, sj, s_suf4, tab, red); break;
+        case BT_MODE_PUT: item_steps32<BT_MODE_PUT>(a, sj, s_suf4, tab, red); break;
+        default: item_steps32<BT_MODE_BOTH>(a, sj, s_suf4, tab, red); break;
+        }
     }
 }
 
@@ -435,8 +529,11 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_steps64(bt_exact_args a, cons
     __shared__ double2 red[BT_THREADS / 32];
     int cur_job = -1;
     while (next_item<double2>(a, sj, s_suf2, reinterpret_cast<const double2 *>(a.suf64), cur_job)) {
-        if (sj.J.mode == BT_MODE_CALL) item_steps64<BT_MODE_CALL>(a, sj, s_suf2, tab, red);
-        else item_steps64<BT_MODE_PUT>(a, sj, s_suf2, tab, red);
+        switch (sj.J.mode) {
+        case BT_MODE_CALL: item_steps64<BT_MODE_CALL>(a, sj, s_suf2, tab, red); break;
+        case BT_MODE_PUT: item_steps64<BT_MODE_PUT>(a, sj, s_suf2, tab, red); break;
+        default: item_steps64<BT_MODE_BOTH>(a, sj, s_suf2, tab, red); break;
+        }
     }
 }
 
@@ -461,6 +558,7 @@ extern "C" int bt_launch_steps_tables(const bt_job *d_jobs, const bt_jparams *d_
     if (bx < 1) bx = 1;
     dim3 grid(bx, n_jobs);
     k_steps_tables<<<grid, 256, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, d_steps, prec, suf32, suf64, tab);
+    if (prec == BT_PREC_FP32_COMP) k_steps_weights<<<n_jobs, 1024, 0, (cudaStream_t)stream>>>(d_jobs, suf32);
     return (int)cudaGetLastError();
 }
 

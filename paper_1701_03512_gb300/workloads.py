@@ -138,11 +138,12 @@ def step_factors(seed: int, N: int, lo: float = 0.02, hi: float = 0.15, p_lo: fl
     return np.stack([np.exp(lu), np.exp(-ld), p], axis=1)
 
 
-def branch_moves(seed: int, N: int, b: int = 3, lo: float = 0.02, hi: float = 0.12):
+def branch_moves(seed: int, N: int, b: int = 3, lo: float = 0.02, hi: float = 0.12, conc: float = 2.0):
     """Per-step moves of a b-ary tree: moves[N][2b] = (factors of digits
     0..b-1, ascending, then their probabilities). Factors: exp of sorted
     draws from U[-hi, hi] with the smallest below -lo and the largest above
-    lo; probabilities: a Dirichlet(2,...,2) draw."""
+    lo; probabilities: a Dirichlet(conc,...,conc) draw (conc = 2 spreads
+    them widely; a large conc keeps them near 1/b)."""
     rng = np.random.default_rng(seed)
     out = np.zeros((N, 2 * b))
     for t in range(N):
@@ -150,5 +151,5 @@ def branch_moves(seed: int, N: int, b: int = 3, lo: float = 0.02, hi: float = 0.
         z[0] = min(z[0], -lo)
         z[-1] = max(z[-1], lo)
         out[t, :b] = np.exp(z)
-        out[t, b:] = rng.dirichlet(np.full(b, 2.0))
+        out[t, b:] = rng.dirichlet(np.full(b, float(conc)))
     return out

@@ -2,6 +2,7 @@
 every symbol the public header declares; host-only entry points behave; no
 kernel is launched."""
 import ctypes
+import math
 import os
 import re
 
@@ -127,6 +128,23 @@ def test_exact_split_needs_no_device(bt):
     with pytest.raises(bt.BtError) as e:
         bt.bt_exact_split(W.opt(41, 100.0, 100.0, 0.05, 0.2, 1.0, W.EURO_CALL))
     assert e.value.status == bt.BT_EINVAL
+
+
+def test_skewed_trees_route_to_the_class_pass(bt):
+    """Host routing of FP32_COMP: an arithmetic Asian from 2^28 paths keeps
+    the per-path pass (L = 13) only while the tree has at least 2^27
+    effective paths, (p^2 + (1-p)^2)^-N; below that the pair-sum class pass
+    (L <= 12). FP64 and the other payoffs are unaffected."""
+    u = 1.05
+    for N in (28, 36):
+        pc = 0.5 * (1.0 + math.sqrt(2.0 * 2.0 ** (-27.0 / N) - 1.0))
+        for p, L in ((0.5, 13), (pc - 1e-3, 13), (pc + 1e-3, 12), (1 - pc - 1e-3, 12), (1 - pc + 1e-3, 13),
+                     (0.996, 12)):
+            o = W.opt(N, 100.0, 100.0, 0.0, 0.2, 1.0, W.ASIAN_ARITH_CALL, W.TREE_EXPLICIT, u=u, d=1 / u, p=p)
+            assert bt.bt_exact_split(o, bt.BT_PREC_FP32_COMP)["L"] == L, (N, p)
+            assert bt.bt_exact_split(o, bt.BT_PREC_FP64)["L"] == 13
+            g = dict(o, payoff=W.ASIAN_GEO_CALL)
+            assert bt.bt_exact_split(g, bt.BT_PREC_FP32_COMP)["L"] == 13
 
 
 def test_plain_c_client(bt, tmp_path):

@@ -1,9 +1,12 @@
 """Trees with b branches per node (the end of Section 3) on the GPU: the
 generic pass with the built-in payoffs against the oracle's b-ary
 enumeration, a recombining trinomial lattice against backward induction,
-b = 2 against the built-in binomial pass, and a plug-in on a trinomial tree
-against numpy brute force."""
+b = 2 against the built-in binomial pass, a plug-in on a trinomial tree
+against the oracle's enumeration of a payoff given as a path function, and
+the affine pass against the oracle at every size it runs (the FP32 pass from
+2^28 paths: 3^18 and 4^14)."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -59,7 +62,7 @@ def test_two_branches_match_the_binomial_pass(bt, ctx):
     assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref) + 1e-13)
 
 
-def test_plugin_on_a_trinomial_tree(bt, ctx):
+def test_plugin_on_a_trinomial_tree(bt, ctx, oracle):
     src = r"""
     struct Payoff {   // up-and-out call, barrier param[1]
         struct state { double S; int out; };
@@ -77,12 +80,8 @@ def test_plugin_on_a_trinomial_tree(bt, ctx):
         moves = W.branch_moves(3, N, b)
         o = W.opt(N, 100.0, 97.0, 0.02, 0.2, 1.0, W.EURO_CALL)
         got = bt.bt_price_exact_branching(ctx.h, [o], b, [moves], plugin=h, params=[[97.0, 115.0]])["value"][0]
-        idx = np.arange(b ** N)
-        x = (idx[:, None] // (b ** (N - 1 - np.arange(N)))[None, :]) % b
-        S = 100.0 * np.cumprod(moves[:, :b][np.arange(N)[None, :], x], axis=1)
-        w = np.prod(moves[:, b:][np.arange(N)[None, :], x], axis=1)
-        v = np.where(S.max(axis=1) >= 115.0, 0.0, np.maximum(S[:, -1] - 97.0, 0.0))
-        ref = math.exp(-0.02) * math.fsum(w * v)
+        ref = oracle.functional_price(
+            o, moves, b, lambda S, x: np.where(S.max(axis=1) >= 115.0, 0.0, np.maximum(S[:, -1] - 97.0, 0.0)))
         assert abs(got - ref) <= 1e-12 * ref
     finally:
         bt.bt_plugin_destroy(h)
@@ -124,11 +123,12 @@ def test_affine_moves_pass_against_the_oracle(bt, ctx, oracle, prec, b, N):
 
 
 def test_affine_moves_probability_floor(bt, ctx, oracle):
-    """From 2^28 paths FP32_COMP runs the FP32 pass, which refuses a branch
-    probability in (0, 0.004) (its weights would leave the FP32 pair range);
-    FP64 takes it. A smaller tree runs the FP64 pass under FP32_COMP too, so
-    there the rare probability is taken. A zero probability (a branch that
-    never happens) is taken by the FP32 pass as well."""
+    """From 2^28 paths (and 2^27 effective paths) FP32_COMP runs the FP32
+    pass, which refuses a branch probability in (0, 0.004) (its weights would
+    leave the FP32 pair range); FP64 takes it. A smaller tree runs the FP64
+    pass under FP32_COMP too, so there the rare probability is taken. A zero
+    probability (a branch that never happens) is taken by the FP32 pass as
+    well."""
     o = W.opt(6, 100.0, 100.0, 0.02, 0.2, 1.0, W.ASIAN_ARITH_CALL)
     rare = W.branch_moves(5, 6, 3)
     rare[3, 3:] = [0.001, 0.5, 0.499]
@@ -136,7 +136,7 @@ def test_affine_moves_probability_floor(bt, ctx, oracle):
     assert abs(r["value"] - oracle.branch_price(o, rare, 3, 8)) <= 1e-12 * abs(r["value"])
     assert r["err_est"] == pytest.approx(1e-12 * abs(r["value"]))      # priced by the FP64 pass
     ob = W.opt(18, 100.0, 100.0, 0.02, 0.2, 1.0, W.ASIAN_ARITH_CALL)   # 3^18 = 3.9e8 paths
-    mvb = W.branch_moves(6, 18, 3)
+    mvb = W.branch_moves(6, 18, 3, conc=50.0)                          # near 1/3: 2^28 effective paths
     rareb = mvb.copy()
     rareb[9, 3:] = [0.001, 0.5, 0.499]
     with pytest.raises(bt.BtError) as e:
@@ -150,22 +150,38 @@ def test_affine_moves_probability_floor(bt, ctx, oracle):
     assert abs(v32 - v64) <= 1e-9 * abs(v64) + 1e-12 * ob["S0"], (v32, v64)
 
 
-@pytest.mark.parametrize("b,N", [(3, 20), (4, 14), (8, 10)])   # 3.5e9, 2.7e8, 1.1e9 paths
+@pytest.mark.parametrize("b,N", [(3, 18), (4, 14)])   # 3.9e8 and 2.7e8 paths
+def test_affine_moves_fp32_pass_against_the_oracle_at_full_size(bt, ctx, oracle, b, N):
+    """From 2^28 paths FP32_COMP runs the FP32 pass: every payoff at two
+    strikes on one non-recombining b-ary tree (call and put of one field
+    adjacent, sharing a pass) against the oracle's enumeration of all b^N
+    paths, at the 1e-9 contract and within the stated error."""
+    opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for K in (95.0, 105.0) for pay in range(8)]
+    mv = W.branch_moves(700 + 10 * b, N, b, 0.01, 0.05, 50.0)
+    assert not np.any((mv[:, b:] > 0) & (mv[:, b:] < 0.004))   # above the FP32 pass's probability floor
+    assert -np.sum(np.log2(np.sum(mv[:, b:] ** 2, axis=1))) >= 27   # enough effective paths for it
+    got = bt.bt_price_exact_moves(ctx.h, opts, b, [mv] * len(opts), 1)
+    ref = oracle.branch_price_multi(opts[0], mv, b, [(o["payoff"], o["K"]) for o in opts], os.cpu_count() or 8)
+    s0 = np.array([o["S0"] for o in opts])
+    err = np.abs(got["value"] - ref)
+    assert np.all(err <= 1e-9 * np.abs(ref) + 1e-12 * s0), (b, N, err / np.abs(ref))
+    assert np.all(err <= got["err_est"] + 1e-12 * s0)
+    assert np.all(got["err_est"] <= 1e-9 * np.abs(got["value"]) * (1 + 1e-12))
+    assert np.all(got["paths"] == b ** N)
+
+
+@pytest.mark.parametrize("b,N", [(3, 20), (8, 10)])   # 3.5e9, 1.1e9 paths
 def test_affine_moves_large_trees_fp32_against_fp64(bt, ctx, b, N):
-    """From 2^28 paths FP32_COMP runs the FP32 pass: every payoff against
-    the FP64 pass (which the oracle pins on smaller trees) at the 1e-9
-    contract."""
-    opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for pay in range(8) for K in (95.0, 105.0)]
-    moves = [W.branch_moves(700 + 10 * b + i, N, b, 0.01, 0.05) for i in range(len(opts))]
-    ok = [not np.any((m[:, b:] > 0) & (m[:, b:] < 0.004)) for m in moves]   # the FP32 pass's floor
-    opts = [o for o, k in zip(opts, ok) if k]
-    moves = [m for m, k in zip(moves, ok) if k]
-    assert len(opts) >= 10
-    v32 = bt.bt_price_exact_moves(ctx.h, opts, b, moves, 1)
-    v64 = bt.bt_price_exact_moves(ctx.h, opts, b, moves, 0)["value"]
+    """A consistency check beyond the oracle's reach in a test: the FP32 pass
+    against the FP64 pass of the same library at the 1e-9 contract (the
+    oracle pins both at 3^18 and 4^14 paths above)."""
+    opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for K in (95.0, 105.0) for pay in range(8)]
+    mv = W.branch_moves(700 + 10 * b, N, b, 0.01, 0.05, 50.0)
+    assert not np.any((mv[:, b:] > 0) & (mv[:, b:] < 0.004))
+    v32 = bt.bt_price_exact_moves(ctx.h, opts, b, [mv] * len(opts), 1)
+    v64 = bt.bt_price_exact_moves(ctx.h, opts, b, [mv] * len(opts), 0)["value"]
     s0 = np.array([o["S0"] for o in opts])
     assert np.all(np.abs(v32["value"] - v64) <= 1e-9 * np.abs(v64) + 1e-12 * s0)
-    assert np.all(np.abs(v32["value"] - v64) <= v32["err_est"] + 1e-12 * s0)
 
 
 def test_affine_moves_recombining_trinomial_fp64(bt, ctx, oracle):

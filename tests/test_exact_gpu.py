@@ -314,27 +314,52 @@ def test_stated_error_covers_the_difference_to_the_oracle(bt, ctx, oracle, N):
 
 
 def test_probability_limit_of_the_fp32_path(bt, ctx, oracle):
-    """min(p, 1-p) >= 0.004 is accepted in FP32 and matches the oracle within
-    the stated error; below it FP32 is refused and FP64 still prices. At
-    p = 0.996 the all-up path carries 0.996^28 = 89 % of the value, so its one
-    FP32 rounding (up to 2^-24) does not average out: the stated error of the
-    per-path pass adds 6e-8 max(p, 1-p)^N to the 1e-9 band, 5.5e-8 relative
-    here."""
+    """min(p, 1-p) >= 0.004 is accepted in FP32 and meets the 1e-9 contract;
+    below it FP32 is refused and FP64 still prices. Skewed trees (p = 0.9,
+    0.996: the all-up path alone carries 89 % of the probability at 0.996)
+    have far fewer than 2^27 effective paths, 1 / sum_x p(x)^2, so per-path
+    FP32 roundings could not average out: they take the pair-sum class pass
+    (L <= 12), which rounds no single path, and every stated error is
+    1e-9 |V|."""
     u = 1.05
     d = 1 / u
-    for p, ok in ((0.004, True), (0.996, True), (0.0039, False)):
+    for p, ok in ((0.004, True), (0.996, True), (0.9, True), (0.0039, False)):
         o = W.opt(28, 100.0, 100.0, 0.0, 0.2, 1.0, W.ASIAN_ARITH_CALL, W.TREE_EXPLICIT, u=u, d=d, p=p)
         if ok:
             r = ctx.price_exact([o], 1)[0]
             ref = oracle.exact(o)
-            stated = tol(1, 28) + 6e-8 * max(p, 1 - p) ** 28
-            assert r["err_est"] == pytest.approx(stated * abs(r["value"]), rel=1e-12)
-            assert abs(r["value"] - ref) <= r["err_est"] + 1e-12 * 100.0
+            assert r["err_est"] == pytest.approx(1e-9 * abs(r["value"]), rel=1e-12)
+            assert abs(r["value"] - ref) <= 1e-9 * abs(ref) + 1e-12 * 100.0, (p, r["value"], ref)
+            assert bt.bt_exact_split(o, 1)["L"] == 12          # the class pass's split
         else:
             with pytest.raises(bt.BtError) as e:
                 ctx.price_exact([o], 1)
             assert e.value.status == bt.BT_EUNSUPPORTED
             assert ctx.price_exact([o], 0)["value"][0] > 0.0
+
+
+def _p_at_neff(N, bits):
+    """p with (p^2 + (1-p)^2)^-N = 2^bits, p >= 1/2."""
+    c = 2.0 ** (-bits / N)
+    return 0.5 * (1.0 + math.sqrt(2.0 * c - 1.0))
+
+
+@pytest.mark.parametrize("N", [28, 32])
+def test_effective_path_threshold(bt, ctx, oracle, N):
+    """Either side of the routing bound of 2^27 effective paths: p just
+    inside it keeps the per-path pass (L = 13), just outside takes the class
+    pass (L = 12); both at the 1e-9 contract against the oracle, for calls
+    and puts in and out of the money, with drift up and down."""
+    pc = _p_at_neff(N, 27.0)
+    u = 1.03
+    for p, L in ((pc - 0.005, 13), (pc + 0.005, 12), (1 - pc - 0.005, 12), (1 - pc + 0.005, 13)):
+        opts = [W.opt(N, 100.0, K, 0.0, 0.2, 1.0, pay, W.TREE_EXPLICIT, u=u, d=1 / u, p=p)
+                for K in (80.0, 100.0, 125.0) for pay in (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT)]
+        assert bt.bt_exact_split(opts[0], 1)["L"] == L, (p, L)
+        got = ctx.price_exact(opts, 1)
+        ref = [oracle.exact(o) for o in opts]
+        _check(got["value"], ref, opts, 1, "N=%d p=%.4f" % (N, p))
+        assert np.allclose(got["err_est"], 1e-9 * np.abs(got["value"]), rtol=1e-12)
 
 
 def test_paper_section5_parameters_to_the_contract(bt, ctx, oracle):

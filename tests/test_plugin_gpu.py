@@ -1,8 +1,10 @@
-"""Payoff plug-ins compiled at run time (bt_plugin_compile): re-stated
-built-in payoffs against the built-in FP64 passes, and payoffs the library
-does not have (an up-and-out barrier call, a pattern count of the bits)
-against an independent numpy brute force."""
-import math
+"""Payoff plug-ins compiled at run time (bt_plugin_compile), against the
+oracle: re-stated built-in payoffs against its exact values on lattice trees
+and its path walk on time-varying trees, and payoffs the library does not
+have (an up-and-out barrier call, a pattern count of the bits) against its
+enumeration of the same payoff written as a function of the whole path
+(eq. expval)."""
+import os
 
 import numpy as np
 import pytest
@@ -84,57 +86,56 @@ def plugins(bt, ctx):
         bt.bt_plugin_destroy(h)
 
 
-def _brute(o, steps, V):
-    N = o["N"]
-    b = np.arange(1 << N, dtype=np.int64)
-    x = ((b[:, None] >> (N - 1 - np.arange(N))[None, :]) & 1).astype(bool)
-    S = o["S0"] * np.cumprod(np.where(x, steps[:, 0], steps[:, 1]), axis=1)
-    w = np.prod(np.where(x, steps[:, 2], 1.0 - steps[:, 2]), axis=1)
-    return math.exp(-o["rate"] * o["T"]) * math.fsum(w * V(S, x))
-
-
-def test_restated_builtins_match_the_builtin_passes(bt, ctx, plugins):
+def test_restated_builtins_against_the_oracle(bt, ctx, plugins, oracle):
+    """Plug-ins restating two built-in payoffs on lattice trees, against the
+    oracle's exact values (meet in the middle / the lookback DP above N = 16,
+    its enumeration below)."""
     for N in (9, 20, 26):
         opts = [W.opt(N, 100.0, 97.0, 0.05, 0.25, 1.0, W.ASIAN_ARITH_CALL),
                 W.opt(N, 100.0, 104.0, 0.05, 0.25, 1.0, W.LOOKBACK_FIXED_PUT, W.TREE_SEYDEL)]
-        ref = ctx.price_exact(opts, 0)["value"]
+        ref = [oracle.exact(o) for o in opts]
         a = bt.bt_price_exact_plugin(ctx.h, plugins["arith"], opts[:1])[0]
         b = bt.bt_price_exact_plugin(ctx.h, plugins["lookput"], opts[1:])[0]
-        assert abs(a["value"] - ref[0]) <= 1e-12 * ref[0] and a["paths"] == 2 ** N
-        assert abs(b["value"] - ref[1]) <= 1e-12 * ref[1]
+        assert abs(a["value"] - ref[0]) <= 1e-12 * ref[0] and a["paths"] == 2 ** N, (N, a["value"], ref[0])
+        assert abs(b["value"] - ref[1]) <= 1e-12 * ref[1], (N, b["value"], ref[1])
 
 
-def test_time_varying_steps_match_the_steps_pass(bt, ctx, plugins):
-    o = W.opt(24, 100.0, 99.0, 0.03, 0.2, 1.0, W.ASIAN_ARITH_CALL)
-    steps = W.step_factors(77, 24)
-    ref = bt.bt_price_exact_steps(ctx.h, [o], [steps], 0)["value"][0]
-    got = bt.bt_price_exact_plugin(ctx.h, plugins["arith"], [o], steps=[steps])["value"][0]
-    assert abs(got - ref) <= 1e-12 * ref
+def test_restated_builtin_on_a_time_varying_tree_against_the_oracle(bt, ctx, plugins, oracle):
+    for N in (16, 24):
+        o = W.opt(N, 100.0, 99.0, 0.03, 0.2, 1.0, W.ASIAN_ARITH_CALL)
+        steps = W.step_factors(77 + N, N)
+        ref = oracle.steps_price(o, steps, os.cpu_count() or 8)
+        got = bt.bt_price_exact_plugin(ctx.h, plugins["arith"], [o], steps=[steps])["value"][0]
+        assert abs(got - ref) <= 1e-12 * ref, (N, got, ref)
 
 
-def test_barrier_call_against_brute_force(bt, ctx, plugins):
-    for N, B in ((12, 120.0), (16, 112.0)):
+def test_barrier_call_against_the_oracle(bt, ctx, plugins, oracle):
+    """A payoff outside the built-ins, against the oracle's enumeration of
+    the same payoff written as a function of the whole path."""
+    for N, B in ((12, 120.0), (16, 112.0), (20, 115.0)):
         o = W.opt(N, 100.0, 98.0, 0.04, 0.3, 1.0, W.EURO_CALL)
         steps = W.step_factors(5 + N, N)
-        ref = _brute(o, steps, lambda S, x: np.where(S.max(axis=1) >= B, 0.0, np.maximum(S[:, -1] - 98.0, 0.0)))
+        ref = oracle.functional_price(
+            o, oracle.steps_as_moves(steps), 2,
+            lambda S, x: np.where(S.max(axis=1) >= B, 0.0, np.maximum(S[:, -1] - 98.0, 0.0)))
         got = bt.bt_price_exact_plugin(ctx.h, plugins["barrier"], [o], steps=[steps], params=[[98.0, B]])
-        assert abs(got["value"][0] - ref) <= 1e-12 * abs(ref) + 1e-14
+        assert abs(got["value"][0] - ref) <= 1e-12 * abs(ref) + 1e-14, (N, got["value"][0], ref)
 
 
-def test_bit_pattern_functional_against_brute_force(bt, ctx, plugins):
+def test_bit_pattern_functional_against_the_oracle(bt, ctx, plugins, oracle):
     def runs(S, x):
-        xi = x.astype(np.int64)
         c = np.zeros(len(x))
         run = np.zeros(len(x), dtype=np.int64)
         for t in range(x.shape[1]):
-            run = np.where(xi[:, t] == 1, run + 1, 0)
+            run = np.where(x[:, t] == 1, run + 1, 0)
             c += run == 3
         return c
-    o = W.opt(15, 100.0, 100.0, 0.0, 0.2, 1.0, W.EURO_CALL)
-    steps = W.step_factors(8, 15)
-    ref = _brute(o, steps, runs)
-    got = bt.bt_price_exact_plugin(ctx.h, plugins["runs"], [o], steps=[steps])["value"][0]
-    assert abs(got - ref) <= 1e-13 * ref
+    for N in (15, 20):
+        o = W.opt(N, 100.0, 100.0, 0.0, 0.2, 1.0, W.EURO_CALL)
+        steps = W.step_factors(8 + N, N)
+        ref = oracle.functional_price(o, oracle.steps_as_moves(steps), 2, runs)
+        got = bt.bt_price_exact_plugin(ctx.h, plugins["runs"], [o], steps=[steps])["value"][0]
+        assert abs(got - ref) <= 1e-13 * ref, (N, got, ref)
 
 
 def test_compile_error_reports_the_log(bt, ctx):
