@@ -25,6 +25,17 @@ void *g_scratch_ptr[BT_NOALLOC_MAX_DEVICES];            // device address of the
 int g_grid32[BT_NOALLOC_MAX_DEVICES], g_grid64[BT_NOALLOC_MAX_DEVICES];
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Waits for the call's stream when the call returns early after enqueuing
+// work, so that the lock (released after this guard) is never given to a
+// later call while this call's kernels may still use the shared array.
+struct drain_on_exit {
+    cudaStream_t st;
+    bool armed = false;
+    ~drain_on_exit() {
+        if (armed) cudaStreamSynchronize(st);
+    }
+};
 }  // namespace
 
 extern "C" bt_status bt_price_exact_noalloc(const bt_option *opts, int32_t n, bt_precision prec, bt_result *out,
@@ -104,9 +115,12 @@ extern "C" bt_status bt_price_exact_noalloc(const bt_option *opts, int32_t n, bt
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return bt_cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-        g_grid32[dev] = bt_exact_grid_size(BT_PREC_FP32_COMP, dev);
-        g_grid64[dev] = bt_exact_grid_size(BT_PREC_FP64, dev);
-        if ((e = cudaGetLastError()) != cudaSuccess) return bt_cuda_fail(e, "kernel attributes");
+        const int g32 = bt_exact_grid_size(BT_PREC_FP32_COMP, dev);
+        if (g32 < 0) return bt_cuda_fail(-g32, "kernel attributes (FP32 pass)");
+        const int g64 = bt_exact_grid_size(BT_PREC_FP64, dev);
+        if (g64 < 0) return bt_cuda_fail(-g64, "kernel attributes (FP64 pass)");
+        g_grid32[dev] = g32;
+        g_grid64[dev] = g64;
         g_scratch_ptr[dev] = p;
     }
     char *base = (char *)g_scratch_ptr[dev];
@@ -123,6 +137,8 @@ extern "C" bt_status bt_price_exact_noalloc(const bt_option *opts, int32_t n, bt
     unsigned long long *d_cnt = (unsigned long long *)(base + o_cnt);
 
     cudaStream_t st = (cudaStream_t)stream;
+    drain_on_exit drain{st};
+    drain.armed = true;   // from the first copy on, every return waits for the stream
     e = cudaMemcpyAsync(d_opts, opts, sizeof(bt_option) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_jobs, jobs, sizeof(bt_job) * nj, cudaMemcpyHostToDevice, st);
     // The array keeps the previous call's contents: clear what must start at zero.
@@ -158,5 +174,6 @@ extern "C" bt_status bt_price_exact_noalloc(const bt_option *opts, int32_t n, bt
     // overwrite the array while it is in use.
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bt_cuda_fail(e, "bt_price_exact_noalloc");
+    drain.armed = false;   // drained above
     return BT_OK;
 }

@@ -39,6 +39,10 @@ static_assert(256 % sizeof(bt_pentry) == 0 && 256 % sizeof(bt_pow) == 0 && 256 %
 namespace {
 
 using clk = std::chrono::steady_clock;
+
+// Longest wait for the set-up stream (the tables of one admission) before the
+// server fails with BT_ETIMEOUT.
+#define BT_SETUP_WAIT_MS 10000
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 double ms_between(clk::time_point a, clk::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
@@ -401,8 +405,19 @@ static void admit(bt_server *S) {
     // grouped by precision (FP64 = 0 first): one table launch per group
     std::stable_sort(rq.begin(), rq.end(), [](const request *x, const request *y) { return x->prec < y->prec; });
     for (size_t i = 0; i < rq.size(); ++i) admitted[i] = rq[i]->ticket;
-    // the pinned staging of the previous admission must have been copied
-    cudaError_t e = cudaEventSynchronize(S->setup_done);
+    // the pinned staging of the previous admission must have been copied:
+    // poll its event with a limit (every wait of the server is bounded)
+    cudaError_t e = cudaEventQuery(S->setup_done);
+    const auto give_up = clk::now() + std::chrono::milliseconds(BT_SETUP_WAIT_MS);
+    while (e == cudaErrorNotReady && clk::now() < give_up) {
+        std::this_thread::yield();
+        e = cudaEventQuery(S->setup_done);
+    }
+    if (e == cudaErrorNotReady) {
+        std::lock_guard<std::mutex> lock(S->mu);
+        server_fail(S, BT_ETIMEOUT, "admission: the set-up stream did not finish its tables in time");
+        return;
+    }
     // tables of the new requests on the set-up stream; launches wait on its event
     int max_len = 0;
     for (size_t i = 0; i < admitted.size(); ++i) {

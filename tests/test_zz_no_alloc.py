@@ -3,10 +3,12 @@
 bt_price_exact_noalloc serves callers that cannot allocate device memory
 while they run (an application whose allocator owns the device, or a loop
 that cannot afford cudaMalloc/cudaFree). It keeps every intermediate buffer
-in one fixed library-owned device array, so these checks call it twice in a
-row with different batches -- the second call must not see the first call's
-leftovers -- and compare each result with bt_price_exact through the C ABI,
-within the tolerances the other exhaustive-sum tests use.
+in one fixed library-owned device array, so these checks call it three
+times in a row with different batches -- a later call must not see an
+earlier call's leftovers -- and compare each result with bt_price_exact
+through the C ABI bit for bit (same plan, split and kernels), and the last
+batch with the oracle within the tolerances the other exhaustive-sum tests
+use.
 """
 import ctypes
 
@@ -40,22 +42,27 @@ def _noalloc(bt, opts, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 0])
-def test_noalloc_matches_regular_entry_point_twice(bt, prec):
+def test_noalloc_matches_regular_entry_point_twice(bt, oracle, prec):
+    """Both entry points run the same plan, split and kernels, so their
+    results must be the same bits; the second call must not see the first
+    call's leftovers in the shared array. The small batch is also checked
+    against the oracle at the contract tolerance."""
     batch_a = W.batch(26, W.option_sets(41, 4), list(range(8)))          # 32 options, pairs and singles
     batch_b = W.random_options(42, 20, 16, 28)                              # different shapes
+    batch_c = W.random_options(45, 12, 8, 18)                               # small enough for the oracle
     ctx = bt.Context(0)
     try:
-        ref_a = ctx.price_exact(batch_a, prec)
-        ref_b = ctx.price_exact(batch_b, prec)
+        refs = [ctx.price_exact(b, prec) for b in (batch_a, batch_b, batch_c)]
     finally:
         ctx.close()
-    for batch, ref in ((batch_a, ref_a), (batch_b, ref_b)):   # two calls in a row
+    for batch, ref in zip((batch_a, batch_b, batch_c), refs):   # three calls in a row
         got = _noalloc(bt, batch, prec)
-        tol = np.array([_tol(prec, o["N"]) for o in batch])
-        s0 = np.array([o["S0"] for o in batch])
-        err = np.abs(got["value"] - ref["value"])
-        assert np.all(err <= tol * np.abs(ref["value"]) + 1e-12 * s0), (prec, err)
+        assert np.array_equal(got["value"], ref["value"]), (prec, got["value"] - ref["value"])
+        assert np.array_equal(got["err_est"], ref["err_est"])
         assert np.array_equal(got["paths"], ref["paths"])
+    exact = np.array([oracle.exact(o) for o in batch_c])
+    s0 = np.array([o["S0"] for o in batch_c])
+    assert np.all(np.abs(got["value"] - exact) <= _tol(prec, 18) * np.abs(exact) + 1e-12 * s0)
 
 
 def test_noalloc_rejects_oversized_batches(bt):
