@@ -37,9 +37,13 @@ Two further measurements ride on the same line (rank 0, N=1 only):
   widened -- time-varying trees (FP32, N=32) and the generic FP64 path walk
             on binomial (N=28) and trinomial (N=17) trees.
 
-Multi-GPU (torchrun): every rank prices its own copy of the batch (weak
-scaling, independent problems, no collective on the data path); the value is
-all ranks' paths over the slowest rank's time.
+Multi-GPU (torchrun): the paper's split of one problem (Section 3, eq. f14
+and f15) -- every rank holds the same batch, runs the work items i with
+i % world == rank (bt_exact_plan_run_shard), and one all-gather of the
+per-option partial values (a few doubles per option) is combined in rank
+order on every rank; the value is the batch's paths over the slowest rank's
+step time (strong scaling). --weak instead prices an independent batch per
+rank (seed = rank) with no exchange.
 
 --impl reference times the CPU oracle on the host cores instead.
 """
@@ -83,6 +87,8 @@ def parse():
     ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--no-greeks", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--weak", action="store_true",
+                    help="N > 1: an independent batch per rank instead of one batch split across the ranks")
     return ap.parse_args()
 
 
@@ -263,24 +269,16 @@ def kernel_source_hash():
 
 def profiled_traffic(N):
     """DRAM bytes per launch of the path-sum kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "k_exact32_batched_asian.md")
+    figures (profiles/k_exact32_batched_asian.json), if they were taken on
+    the current kernel source; None otherwise."""
     try:
-        txt = open(path).read()
-    except OSError:
+        vals = json.load(open(os.path.join(ROOT, "profiles", "k_exact32_batched_asian.json")))
+    except (OSError, ValueError):
         return None
-    vals = {}
-    for ln in txt.splitlines():
-        if ":" in ln and ln.strip().startswith("- "):
-            k, v = ln.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
-    key = "dram_bytes_per_launch_N%d" % N
-    try:
-        return float(vals[key])
-    except (KeyError, ValueError):
-        return None
+    v = vals.get("dram_bytes_per_launch_N%d" % N)
+    return float(v) if isinstance(v, (int, float)) else None
 
 
 # ---------------------------------------------------------------------------
@@ -476,22 +474,49 @@ def _oracle_rate(fn, units, sample):
     return {"value": units / dt, "cores": 1, "kind": "oracle", "sample": sample}
 
 
+CLS_OPS_SINGLE = 22   # per (prefix, class): TwoSum tau + f (6), low parts (3), sign select (2),
+                      # multiplicity x pair by TwoProd (3), TwoSum into the group sum (8)
+CLS_OPS_PAIR = 35     # a call and a put: the 9 ops of tau + f shared, 13 each for select and accumulate
+
+
+def class_evaluations(bt, o):
+    """(prefix, class) evaluations of one option's class pass: 2^P prefixes
+    times the distinct suffix classes of its split -- suffixes of one
+    up-count with the same key (level sum, end level, max or min level); the
+    arithmetic Asian's classes are its suffixes."""
+    import numpy as np
+    sp = bt.bt_exact_split(o, bt.BT_PREC_FP32_COMP)
+    L, P = sp["L"], sp["P"]
+    if o["payoff"] in (2, 3):
+        return float(2 ** P) * float(2 ** L)
+    s = np.arange(1 << L)
+    bits = (s[:, None] >> (L - 1 - np.arange(L))[None, :]) & 1
+    lvl = np.cumsum(2 * bits - 1, axis=1)
+    key = {4: lvl.sum(axis=1), 5: lvl.sum(axis=1), 0: lvl[:, -1], 1: lvl[:, -1],
+           6: lvl.max(axis=1), 7: lvl.min(axis=1)}[o["payoff"]]
+    classes = len(set(zip(bits.sum(axis=1).tolist(), key.tolist())))
+    return float(2 ** P) * classes
+
+
 def extras_bench(bt, W, ctx, sms, fmax, with_cpu=True):
     import numpy as np
     peak = sms * 128 * fmax * 1e6
     out = {}
     if with_cpu:
         from oracle import py_oracle as O
-    # time-varying trees, FP32: 16 options at N=32 (arithmetic call/put, lookback call, geometric call)
+    # time-varying trees, FP32: 8 trees at N=32, an arithmetic Asian call and put on each (a pair
+    # shares one pass)
     N = 32
-    opts = [W.opt(N, 100.0, 90.0 + 5 * (i % 4), 0.03, 0.2, 1.0, pay)
-            for i, pay in enumerate([W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT, W.LOOKBACK_FIXED_CALL,
-                                     W.ASIAN_GEO_CALL] * 4)]
-    steps = [W.step_factors(900 + i, N, 0.01, 0.05) for i in range(len(opts))]
+    opts, steps = [], []
+    for i in range(8):
+        st = W.step_factors(900 + i, N, 0.01, 0.05)
+        for pay in (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT):
+            opts.append(W.opt(N, 100.0, 90.0 + 5 * (i % 4), 0.03, 0.2, 1.0, pay))
+            steps.append(st)
     t = _timed(lambda: bt.bt_price_exact_steps(ctx.h, opts, steps, bt.BT_PREC_FP32_COMP))
     paths = len(opts) * 2.0 ** N
-    out["steps"] = {"workload": "time-varying trees (per-step u_t, d_t, p_t), 16 options x 2^32 paths, FP32_COMP, "
-                                "host arrays in and out",
+    out["steps"] = {"workload": "time-varying trees (per-step u_t, d_t, p_t), 8 trees x arithmetic Asian call+put, "
+                                "16 x 2^32 payoff-paths, FP32_COMP, host arrays in and out",
                     "ms": 1e3 * t, "payoff_paths_per_s": paths / t, "ops_per_payoff_path": 3,
                     "frac_of_issue_peak": 3 * paths / t / peak}
     if with_cpu:
@@ -514,13 +539,14 @@ def extras_bench(bt, W, ctx, sms, fmax, with_cpu=True):
             "the arithmetic Asian call at N=20 (2^20 paths) through the b-ary enumeration, one thread")
     # trinomial trees through the affine pass (prefix/suffix tables, FP32), N=22: 8 x 3^22 paths
     N4 = 22
-    o4 = [W.opt(N4, 100.0, 90.0 + 5 * (i % 4), 0.03, 0.2, 1.0, pay)
-          for i, pay in enumerate([W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT] * 4)]
-    mv4 = [W.branch_moves(800 + i, N4, 3, 0.01, 0.05) for i in range(len(o4))]
+    o4 = [W.opt(N4, 100.0, 90.0 + 5 * i, 0.03, 0.2, 1.0, pay)
+          for i in range(4) for pay in (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT)]
+    mv4 = [W.branch_moves(800 + i // 2, N4, 3, 0.01, 0.05, 50.0) for i in range(len(o4))]
     t = _timed(lambda: bt.bt_price_exact_moves(ctx.h, o4, 3, mv4, bt.BT_PREC_FP32_COMP))
     paths4 = len(o4) * 3.0 ** N4
-    out["trinomial_affine"] = {"workload": "trinomial trees (per-step moves), arithmetic Asian call/put, N=22, "
-                                           "8 x 3^22 paths, FP32_COMP, host arrays in and out",
+    out["trinomial_affine"] = {"workload": "4 trinomial trees (per-step moves, probabilities Dirichlet(50)) x "
+                                           "arithmetic Asian call+put, N=22, 8 x 3^22 payoff-paths, FP32_COMP, "
+                                           "host arrays in and out",
                                "ms": 1e3 * t, "payoff_paths_per_s": paths4 / t,
                                "frac_of_issue_peak": 3 * paths4 / t / peak}
     if with_cpu:
@@ -555,18 +581,28 @@ def extras_bench(bt, W, ctx, sms, fmax, with_cpu=True):
             lambda: O.price_exhaustive(o1, 1), 2.0 ** 20, "the same option, all 2^20 paths, one thread")
     # the class pass: recombined classes (geometric, lookback, European) at N=36, and the small
     # arithmetic Asians (N <= 27) whose every suffix is a class
+    # The class pass evaluates each (prefix, suffix class) once in FP32 pairs, a class standing for
+    # its multiplicity of paths (a regrouping of eq. f14's sum): its work is counted in
+    # (prefix, class) evaluations, CLS_OPS_SINGLE counted FP32 ops each (CLS_OPS_PAIR for a
+    # call/put pair sharing tau + f); payoff-paths/s is the equivalent count.
     oc = W.batch(36, W.option_sets(0, 64), (W.ASIAN_GEO_CALL, W.LOOKBACK_FIXED_CALL, W.EURO_PUT))
     tc = _timed(lambda: bt.bt_price_exact(ctx.h, oc, bt.BT_PREC_FP32_COMP), reps=2)
+    ev_c = sum(class_evaluations(bt, o) for o in oc)
     out["class_payoffs_n36"] = {
         "workload": "64 sets (seed 0) x {geometric Asian call, fixed-strike lookback call, European put}, N=36, "
                     "FP32_COMP (recombined suffix classes), host arrays in and out",
-        "ms": 1e3 * tc, "payoff_paths_per_s": len(oc) * 2.0 ** 36 / tc}
+        "ms": 1e3 * tc, "prefix_class_evaluations_per_s": ev_c / tc, "ops_per_evaluation": CLS_OPS_SINGLE,
+        "frac_of_issue_peak": CLS_OPS_SINGLE * ev_c / tc / peak,
+        "equivalent_payoff_paths_per_s": len(oc) * 2.0 ** 36 / tc}
     oa = W.batched_exact_workload(24, 0, 64)
     ta = _timed(lambda: bt.bt_price_exact(ctx.h, oa, bt.BT_PREC_FP32_COMP), reps=3)
+    ev_a = sum(class_evaluations(bt, o) for o in oa[::2])     # call/put pairs: one evaluation per pair
     out["small_arith_n24_class_pass"] = {
-        "workload": "64 sets (seed 0) x arithmetic Asian call+put, N=24, FP32_COMP (each suffix a class), "
-                    "host arrays in and out",
-        "ms": 1e3 * ta, "payoff_paths_per_s": len(oa) * 2.0 ** 24 / ta}
+        "workload": "64 sets (seed 0) x arithmetic Asian call+put, N=24, FP32_COMP (each suffix a class, a "
+                    "call/put pair per pass), host arrays in and out",
+        "ms": 1e3 * ta, "prefix_class_pair_evaluations_per_s": ev_a / ta, "ops_per_pair_evaluation": CLS_OPS_PAIR,
+        "frac_of_issue_peak": CLS_OPS_PAIR * ev_a / ta / peak,
+        "equivalent_payoff_paths_per_s": len(oa) * 2.0 ** 24 / ta}
     # the batched workload at N=32 in the all-FP64 kernel (the accuracy reference) beside FP32_COMP
     o32 = W.batched_exact_workload(32, 0, 64)
     t64 = _timed(lambda: bt.bt_price_exact(ctx.h, o32, bt.BT_PREC_FP64), reps=1)
@@ -624,6 +660,59 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def summary(line):
+    """The headline figures of every part in one compact object."""
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+    out = {"exact_n36_paths_per_s": line["value"], "exact_n36_frac_of_issue_peak": g(line, "roofline", "frac"),
+           "e2e_paths_per_s": g(line, "e2e", "value"), "scaling": line["scaling"], "n_gpus": line["n_gpus"]}
+    sv = line.get("serving")
+    if isinstance(sv, dict):
+        out["serving_capacity_rps"] = sv.get("capacity_rps")
+        out["serving_identical_values"] = sv.get("identical_values")
+        out["serving_p50_p99_ms"] = {
+            "%.2f" % r["load_vs_plain_capacity"]: {m: [round(r[m]["p50_ms"], 3), round(r[m]["p99_ms"], 3)]
+                                                 for m in ("plain", "batched")} for r in sv.get("loads", [])}
+    mc = line.get("mc")
+    if isinstance(mc, dict):
+        out["mc_n252_samples_per_s"] = mc.get("samples_per_s")
+        out["mc_frac_of_issue_peak"] = mc.get("frac_of_issue_peak")
+    gr = line.get("greeks")
+    if isinstance(gr, dict):
+        out["greeks_n28_ms"] = gr.get("ms")
+        out["greeks_frac_of_issue_peak"] = gr.get("frac_of_issue_peak")
+    w = line.get("widened")
+    if isinstance(w, dict):
+        out["steps_n32_payoff_paths_per_s"] = g(w, "steps", "payoff_paths_per_s")
+        out["steps_frac_of_issue_peak"] = g(w, "steps", "frac_of_issue_peak")
+        out["trinomial_frac_of_issue_peak"] = g(w, "trinomial_affine", "frac_of_issue_peak")
+        out["class_pass_n36_evaluations_per_s"] = g(w, "class_payoffs_n36", "prefix_class_evaluations_per_s")
+        out["class_pass_n36_frac_of_issue_peak"] = g(w, "class_payoffs_n36", "frac_of_issue_peak")
+        out["n32_fp32_comp_payoff_paths_per_s"] = g(w, "batched_n32_fp64_vs_fp32", "fp32_comp_payoff_paths_per_s")
+        out["n32_fp64_payoff_paths_per_s"] = g(w, "batched_n32_fp64_vs_fp32", "fp64_payoff_paths_per_s")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# The split of one batch across ranks (Section 3, eq. f14/f15)
+# ---------------------------------------------------------------------------
+def split_combine(ex, local_values):
+    """eq. f15 across ranks: every rank's per-option partial values (its work
+    items' discounted sums) are gathered and added in rank order with
+    Neumaier's compensated sum, so every rank returns the same numbers.
+    `ex` is a sharded.Exchange (None for a single rank)."""
+    import numpy as np
+    from paper_1701_03512_gb300 import sharded as S
+    local_values = np.asarray(local_values, dtype=np.float64)
+    if ex is None:
+        return S.combine(local_values[None, :])
+    return S.combine(ex.gather(local_values, "bench-split"))
+
+
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
@@ -652,67 +741,91 @@ def main():
         torch.cuda.synchronize()
 
     ctx = bt.Context(local_rank)
-    # weak scaling: every rank prices its own batch of option sets (seed = rank;
-    # rank 0's is the one-GPU workload), no data crosses between ranks
-    opts = W.batched_exact_workload(args.N, rank, args.sets)
+    split = world > 1 and not args.weak
+    ex = None
+    if split:
+        from paper_1701_03512_gb300 import sharded as S
+        ex = S.Exchange(rank, world, dist.distributed_c10d._get_default_store(), timeout_s=120.0)
+    # split (default): every rank holds the one batch and runs its share of the
+    # work items; weak: every rank prices its own batch (seed = rank; rank 0's
+    # is the one-GPU workload)
+    opts = W.batched_exact_workload(args.N, 0 if split else rank, args.sets)
     plan = bt.bt_exact_plan_create(ctx.h, opts, bt.BT_PREC_FP32_COMP)
     info = bt.bt_exact_plan_info_get(plan)
-    step_paths = info["payoff_paths"]
+    step_paths = info["payoff_paths"]            # the batch: every rank's share together when split
+    shard, n_shards = (rank, world) if split else (0, 1)
     stream = torch.cuda.Stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
-        bt.bt_exact_plan_run(plan, stream)
+        bt.bt_exact_plan_run_shard(plan, shard, n_shards, stream)
+        if split:
+            split_combine(ex, bt.bt_exact_plan_read(plan, stream)["value"])
     stream.synchronize()
 
     sampler = ClockSampler(physical_gpu_index(local_rank))
     sampler.start()
     barrier()
     t_wall0 = time.perf_counter()
-    step_ms, kern_ms = [], []
+    step_ms, kern_ms, xchg_ms = [], [], []
+    res_split = None
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        bt.bt_exact_plan_run(plan, stream)
+        bt.bt_exact_plan_run_shard(plan, shard, n_shards, stream)
         e1.record(stream)
         kern_ms.append(bt.bt_exact_plan_kernel_ms(plan))
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
+        if split:   # the exchange of eq. f15: read this rank's partials, gather, combine (host clock)
+            t0 = time.perf_counter()
+            res_split = split_combine(ex, bt.bt_exact_plan_read(plan, stream)["value"])
+            xchg_ms.append(1e3 * (time.perf_counter() - t0))
     barrier()
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
     res = bt.bt_exact_plan_read(plan, stream)
-    assert np.all(np.isfinite(res["value"])) and np.all(res["value"] >= 0.0)
+    vals = res_split if split else res["value"]
+    assert np.all(np.isfinite(vals)) and np.all(vals >= 0.0)
 
-    tot_s = sum(step_ms) / 1e3
+    tot_s = (sum(step_ms) + sum(xchg_ms)) / 1e3
     if dist is not None:
         t = torch.tensor([tot_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_s = float(t.item())
-    value = world * step_paths * args.steps / tot_s
+    value = (1 if split else world) * step_paths * args.steps / tot_s
 
-    # end to end through the public API with host arrays
+    # end to end through the public API with host arrays (split: the sharded
+    # call, plan creation and the exchange included)
     e2e = None
     if not args.no_e2e:
         host_opts = bt.options_array(opts)
-        bt.bt_price_exact(ctx.h, host_opts, bt.BT_PREC_FP32_COMP, stream)  # warm
+        if split:
+            from paper_1701_03512_gb300 import sharded as S
+
+            def call():
+                return S.price_exact_sharded(ex, opts, bt.BT_PREC_FP32_COMP, ctx.h)
+        else:
+            def call():
+                return bt.bt_price_exact(ctx.h, host_opts, bt.BT_PREC_FP32_COMP, stream)["value"]
+        call()  # warm
         barrier()
         ts = []
         for _ in range(args.steps):
             t0 = time.perf_counter()
-            out = bt.bt_price_exact(ctx.h, host_opts, bt.BT_PREC_FP32_COMP, stream)
+            out = call()
             ts.append(time.perf_counter() - t0)
-            assert np.all(np.isfinite(out["value"]))
+            assert np.all(np.isfinite(out))
         barrier()
         e2e_s = sum(ts)
         if dist is not None:
             t = torch.tensor([e2e_s], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
-        e2e = {"value": world * step_paths * args.steps / e2e_s, "unit": UNIT,
+        e2e = {"value": (1 if split else world) * step_paths * args.steps / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(info["h2d_bytes"]), "d2h_bytes_per_step": int(info["d2h_bytes"]),
                "ms_per_step": 1e3 * e2e_s / args.steps}
 
@@ -728,7 +841,7 @@ def main():
     fmax = float(peaks.get("sm_max_mhz", 2070.0))
     peak_gops = sms * 128 * fmax * 1e6 / 1e9
     kernel_s = statistics.mean(kern_ms) / 1e3
-    achieved = OPS_PER_PATH * step_paths / kernel_s / 1e9
+    achieved = OPS_PER_PATH * step_paths / (world if split else 1) / kernel_s / 1e9   # this rank's share
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s", "frac": achieved / peak_gops,
             "traffic": profiled_traffic(args.N),
             "kernel": "k_exact32", "kernel_ms": 1e3 * kernel_s,
@@ -760,16 +873,25 @@ def main():
         serving = serving_bench(bt, W, sctx, args.serving_requests, loads)
         sctx.close()
 
+    if split:
+        par = ("split%d: one batch, rank r runs work items i %% %d == r (Section 3), one all-gather of the "
+               "per-option partials combined in rank order (eq. f15)" % (world, world))
+    elif world > 1:
+        par = "dp%d: one batch of option sets per rank (seed = rank), no collective on the data path" % world
+    else:
+        par = "single GPU"
+    extra_cfg = {"parallelism": par, "wall_s_timed": t_wall}
+    if split:
+        extra_cfg["exchange_ms_per_step"] = statistics.mean(xchg_ms)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(args, {"parallelism": ("dp%d: one batch of option sets per rank (seed = rank), "
-                                                             "no collective on the data path" % world)
-                                             if world > 1 else "single GPU", "wall_s_timed": t_wall}),
+            "scaling": "weak" if (world > 1 and not split) else "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(args, extra_cfg),
             "fp32_peak_frac": roof["frac"], "clocks": clocks, "e2e": e2e,
             # per step: k_params, k_tables, k_class_tables, k_exact32, k_finalize
             "gpu_launches": 5 * args.steps, "roofline": roof, "cpu_baseline": cpu,
             "serving": serving, "mc": mc, "greeks": greeks, "widened": extras}
+    line["summary"] = summary(line)   # last, so that a kept tail of the line holds it
     print(json.dumps(line), flush=True)
     bt.bt_exact_plan_destroy(plan)
     ctx.close()

@@ -1,7 +1,8 @@
 """One rank of a sharded pricing run, for the multi-process tests.
 
 Usage: python tests/shard_worker.py RANK WORLD PORT OUT.json MODE PROVIDER FAIL
-  MODE      exact | mc
+  MODE      exact | mc | bench (bench.py's split step: the exchange and the
+            rank-order combination of the exact mode's per-option partials)
   PROVIDER  oracle (this rank's part from the CPU oracle) | gpu (from this
             rank's GPU through the C ABI)
   FAIL      none | die (exit before the exchange) | nan (return NaN partials)
@@ -82,7 +83,11 @@ def main():
         os._exit(3)   # leaves between steps, nothing in flight
     res = {}
     try:
-        if mode == "exact":
+        if mode == "bench":
+            import bench
+            part = oracle_exact_part(rank, world) if fail != "nan" else np.full(len(EXACT_OPTS), np.nan)
+            res["value"] = bench.split_combine(ex, part).tolist()
+        elif mode == "exact":
             local = oracle_exact_part if provider == "oracle" else None
             if fail == "nan":
                 local = lambda r, w: np.full(len(EXACT_OPTS), np.nan)  # noqa: E731

@@ -47,6 +47,27 @@ def test_exact_shards_sum_to_the_oracle_value(tmp_path, oracle, world):
     assert all(r["value"] == res[0]["value"] for r in res)   # every rank returns the same numbers
 
 
+@pytest.mark.parametrize("world", [2, 3])
+def test_bench_split_step_sums_to_the_oracle_value(tmp_path, oracle, world):
+    """bench.py's multi-GPU step (every rank runs its share of the work items
+    of one batch, then one all-gather of the per-option partials combined in
+    rank order): the exchange and combination path with oracle parts."""
+    import shard_worker as SW
+    codes, res = run_ranks(tmp_path, world, "bench", ["oracle"] * world)
+    assert codes == [0] * world
+    ref = np.array([oracle.exact(o) for o in SW.EXACT_OPTS])
+    for r in res:
+        assert np.allclose(r["value"], ref, rtol=1e-13, atol=1e-14)
+    assert all(r["value"] == res[0]["value"] for r in res)
+
+
+def test_bench_split_step_names_a_nan_rank(tmp_path):
+    codes, res = run_ranks(tmp_path, 2, "bench", ["oracle", "oracle"], ["none", "nan"])
+    assert codes == [0, 0]
+    for r in res:
+        assert "error" in r and "ranks [1]" in r["error"], r
+
+
 def test_mc_strata_shards_sum_to_the_full_estimate(tmp_path, oracle):
     import shard_worker as SW
     codes, res = run_ranks(tmp_path, 2, "mc", ["oracle", "oracle"])
