@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--no-greeks", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--only", default="",
+                    help="comma-separated widened rows (e.g. steps,trinomial_affine): print only those as a JSON "
+                         "object and exit (for profiling one kernel)")
     ap.add_argument("--weak", action="store_true",
                     help="N > 1: an independent batch per rank instead of one batch split across the ranks")
     return ap.parse_args()
@@ -498,134 +501,154 @@ def class_evaluations(bt, o):
     return float(2 ** P) * classes
 
 
-def extras_bench(bt, W, ctx, sms, fmax, with_cpu=True):
+def extras_bench(bt, W, ctx, sms, fmax, with_cpu=True, only=None):
+    """The widened rows, each timed with host arrays in and out; `only`
+    (a set of row names) runs a subset."""
     import numpy as np
     peak = sms * 128 * fmax * 1e6
-    out = {}
     if with_cpu:
         from oracle import py_oracle as O
-    # time-varying trees, FP32: 8 trees at N=32, an arithmetic Asian call and put on each (a pair
-    # shares one pass)
-    N = 32
-    opts, steps = [], []
-    for i in range(8):
-        st = W.step_factors(900 + i, N, 0.01, 0.05)
-        for pay in (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT):
-            opts.append(W.opt(N, 100.0, 90.0 + 5 * (i % 4), 0.03, 0.2, 1.0, pay))
-            steps.append(st)
-    t = _timed(lambda: bt.bt_price_exact_steps(ctx.h, opts, steps, bt.BT_PREC_FP32_COMP))
-    paths = len(opts) * 2.0 ** N
-    out["steps"] = {"workload": "time-varying trees (per-step u_t, d_t, p_t), 8 trees x arithmetic Asian call+put, "
-                                "16 x 2^32 payoff-paths, FP32_COMP, host arrays in and out",
-                    "ms": 1e3 * t, "payoff_paths_per_s": paths / t, "ops_per_payoff_path": 3,
-                    "frac_of_issue_peak": 3 * paths / t / peak}
-    if with_cpu:
-        out["steps"]["cpu_baseline"] = _oracle_rate(
-            lambda: O.steps_sum_range(opts[0], steps[0], 0, 1 << 22), float(1 << 22),
-            "paths [0, 2^22) of option 0 (arithmetic Asian call), one thread")
-    # generic pass, built-in payoffs, binomial and trinomial
-    N2 = 28
-    o2 = [W.opt(N2, 100.0, 100.0, 0.05, 0.2, 1.0, pay) for pay in (W.ASIAN_ARITH_CALL, W.LOOKBACK_FIXED_CALL)]
-    u, d, p = bt.bt_tree_params(o2[0])
-    mv2 = [np.tile([d, u, 1 - p, p], (N2, 1))] * 2
-    t = _timed(lambda: bt.bt_price_exact_branching(ctx.h, o2, 2, mv2))
-    out["generic_binomial"] = {"workload": "generic pass (FP64 path walk), arithmetic Asian and lookback calls, "
-                                           "N=28, 2 x 2^28 paths", "ms": 1e3 * t,
-                               "payoff_paths_per_s": 2 * 2.0 ** N2 / t}
-    if with_cpu:
-        o2c = dict(o2[0], N=20)
-        out["generic_binomial"]["cpu_baseline"] = _oracle_rate(
-            lambda: O.branch_price(o2c, np.tile([d, u, 1 - p, p], (20, 1)), 2, 1), 2.0 ** 20,
-            "the arithmetic Asian call at N=20 (2^20 paths) through the b-ary enumeration, one thread")
-    # trinomial trees through the affine pass (prefix/suffix tables, FP32), N=22: 8 x 3^22 paths
-    N4 = 22
-    o4 = [W.opt(N4, 100.0, 90.0 + 5 * i, 0.03, 0.2, 1.0, pay)
-          for i in range(4) for pay in (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT)]
-    mv4 = [W.branch_moves(800 + i // 2, N4, 3, 0.01, 0.05, 50.0) for i in range(len(o4))]
-    t = _timed(lambda: bt.bt_price_exact_moves(ctx.h, o4, 3, mv4, bt.BT_PREC_FP32_COMP))
-    paths4 = len(o4) * 3.0 ** N4
-    out["trinomial_affine"] = {"workload": "4 trinomial trees (per-step moves, probabilities Dirichlet(50)) x "
-                                           "arithmetic Asian call+put, N=22, 8 x 3^22 payoff-paths, FP32_COMP, "
-                                           "host arrays in and out",
-                               "ms": 1e3 * t, "payoff_paths_per_s": paths4 / t,
-                               "frac_of_issue_peak": 3 * paths4 / t / peak}
-    if with_cpu:
-        o4c = dict(o4[0], N=13)
-        mv4c = W.branch_moves(800, 13, 3, 0.01, 0.05)
-        out["trinomial_affine"]["cpu_baseline"] = _oracle_rate(
-            lambda: O.branch_price(o4c, mv4c, 3, 1), 3.0 ** 13,
-            "the arithmetic Asian call on a trinomial tree at N=13 (3^13 paths), one thread")
-    N3 = 17
-    o3 = [W.opt(N3, 100.0, 100.0, 0.05, 0.2, 1.0, pay) for pay in (W.ASIAN_ARITH_CALL, W.LOOKBACK_FIXED_CALL)]
-    mv3 = [W.branch_moves(3, N3, 3), W.branch_moves(4, N3, 3)]
-    t = _timed(lambda: bt.bt_price_exact_branching(ctx.h, o3, 3, mv3))
-    out["generic_trinomial"] = {"workload": "generic pass, trinomial trees, arithmetic Asian and lookback calls, "
-                                            "N=17, 2 x 3^17 paths", "ms": 1e3 * t,
-                                "payoff_paths_per_s": 2 * 3.0 ** N3 / t}
-    if with_cpu:
-        o3c = dict(o3[0], N=13)
-        mv3c = W.branch_moves(3, 13, 3)
-        out["generic_trinomial"]["cpu_baseline"] = _oracle_rate(
-            lambda: O.branch_price(o3c, mv3c, 3, 1), 3.0 ** 13,
-            "the arithmetic Asian call on a trinomial tree at N=13 (3^13 paths), one thread")
-    # the plain single-option case: arithmetic Asian call, N=20 (2^20 paths), FP64, one call with
-    # host arrays (its parity against the oracle, <= 1e-12, is asserted by the tests)
-    o1 = W.single_asian_n20()
-    t1 = _timed(lambda: bt.bt_price_exact(ctx.h, [o1], bt.BT_PREC_FP64), reps=5)
-    v1 = float(bt.bt_price_exact(ctx.h, [o1], bt.BT_PREC_FP64)[0]["value"])
-    out["single_asian_n20_fp64"] = {
-        "workload": "arithmetic Asian call, N=20, S0=K=100, rate 0.05, sigma 0.2, T=1, CRR, FP64, one option, "
-                    "host arrays in and out", "ms": 1e3 * t1, "value": v1, "paths_per_s": 2.0 ** 20 / t1}
-    if with_cpu:
-        out["single_asian_n20_fp64"]["cpu_baseline"] = _oracle_rate(
-            lambda: O.price_exhaustive(o1, 1), 2.0 ** 20, "the same option, all 2^20 paths, one thread")
-    # the class pass: recombined classes (geometric, lookback, European) at N=36, and the small
-    # arithmetic Asians (N <= 27) whose every suffix is a class
+
+    def steps_row():
+        # time-varying trees, FP32: 8 trees at N=32, an arithmetic Asian call and put on each (a pair
+        # shares one pass)
+        N = 32
+        opts, steps = [], []
+        for i in range(8):
+            st = W.step_factors(900 + i, N, 0.01, 0.05)
+            for pay in (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT):
+                opts.append(W.opt(N, 100.0, 90.0 + 5 * (i % 4), 0.03, 0.2, 1.0, pay))
+                steps.append(st)
+        t = _timed(lambda: bt.bt_price_exact_steps(ctx.h, opts, steps, bt.BT_PREC_FP32_COMP))
+        paths = len(opts) * 2.0 ** N
+        r = {"workload": "time-varying trees (per-step u_t, d_t, p_t), 8 trees x arithmetic Asian call+put, "
+                         "16 x 2^32 payoff-paths, FP32_COMP, host arrays in and out",
+             "ms": 1e3 * t, "payoff_paths_per_s": paths / t, "ops_per_payoff_path": 3,
+             "frac_of_issue_peak": 3 * paths / t / peak}
+        if with_cpu:
+            r["cpu_baseline"] = _oracle_rate(
+                lambda: O.steps_sum_range(opts[0], steps[0], 0, 1 << 22), float(1 << 22),
+                "paths [0, 2^22) of option 0 (arithmetic Asian call), one thread")
+        return r
+
+    def generic_binomial_row():
+        N2 = 28
+        o2 = [W.opt(N2, 100.0, 100.0, 0.05, 0.2, 1.0, pay) for pay in (W.ASIAN_ARITH_CALL, W.LOOKBACK_FIXED_CALL)]
+        u, d, p = bt.bt_tree_params(o2[0])
+        mv2 = [np.tile([d, u, 1 - p, p], (N2, 1))] * 2
+        t = _timed(lambda: bt.bt_price_exact_branching(ctx.h, o2, 2, mv2))
+        r = {"workload": "generic pass (FP64 path walk), arithmetic Asian and lookback calls, N=28, 2 x 2^28 paths",
+             "ms": 1e3 * t, "payoff_paths_per_s": 2 * 2.0 ** N2 / t}
+        if with_cpu:
+            o2c = dict(o2[0], N=20)
+            r["cpu_baseline"] = _oracle_rate(
+                lambda: O.branch_price(o2c, np.tile([d, u, 1 - p, p], (20, 1)), 2, 1), 2.0 ** 20,
+                "the arithmetic Asian call at N=20 (2^20 paths) through the b-ary enumeration, one thread")
+        return r
+
+    def trinomial_affine_row():
+        # trinomial trees through the affine pass (prefix/suffix tables, FP32), N=22: 8 x 3^22 paths
+        N4 = 22
+        o4 = [W.opt(N4, 100.0, 90.0 + 5 * i, 0.03, 0.2, 1.0, pay)
+              for i in range(4) for pay in (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT)]
+        mv4 = [W.branch_moves(800 + i // 2, N4, 3, 0.01, 0.05, 50.0) for i in range(len(o4))]
+        t = _timed(lambda: bt.bt_price_exact_moves(ctx.h, o4, 3, mv4, bt.BT_PREC_FP32_COMP))
+        paths4 = len(o4) * 3.0 ** N4
+        r = {"workload": "4 trinomial trees (per-step moves, probabilities Dirichlet(50)) x arithmetic Asian "
+                         "call+put, N=22, 8 x 3^22 payoff-paths, FP32_COMP, host arrays in and out",
+             "ms": 1e3 * t, "payoff_paths_per_s": paths4 / t, "frac_of_issue_peak": 3 * paths4 / t / peak}
+        if with_cpu:
+            o4c = dict(o4[0], N=13)
+            mv4c = W.branch_moves(800, 13, 3, 0.01, 0.05, 50.0)
+            r["cpu_baseline"] = _oracle_rate(
+                lambda: O.branch_price(o4c, mv4c, 3, 1), 3.0 ** 13,
+                "the arithmetic Asian call on a trinomial tree at N=13 (3^13 paths), one thread")
+        return r
+
+    def generic_trinomial_row():
+        N3 = 17
+        o3 = [W.opt(N3, 100.0, 100.0, 0.05, 0.2, 1.0, pay) for pay in (W.ASIAN_ARITH_CALL, W.LOOKBACK_FIXED_CALL)]
+        mv3 = [W.branch_moves(3, N3, 3), W.branch_moves(4, N3, 3)]
+        t = _timed(lambda: bt.bt_price_exact_branching(ctx.h, o3, 3, mv3))
+        r = {"workload": "generic pass, trinomial trees, arithmetic Asian and lookback calls, N=17, 2 x 3^17 paths",
+             "ms": 1e3 * t, "payoff_paths_per_s": 2 * 3.0 ** N3 / t}
+        if with_cpu:
+            o3c = dict(o3[0], N=13)
+            mv3c = W.branch_moves(3, 13, 3)
+            r["cpu_baseline"] = _oracle_rate(
+                lambda: O.branch_price(o3c, mv3c, 3, 1), 3.0 ** 13,
+                "the arithmetic Asian call on a trinomial tree at N=13 (3^13 paths), one thread")
+        return r
+
+    def single_row():
+        # the plain single-option case: arithmetic Asian call, N=20 (2^20 paths), FP64, one call with
+        # host arrays (its parity against the oracle, <= 1e-12, is asserted by the tests)
+        o1 = W.single_asian_n20()
+        t1 = _timed(lambda: bt.bt_price_exact(ctx.h, [o1], bt.BT_PREC_FP64), reps=5)
+        v1 = float(bt.bt_price_exact(ctx.h, [o1], bt.BT_PREC_FP64)[0]["value"])
+        r = {"workload": "arithmetic Asian call, N=20, S0=K=100, rate 0.05, sigma 0.2, T=1, CRR, FP64, one option, "
+                         "host arrays in and out", "ms": 1e3 * t1, "value": v1, "paths_per_s": 2.0 ** 20 / t1}
+        if with_cpu:
+            r["cpu_baseline"] = _oracle_rate(lambda: O.price_exhaustive(o1, 1), 2.0 ** 20,
+                                             "the same option, all 2^20 paths, one thread")
+        return r
+
     # The class pass evaluates each (prefix, suffix class) once in FP32 pairs, a class standing for
     # its multiplicity of paths (a regrouping of eq. f14's sum): its work is counted in
     # (prefix, class) evaluations, CLS_OPS_SINGLE counted FP32 ops each (CLS_OPS_PAIR for a
     # call/put pair sharing tau + f); payoff-paths/s is the equivalent count.
-    oc = W.batch(36, W.option_sets(0, 64), (W.ASIAN_GEO_CALL, W.LOOKBACK_FIXED_CALL, W.EURO_PUT))
-    tc = _timed(lambda: bt.bt_price_exact(ctx.h, oc, bt.BT_PREC_FP32_COMP), reps=2)
-    ev_c = sum(class_evaluations(bt, o) for o in oc)
-    out["class_payoffs_n36"] = {
-        "workload": "64 sets (seed 0) x {geometric Asian call, fixed-strike lookback call, European put}, N=36, "
-                    "FP32_COMP (recombined suffix classes), host arrays in and out",
-        "ms": 1e3 * tc, "prefix_class_evaluations_per_s": ev_c / tc, "ops_per_evaluation": CLS_OPS_SINGLE,
-        "frac_of_issue_peak": CLS_OPS_SINGLE * ev_c / tc / peak,
-        "equivalent_payoff_paths_per_s": len(oc) * 2.0 ** 36 / tc}
-    oa = W.batched_exact_workload(24, 0, 64)
-    ta = _timed(lambda: bt.bt_price_exact(ctx.h, oa, bt.BT_PREC_FP32_COMP), reps=3)
-    ev_a = sum(class_evaluations(bt, o) for o in oa[::2])     # call/put pairs: one evaluation per pair
-    out["small_arith_n24_class_pass"] = {
-        "workload": "64 sets (seed 0) x arithmetic Asian call+put, N=24, FP32_COMP (each suffix a class, a "
-                    "call/put pair per pass), host arrays in and out",
-        "ms": 1e3 * ta, "prefix_class_pair_evaluations_per_s": ev_a / ta, "ops_per_pair_evaluation": CLS_OPS_PAIR,
-        "frac_of_issue_peak": CLS_OPS_PAIR * ev_a / ta / peak,
-        "equivalent_payoff_paths_per_s": len(oa) * 2.0 ** 24 / ta}
-    # the batched workload at N=32 in the all-FP64 kernel (the accuracy reference) beside FP32_COMP
-    o32 = W.batched_exact_workload(32, 0, 64)
-    t64 = _timed(lambda: bt.bt_price_exact(ctx.h, o32, bt.BT_PREC_FP64), reps=1)
-    t32 = _timed(lambda: bt.bt_price_exact(ctx.h, o32, bt.BT_PREC_FP32_COMP), reps=2)
-    out["batched_n32_fp64_vs_fp32"] = {
-        "workload": "batched arithmetic-Asian call+put, N=32, 64 sets (seed 0), host arrays in and out",
-        "fp64_s": t64, "fp32_comp_s": t32, "fp64_payoff_paths_per_s": 128 * 2.0 ** 32 / t64,
-        "fp32_comp_payoff_paths_per_s": 128 * 2.0 ** 32 / t32}
-    # the paper's runtime workload (Section 5): a European put, K=10, S0=5,
-    # sigma 0.3, rate 0.06, T=1, CRR, N=32; the paper's 64-core Julia run took
-    # 13:38 (818 s) and R 2:22:59 (8579 s) on 2x E5-2650v2 nodes
-    op = W.paper_runtime_workload(32)
-    t_fast = _timed(lambda: bt.bt_price_exact(ctx.h, [op], bt.BT_PREC_FP64))
-    u, d, p = bt.bt_tree_params(op)
-    mvp = [np.tile([d, u, 1 - p, p], (32, 1))]
-    t_walk = _timed(lambda: bt.bt_price_exact_branching(ctx.h, [op], 2, mvp), reps=1)
-    out["paper_runtime_workload"] = {
-        "workload": "European put, K=10, S0=5, sigma 0.3, rate 0.06, T=1, CRR, N=32 (2^32 paths)",
-        "exact_fp64_s": t_fast, "generic_per_path_walk_s": t_walk,
-        "paper_context": {"julia_64_cores_s": 818, "r_64_cores_s": 8579,
-                          "hardware": "8 nodes of 2x Intel E5-2650v2 (16 cores each), QDR InfiniBand",
-                          "note": "context, not the target: the paper's workload on the paper's cluster"}}
-    return out
+    def class_row():
+        # recombined classes (geometric, lookback, European) at N=36
+        oc = W.batch(36, W.option_sets(0, 64), (W.ASIAN_GEO_CALL, W.LOOKBACK_FIXED_CALL, W.EURO_PUT))
+        tc = _timed(lambda: bt.bt_price_exact(ctx.h, oc, bt.BT_PREC_FP32_COMP), reps=2)
+        ev = sum(class_evaluations(bt, o) for o in oc)
+        return {"workload": "64 sets (seed 0) x {geometric Asian call, fixed-strike lookback call, European put}, "
+                            "N=36, FP32_COMP (recombined suffix classes), host arrays in and out",
+                "ms": 1e3 * tc, "prefix_class_evaluations_per_s": ev / tc, "ops_per_evaluation": CLS_OPS_SINGLE,
+                "frac_of_issue_peak": CLS_OPS_SINGLE * ev / tc / peak,
+                "equivalent_payoff_paths_per_s": len(oc) * 2.0 ** 36 / tc}
+
+    def small_arith_row():
+        # the small arithmetic Asians (N <= 27), every suffix a class
+        oa = W.batched_exact_workload(24, 0, 64)
+        ta = _timed(lambda: bt.bt_price_exact(ctx.h, oa, bt.BT_PREC_FP32_COMP), reps=3)
+        ev = sum(class_evaluations(bt, o) for o in oa[::2])     # call/put pairs: one evaluation per pair
+        return {"workload": "64 sets (seed 0) x arithmetic Asian call+put, N=24, FP32_COMP (each suffix a class, "
+                            "a call/put pair per pass), host arrays in and out",
+                "ms": 1e3 * ta, "prefix_class_pair_evaluations_per_s": ev / ta,
+                "ops_per_pair_evaluation": CLS_OPS_PAIR, "frac_of_issue_peak": CLS_OPS_PAIR * ev / ta / peak,
+                "equivalent_payoff_paths_per_s": len(oa) * 2.0 ** 24 / ta}
+
+    def n32_row():
+        # the batched workload at N=32 in the all-FP64 kernel (the accuracy reference) beside FP32_COMP
+        o32 = W.batched_exact_workload(32, 0, 64)
+        t64 = _timed(lambda: bt.bt_price_exact(ctx.h, o32, bt.BT_PREC_FP64), reps=1)
+        t32 = _timed(lambda: bt.bt_price_exact(ctx.h, o32, bt.BT_PREC_FP32_COMP), reps=2)
+        return {"workload": "batched arithmetic-Asian call+put, N=32, 64 sets (seed 0), host arrays in and out",
+                "fp64_s": t64, "fp32_comp_s": t32, "fp64_payoff_paths_per_s": 128 * 2.0 ** 32 / t64,
+                "fp32_comp_payoff_paths_per_s": 128 * 2.0 ** 32 / t32}
+
+    def paper_row():
+        # the paper's runtime workload (Section 5): a European put, K=10, S0=5,
+        # sigma 0.3, rate 0.06, T=1, CRR, N=32; the paper's 64-core Julia run took
+        # 13:38 (818 s) and R 2:22:59 (8579 s) on 2x E5-2650v2 nodes
+        op = W.paper_runtime_workload(32)
+        t_fast = _timed(lambda: bt.bt_price_exact(ctx.h, [op], bt.BT_PREC_FP64))
+        u, d, p = bt.bt_tree_params(op)
+        mvp = [np.tile([d, u, 1 - p, p], (32, 1))]
+        t_walk = _timed(lambda: bt.bt_price_exact_branching(ctx.h, [op], 2, mvp), reps=1)
+        return {"workload": "European put, K=10, S0=5, sigma 0.3, rate 0.06, T=1, CRR, N=32 (2^32 paths)",
+                "exact_fp64_s": t_fast, "generic_per_path_walk_s": t_walk,
+                "paper_context": {"julia_64_cores_s": 818, "r_64_cores_s": 8579,
+                                  "hardware": "8 nodes of 2x Intel E5-2650v2 (16 cores each), QDR InfiniBand",
+                                  "note": "context, not the target: the paper's workload on the paper's cluster"}}
+
+    rows = (("steps", steps_row), ("generic_binomial", generic_binomial_row),
+            ("trinomial_affine", trinomial_affine_row), ("generic_trinomial", generic_trinomial_row),
+            ("single_asian_n20_fp64", single_row), ("class_payoffs_n36", class_row),
+            ("small_arith_n24_class_pass", small_arith_row), ("batched_n32_fp64_vs_fp32", n32_row),
+            ("paper_runtime_workload", paper_row))
+    return {name: fn() for name, fn in rows if only is None or name in only}
 
 
 # ---------------------------------------------------------------------------
@@ -730,6 +753,14 @@ def main():
     from paper_1701_03512_gb300 import workloads as W
 
     torch.cuda.set_device(local_rank)
+    if args.only:
+        ctx = bt.Context(local_rank)
+        sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+        fmax = float(measured_peaks().get("sm_max_mhz", 2070.0))
+        rows = extras_bench(bt, W, ctx, sms, fmax, with_cpu=False, only=set(args.only.split(",")))
+        print(json.dumps(rows), flush=True)
+        ctx.close()
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -117,6 +117,25 @@ void ctx_free(bt_ctx *c, void *p, size_t bytes) {
 
 cudaStream_t ctx_stream(bt_ctx *c, void *s) { return s ? (cudaStream_t)s : c->stream; }
 
+// The context's reusable scratch of at least `bytes` (the caller holds
+// cache_mu): grown on demand, after the context's stream has drained the work
+// that used the old one; freed with the context.
+bt_status ctx_scratch(bt_ctx *c, size_t bytes, void **p) {
+    if (c->cache_bytes < bytes) {
+        if (c->cache) {
+            cudaStreamSynchronize(c->stream);
+            ctx_free(c, c->cache, c->cache_bytes);
+            c->cache = nullptr;
+            c->cache_bytes = 0;
+        }
+        bt_status s = ctx_alloc(c, bytes, &c->cache);
+        if (s != BT_OK) return s;
+        c->cache_bytes = bytes;
+    }
+    *p = c->cache;
+    return BT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Tree parameters on the host (validation) -- Section 2, A1-A3
 // ---------------------------------------------------------------------------
@@ -483,21 +502,11 @@ static bt_status plan_create(bt_ctx *ctx, const bt_option *opts, int32_t n, bt_p
     cudaSetDevice(ctx->device);
     void *arena = nullptr;
     if (cached) {
-        if (ctx->cache_bytes < off) {
-            if (ctx->cache) {
-                cudaStreamSynchronize(ctx->stream);
-                ctx_free(ctx, ctx->cache, ctx->cache_bytes);
-                ctx->cache = nullptr;
-                ctx->cache_bytes = 0;
-            }
-            s = ctx_alloc(ctx, off, &ctx->cache);
-            if (s != BT_OK) {
-                delete pl;
-                return s;
-            }
-            ctx->cache_bytes = off;
+        s = ctx_scratch(ctx, off, &arena);
+        if (s != BT_OK) {
+            delete pl;
+            return s;
         }
-        arena = ctx->cache;
         pl->cached = true;
     } else {
         s = ctx_alloc(ctx, off, &arena);

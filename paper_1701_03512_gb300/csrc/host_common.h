@@ -27,6 +27,7 @@ bt_status bt_cuda_fail(int err, const char *what);
 bt_status ctx_alloc(bt_ctx *c, size_t bytes, void **p);
 void ctx_free(bt_ctx *c, void *p, size_t bytes);
 cudaStream_t ctx_stream(bt_ctx *c, void *s);
+bt_status ctx_scratch(bt_ctx *c, size_t bytes, void **p);
 bt_status host_tree(const bt_option *o, double *u, double *d, double *p);
 bt_status validate_option(const bt_option *o, int idx, int max_n);
 int exact_split_L(int N);

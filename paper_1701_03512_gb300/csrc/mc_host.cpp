@@ -113,6 +113,8 @@ static bt_status mc_run(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t s
         a.n_items = items;
         a.item_stats = d_stats;
         a.counter = d_cnt;
+        a.key_lo = (uint32_t)(seed & 0xffffffffu);
+        a.key_hi = (uint32_t)(seed >> 32);
         int le = bt_launch_mc(&a, kind == BT_MC_SHARED, bt_mc_grid_size(ctx->device, kind == BT_MC_SHARED), st);
         if (le) rs = bt_cuda_fail(le, "MC kernel");
     }

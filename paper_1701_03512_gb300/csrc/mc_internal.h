@@ -30,6 +30,8 @@ struct bt_mc_args {
     const bt_mc_job *jobs;
     int32_t n_jobs;
     int32_t pad;
+    uint32_t key_lo, key_hi;       // the Philox key (the seed), the same for every job of a launch: as a
+                                   // kernel argument it is warp-uniform, and so are its round keys
     int64_t n_items;
     double4 *item_stats;           // per item: (count, mean, M2, stratum)
     unsigned long long *counter;

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "host_common.h"
@@ -153,8 +154,10 @@ static bt_status price_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int 
     const size_t o_out = off; off = up256(off + sizeof(bt_result) * n);
     const size_t o_cnt = off; off = up256(off + sizeof(unsigned long long));
     cudaSetDevice(ctx->device);
+    // the context's reusable scratch (no allocation per call once it is large enough)
+    std::lock_guard<std::mutex> lock(ctx->cache_mu);
     void *arena = nullptr;
-    bt_status rs = ctx_alloc(ctx, off, &arena);
+    bt_status rs = ctx_scratch(ctx, off, &arena);
     if (rs != BT_OK) return rs;
     char *base = (char *)arena;
     bt_option *d_opts = (bt_option *)(base + o_opts);
@@ -202,8 +205,7 @@ static bt_status price_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int 
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rs = bt_cuda_fail(e, "move-by-move pass: results");
     }
-    cudaStreamSynchronize(st);
-    ctx_free(ctx, arena, off);
+    cudaStreamSynchronize(st);   // the scratch is free for the next call only after this one's work
     if (rs == BT_OK)
         for (int i = 0; i < n; ++i) {  // b^N paths (finalize wrote 2^N)
             long long paths = 1;
