@@ -92,6 +92,8 @@ def parse():
                          "object and exit (for profiling one kernel)")
     ap.add_argument("--weak", action="store_true",
                     help="N > 1: an independent batch per rank instead of one batch split across the ranks")
+    ap.add_argument("--split", action="store_true",
+                    help="the split step (shard run, partials read back, rank-order combination) also at N = 1")
     return ap.parse_args()
 
 
@@ -772,9 +774,9 @@ def main():
         torch.cuda.synchronize()
 
     ctx = bt.Context(local_rank)
-    split = world > 1 and not args.weak
+    split = (world > 1 and not args.weak) or args.split
     ex = None
-    if split:
+    if split and world > 1:
         from paper_1701_03512_gb300 import sharded as S
         ex = S.Exchange(rank, world, dist.distributed_c10d._get_default_store(), timeout_s=120.0)
     # split (default): every rank holds the one batch and runs its share of the
@@ -834,7 +836,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         host_opts = bt.options_array(opts)
-        if split:
+        if split and ex is not None:
             from paper_1701_03512_gb300 import sharded as S
 
             def call():
