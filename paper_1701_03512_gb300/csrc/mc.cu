@@ -176,6 +176,9 @@ __device__ __forceinline__ void simulate_w(const bt_mc_job &J, const unsigned (&
 #ifndef BT_MC_WALKERS
 #define BT_MC_WALKERS 4   // samples per thread at once in the Partitioned kernel (measured: 2 < 8 < 4)
 #endif
+#ifndef BT_MC_WARP_THREADS
+#define BT_MC_WARP_THREADS 256   // block size of the Partitioned kernel (its warps are independent)
+#endif
 #ifndef BT_MC_MIN_BLOCKS
 #define BT_MC_MIN_BLOCKS 2   // resident blocks per SM the Partitioned kernel is compiled for
 #endif
@@ -372,7 +375,7 @@ __device__ __forceinline__ void mc_warp_item(const bt_mc_args &a, const bt_mc_jo
     if (lane == 0) a.item_stats[J.item_begin + item_local] = make_double4(n, mean, M2, (double)m);
 }
 
-__global__ void __launch_bounds__(BT_THREADS, BT_MC_MIN_BLOCKS) k_mc_warp(bt_mc_args a) {
+__global__ void __launch_bounds__(BT_MC_WARP_THREADS, BT_MC_MIN_BLOCKS) k_mc_warp(bt_mc_args a) {
     const int lane = threadIdx.x & 31;
     int cur_job = -1;
     int64_t cur_stratum = -1;
@@ -522,9 +525,10 @@ extern "C" int bt_launch_mc(const bt_mc_args *a, int shared, int grid, void *str
         if ((int64_t)grid > a->n_items) grid = (int)a->n_items;
         k_mc<<<grid, BT_THREADS, 0, (cudaStream_t)stream>>>(*a);
     } else {
-        const int64_t warps = (int64_t)grid * (BT_THREADS / 32);
-        if (warps > a->n_items) grid = (int)((a->n_items + BT_THREADS / 32 - 1) / (BT_THREADS / 32));
-        k_mc_warp<<<grid, BT_THREADS, 0, (cudaStream_t)stream>>>(*a);
+        const int64_t warps = (int64_t)grid * (BT_MC_WARP_THREADS / 32);
+        if (warps > a->n_items)
+            grid = (int)((a->n_items + BT_MC_WARP_THREADS / 32 - 1) / (BT_MC_WARP_THREADS / 32));
+        k_mc_warp<<<grid, BT_MC_WARP_THREADS, 0, (cudaStream_t)stream>>>(*a);
     }
     return (int)cudaGetLastError();
 }
@@ -549,7 +553,7 @@ extern "C" int bt_mc_grid_size(int device, int shared) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (shared) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc, BT_THREADS, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_warp, BT_THREADS, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_warp, BT_MC_WARP_THREADS, 0);
     if (per < 1) per = 1;
     return sms * per;
 }
