@@ -29,7 +29,9 @@
 #define BT_SUF_MAX ((1 << BT_MAX_L) + (BT_MAX_L + 1) * (BT_UNROLL - 1))
 #define BT_SUF_MAX_EVEN ((BT_SUF_MAX + 1) & ~1)   // float2 count keeping what follows 16-byte aligned
 #define BT_LVL_NONE 30000      // sentinel level: "no price in this block"
-#define BT_CLS_UNROLL 4        // class groups are padded to a multiple of this
+#ifndef BT_CLS_UNROLL
+#define BT_CLS_UNROLL 2        // class groups are padded to a multiple of this (measured: 2 beats 1 and 4)
+#endif
 #define BT_KEY_SPAN (BT_MAX_L * (BT_MAX_L + 1) / 2)   // |class key| <= this (level sum of the suffix)
 
 // What the suffix table of a job holds (one field per job).

@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "host_common.h"
@@ -88,8 +89,10 @@ extern "C" bt_status bt_greeks_exact(bt_ctx *ctx, const bt_option *opts, int32_t
     const size_t o_sum = off; off = up256(off + sizeof(double4) * n);
     const size_t o_cnt = off; off = up256(off + sizeof(unsigned long long));
     cudaSetDevice(ctx->device);
+    // the context's reusable scratch (no allocation per call once it is large enough)
+    std::lock_guard<std::mutex> lock(ctx->cache_mu);
     void *arena = nullptr;
-    bt_status s = ctx_alloc(ctx, off, &arena);
+    bt_status s = ctx_scratch(ctx, off, &arena);
     if (s != BT_OK) return s;
     char *b = (char *)arena;
     bt_option *d_opts = (bt_option *)(b + o_opts);
@@ -141,8 +144,7 @@ extern "C" bt_status bt_greeks_exact(bt_ctx *ctx, const bt_option *opts, int32_t
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rs = bt_cuda_fail(e, "bt_greeks_exact: results");
     }
-    cudaStreamSynchronize(st);
-    ctx_free(ctx, arena, off);
+    cudaStreamSynchronize(st);   // the scratch is free for the next call only after this one's work
     if (rs != BT_OK) return rs;
     for (int i = 0; i < n; ++i) {
         const bt_option &o = opts[i];

@@ -3,6 +3,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "host_common.h"
@@ -90,8 +91,10 @@ static bt_status mc_run(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t s
     const size_t o_nmq = off; off = up256(off + sizeof(double4) * strata_total);
     const size_t o_cnt = off; off = up256(off + sizeof(unsigned long long));
     cudaSetDevice(ctx->device);
+    // the context's reusable scratch (no allocation per call once it is large enough)
+    std::lock_guard<std::mutex> lock(ctx->cache_mu);
     void *arena = nullptr;
-    bt_status s = ctx_alloc(ctx, off, &arena);
+    bt_status s = ctx_scratch(ctx, off, &arena);
     if (s != BT_OK) return s;
     char *b = (char *)arena;
     bt_mc_job *d_jobs = (bt_mc_job *)(b + o_jobs);
@@ -129,8 +132,7 @@ static bt_status mc_run(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t s
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rs = bt_cuda_fail(e, "bt_price_mc: results");
     }
-    cudaStreamSynchronize(st);
-    ctx_free(ctx, arena, off);
+    cudaStreamSynchronize(st);   // the scratch is free for the next call only after this one's work
     return rs;
 }
 

@@ -190,8 +190,10 @@ static bt_status generic_run(bt_ctx *ctx, const bt_payoff_plugin *pl, const bt_o
     const size_t o_part = off; off = up256(off + sizeof(double) * items);
     const size_t o_cnt = off; off = up256(off + sizeof(unsigned long long));
     cudaSetDevice(ctx->device);
+    // the context's reusable scratch (no allocation per call once it is large enough)
+    std::lock_guard<std::mutex> lock(ctx->cache_mu);
     void *arena = nullptr;
-    bt_status rs = ctx_alloc(ctx, off, &arena);
+    bt_status rs = ctx_scratch(ctx, off, &arena);
     if (rs != BT_OK) return rs;
     char *base = (char *)arena;
     const double *d_mv = (const double *)(base + o_mv);
@@ -222,8 +224,7 @@ static bt_status generic_run(bt_ctx *ctx, const bt_payoff_plugin *pl, const bt_o
     if (e == cudaSuccess) e = cudaMemcpyAsync(part.data(), base + o_part, sizeof(double) * items, cudaMemcpyDeviceToHost, sm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
     if (e != cudaSuccess) rs = bt_cuda_fail(e, "generic path pass");
-    cudaStreamSynchronize(sm);
-    ctx_free(ctx, arena, off);
+    cudaStreamSynchronize(sm);   // the scratch is free for the next call only after this one's work
     if (rs != BT_OK) return rs;
     for (int i = 0; i < n; ++i) {
         const btp::job &J = jobs[i];

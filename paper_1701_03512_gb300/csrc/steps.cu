@@ -213,15 +213,19 @@ __global__ void k_steps_tables(const bt_job *jobs, const bt_jparams *prm, const 
 
 // FP32 suffix weights by error diffusion (one block per job, FP32 tables):
 // the entries (f_hi, -f_lo, w_hi, w_lo) written by k_steps_tables are sorted
-// by f = f_hi + f_lo (bitonic sort in shared memory, padding keys +inf), then
-// one thread walks them in ascending f carrying the rounding residual:
-// w32 = RN_f32(w + carry), carry = w + carry - w32, so that the residuals of
-// any run of consecutive f telescope to the difference of two carries, each
-// at most half an FP32 ulp. The entry keeps (f_hi, -f_lo, w32, 0).
+// by f = f_hi + f_lo (bitonic sort in shared memory on the bit patterns of the
+// FP64 values, which order like the values since every f_s > 0; padding keys
+// after every suffix), then one thread walks them in ascending f carrying the
+// rounding residual: w32 = RN_f32(w + carry), carry = w + carry - w32, with
+// w the FP32 pair (w_hi, w_lo) and the carry kept exactly by error-free sums
+// (TwoSum, Fast2Sum), so that the residuals of any run of consecutive f
+// telescope to the difference of two carries, each at most half an FP32 ulp.
+// A weight of 0 (a branch of probability 0) stays 0. The entry keeps
+// (f_hi, -f_lo, w32, 0).
 #define BT_SORT_N (1 << BT_STEPS_MAX_L)
 __global__ void __launch_bounds__(1024) k_steps_weights(const bt_job *jobs, float4 *suf32) {
     const bt_job J = jobs[blockIdx.x];
-    __shared__ double key[BT_SORT_N];
+    __shared__ unsigned long long key[BT_SORT_N];
     __shared__ int16_t idx[BT_SORT_N];
     const int n = (int)J.n_suffix;
     int np = 1;
@@ -230,9 +234,9 @@ __global__ void __launch_bounds__(1024) k_steps_weights(const bt_job *jobs, floa
     for (int i = threadIdx.x; i < np; i += blockDim.x) {
         if (i < n) {
             const float4 e = tab[i];
-            key[i] = (double)e.x - (double)e.y;   // f_hi - (-f_lo), exact in FP64
+            key[i] = (unsigned long long)__double_as_longlong((double)e.x - (double)e.y);  // f, exact in FP64
         } else {
-            key[i] = __longlong_as_double(0x7ff0000000000000ll);   // +inf after every suffix
+            key[i] = ~0ull;
         }
         idx[i] = (int16_t)i;
     }
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(1024) k_steps_weights(const bt_job *jobs, floa
             for (int i = threadIdx.x; i < np; i += blockDim.x) {
                 const int l = i ^ j;
                 if (l <= i) continue;
-                const double a = key[i], c = key[l];
+                const unsigned long long a = key[i], c = key[l];
                 const bool asc = (i & k) == 0;
                 if (asc ? a > c : a < c) {
                     key[i] = c;
@@ -255,24 +259,28 @@ __global__ void __launch_bounds__(1024) k_steps_weights(const bt_job *jobs, floa
             __syncthreads();
         }
     }
+    float2 *wp = reinterpret_cast<float2 *>(key);   // the keys are no longer needed
     for (int r = threadIdx.x; r < n; r += blockDim.x) {   // the weights in ascending f
         const float4 e = tab[idx[r]];
-        key[r] = (double)e.z + (double)e.w;
+        wp[r] = make_float2(e.z, e.w);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double carry = 0.0;
+        float carry = 0.0f;
         for (int r = 0; r < n; ++r) {
-            const double target = key[r] + carry;
-            const float w32 = __double2float_rn(target);
-            carry = target - (double)w32;
-            key[r] = (double)w32;
+            const float2 w = wp[r];
+            if (w.x == 0.0f) continue;               // probability 0: weight 0, carry kept
+            const df32 t = two_sum(w.x, carry);      // w_hi + carry, exactly
+            const float lo = __fadd_rn(t.lo, w.y);   // + w_lo (error 2^-24 of a 2^-24 term)
+            const float h = __fadd_rn(t.hi, lo);     // the target rounded once to FP32
+            carry = __fsub_rn(lo, __fsub_rn(h, t.hi));   // Fast2Sum remainder (|t.hi| >= |lo|)
+            wp[r].x = h;
         }
     }
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
         float4 &e = tab[idx[r]];
-        e.z = (float)key[r];
+        e.z = wp[r].x;
         e.w = 0.0f;
     }
 }
