@@ -92,7 +92,6 @@ struct bt_jparams {
     double S0, K;
     double NKoS0, KoS0, S0oN;
     double fmin, fmax;
-    double wmax;                     // probability of the likeliest path
     double W[BT_MAX_L + 1];          // suffix-group weights p^k (1-p)^{L-k}
     double wl[BT_LOW_BITS + 1];      // p^c (1-p)^{Plo-c}, Plo = min(P, BT_LOW_BITS)
     double wh[BT_MAX_N_EXACT + 1];   // p^c (1-p)^{Phi-c}, Phi = P - Plo

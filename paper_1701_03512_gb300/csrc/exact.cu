@@ -86,7 +86,6 @@ __global__ void k_params(const bt_option *opts, const bt_job *jobs, bt_jparams *
     memset(&P, 0, sizeof(P));
     P.ok = dev_tree(o, &P.u, &P.d, &P.p);
     P.disc = exp(-o.rate * o.T);
-    P.wmax = pow(fmax(P.p, 1.0 - P.p), (double)J.N);
     P.lnu = log(P.u);
     P.S0 = o.S0;
     P.K = o.K;

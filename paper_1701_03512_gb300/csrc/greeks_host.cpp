@@ -55,7 +55,7 @@ extern "C" bt_status bt_greeks_exact(bt_ctx *ctx, const bt_option *opts, int32_t
         bt_job &J = jobs[i];
         memset(&J, 0, sizeof(J));
         int step = 1;
-        plan_one_job(opts + i, 1, 0, &J, &step, BT_PREC_FP32_COMP);  // one option per pass (no call/put fusion)
+        plan_one_job(opts + i, 1, 0, &J, &step, BT_PREC_FP32_COMP);  // one option per pass
         J.opt = i;
         J.out_call = J.out_call >= 0 ? i : -1;
         J.out_put = J.out_put >= 0 ? i : -1;

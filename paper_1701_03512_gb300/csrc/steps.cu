@@ -121,13 +121,6 @@ __global__ void k_steps_params(const bt_option *opts, const bt_job *jobs, const 
     P.KoS0 = o.K / o.S0;
     P.S0oN = o.S0 / (double)J.N;
     const int b = J.branches;
-    P.wmax = 1.0;  // the likeliest path: the likeliest move of every step
-    for (int t = 0; t < J.N; ++t) {
-        const double *m = steps + 2 * b * (J.off_pow + t) + b;
-        double q = 0.0;
-        for (int k = 0; k < b; ++k) q = fmax(q, m[k]);
-        P.wmax *= q;
-    }
     const double *st = steps + 2 * b * (J.off_pow + J.P);
     P.fmin = suffix_f(J.field, walk_steps(0, J.L, b, st, -1), J.N);
     P.fmax = suffix_f(J.field, walk_steps(0, J.L, b, st, +1), J.N);
