@@ -132,6 +132,27 @@ def test_batch_matches_singles_bit_for_bit(bt, ctx):
         assert bt.bt_price_exact_steps(ctx.h, [o], [steps[i]], 1)["value"][0] == batch[i]
 
 
+@pytest.mark.parametrize("N,prec", [(30, 1), (22, 0), (22, 1)])
+def test_call_put_pair_matches_each_alone(bt, ctx, N, prec):
+    """A call followed by the put of the same steps and strike share one pass
+    (the affine form computed once); each payoff's arithmetic is that of its
+    own pass, so the values are the same bits as pricing each alone. A pair
+    whose steps differ is not fused and prices the same way."""
+    steps = W.step_factors(70 + N, N, 0.01, 0.05, 0.45, 0.55)
+    for field in ((W.EURO_CALL, W.EURO_PUT), (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT),
+                  (W.ASIAN_GEO_PUT, W.ASIAN_GEO_CALL)):
+        pair = [W.opt(N, 100.0, 101.0, 0.03, 0.2, 1.0, pay) for pay in field]
+        fused = bt.bt_price_exact_steps(ctx.h, pair, [steps, steps], prec)["value"]
+        alone = [bt.bt_price_exact_steps(ctx.h, [o], [steps], prec)["value"][0] for o in pair]
+        assert fused.tolist() == alone, (N, prec, field)
+    other = steps.copy()
+    other[3, 0] *= 1.001
+    pair = [W.opt(N, 100.0, 101.0, 0.03, 0.2, 1.0, pay) for pay in (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT)]
+    two = bt.bt_price_exact_steps(ctx.h, pair, [steps, other], prec)["value"]
+    assert two[0] == bt.bt_price_exact_steps(ctx.h, pair[:1], [steps], prec)["value"][0]
+    assert two[1] == bt.bt_price_exact_steps(ctx.h, pair[1:], [other], prec)["value"][0]
+
+
 def test_invalid_steps(bt, ctx):
     o = W.opt(6, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
     good = W.step_factors(1, 6)
