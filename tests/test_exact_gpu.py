@@ -362,6 +362,25 @@ def test_effective_path_threshold(bt, ctx, oracle, N):
         assert np.allclose(got["err_est"], 1e-9 * np.abs(got["value"]), rtol=1e-12)
 
 
+@pytest.mark.parametrize("N", [28, 32])
+def test_per_path_pass_across_the_accepted_skews(bt, ctx, oracle, N):
+    """The per-path FP32 pass over the trees it accepts, from p = 1/2 to the
+    effective-path bound (2^27): explicit lattices with small and large moves,
+    calls and puts from deep in to deep out of the money, every value within
+    1e-9 of the oracle's meet-in-the-middle value (plus 1e-12 S0)."""
+    pc = _p_at_neff(N, 27.0)
+    opts = []
+    for u in (1.02, 1.05):
+        for p in np.linspace(0.5, pc - 1e-3, 4):
+            for pp in (p, 1.0 - p):
+                opts += [W.opt(N, 100.0, K, 0.0, 0.2, 1.0, pay, W.TREE_EXPLICIT, u=u, d=1 / u, p=pp)
+                         for K in (70.0, 95.0, 105.0, 140.0) for pay in (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT)]
+    assert all(bt.bt_exact_split(o, 1)["L"] == 13 for o in opts)     # all on the per-path pass
+    got = ctx.price_exact(opts, 1)["value"]
+    ref = [oracle.exact(o) for o in opts]
+    _check(got, ref, opts, 1, "per-path pass, N=%d" % N)
+
+
 def test_paper_section5_parameters_to_the_contract(bt, ctx, oracle):
     """The Section 5 tree (Seydel, sigma = 3, S0 = 20, K = 100, N = 32: prices
     spread over ten decades) for every payoff, FP32 and FP64, against the
