@@ -14,6 +14,10 @@
  *     stream. Calls that return host results synchronise that stream first.
  *   - There is no CPU fallback: without a usable GPU, bt_create returns
  *     BT_ECUDA.
+ *   - The synchronous pricing calls of one context (exact, move-by-move,
+ *     plug-in, Greeks and Monte Carlo) share the context's reusable device
+ *     scratch and run one at a time when called from several threads; a
+ *     context per thread runs them concurrently.
  *
  * Notation (the paper's): a path x = (x_1..x_N), 1 = up (Section 1); path
  * index b in [0,2^N) holds x_t in bit N-t, so x_1 is the most significant bit,
