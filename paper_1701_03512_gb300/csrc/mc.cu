@@ -174,7 +174,7 @@ __device__ __forceinline__ void simulate_w(const bt_mc_job &J, const unsigned (&
 }
 
 #ifndef BT_MC_WALKERS
-#define BT_MC_WALKERS 4   // samples per thread at once in the Partitioned kernel (measured: 2 < 8 < 4)
+#define BT_MC_WALKERS 8   // samples per thread at once in the Partitioned kernel (measured: 2 < 4 < 8)
 #endif
 #ifndef BT_MC_WARP_THREADS
 #define BT_MC_WARP_THREADS 256   // block size of the Partitioned kernel (its warps are independent)
