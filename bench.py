@@ -345,6 +345,9 @@ def serving_bench(bt, W, ctx, n_req, loads):
 # ---------------------------------------------------------------------------
 MC_OPS_PER_STEP = 14   # Philox-4x32-10 per 4 steps: 10 rounds x (2 wide multiplies + 2 three-input xors) = 40
                        # (the key schedule is the same for every thread); + compare, select, multiply, add
+# Shared-Sample pair (prefix m, suffix i): FADD sign tau_m + sign f_i, FMNMX with 0, FFMA into the sum
+# with the folded weight P(D_m) beta_m
+SHARED_OPS_PER_PAIR = 3
 
 
 def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
@@ -385,8 +388,8 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
     shared = None
     try:
         osh = W.opt(64, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
-        msh, rsh = 10, 1 << 14
-        bt.bt_price_mc_ex(ctx.h, [osh], msh, 1024, 3, bt.BT_MC_SHARED, stream=stream)
+        msh, rsh = 10, 1 << 22
+        bt.bt_price_mc_ex(ctx.h, [osh], msh, 1 << 16, 3, bt.BT_MC_SHARED, stream=stream)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -394,12 +397,20 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
         e1.record(stream)
         e1.synchronize()
         tsh = e0.elapsed_time(e1) / 1e3
-        rpart = bt.bt_price_mc_ex(ctx.h, [osh], msh, rsh, 4, bt.BT_MC_PARTITIONED, stream=stream)[0]
-        shared = {"workload": "Shared-Sample MC, arithmetic Asian call, N=64, 2^10 prefixes x 2^14 shared suffixes",
-                  "ms": 1e3 * tsh, "suffixes_per_s": rsh / tsh, "prefix_suffix_pairs_per_s": (rsh << msh) / tsh,
+        pairs = float(rsh) * (1 << msh)
+        # Theorem 1 beside it: both estimators with R = 2^14 suffixes per prefix
+        rvs = 1 << 14
+        rshs = bt.bt_price_mc_ex(ctx.h, [osh], msh, rvs, 5, bt.BT_MC_SHARED, stream=stream)[0]
+        rpart = bt.bt_price_mc_ex(ctx.h, [osh], msh, rvs, 5, bt.BT_MC_PARTITIONED, stream=stream)[0]
+        shared = {"workload": "Shared-Sample MC, arithmetic Asian call, N=64, 2^%d prefixes x 2^%d shared suffixes"
+                              % (msh, rsh.bit_length() - 1),
+                  "ms": 1e3 * tsh, "suffixes_per_s": rsh / tsh, "prefix_suffix_pairs_per_s": pairs / tsh,
+                  "ops_per_pair": SHARED_OPS_PER_PAIR,
+                  "frac_of_issue_peak": SHARED_OPS_PER_PAIR * pairs / tsh / peak,
                   "value": float(rs["value"]), "stderr": float(rs["stderr_mc"]),
-                  "partitioned_same_R_per_stratum": {"value": float(rpart["value"]),
-                                                     "stderr": float(rpart["stderr_mc"])}}
+                  "same_R_2^14": {"shared": {"value": float(rshs["value"]), "stderr": float(rshs["stderr_mc"])},
+                                  "partitioned": {"value": float(rpart["value"]),
+                                                  "stderr": float(rpart["stderr_mc"])}}}
     except Exception as exc:  # keep the rest of the line if this extra entry fails
         shared = {"error": str(exc)}
     # the other stratifications of the MC workload: N = 64 and 252, m = 10, 12, 16

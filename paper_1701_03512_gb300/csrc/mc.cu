@@ -9,7 +9,8 @@
 // counter word 2 = 0 for every stratum, i.e. the same R suffixes under every
 // prefix. A work item is 1024 consecutive samples of one stratum: one warp
 // runs it in the Partitioned kernel (k_mc_warp), one block in the
-// Shared-Sample kernel (k_mc, whose strata states sit in shared memory).
+// Shared-Sample kernel (k_mc_shared, whose strata table, written once per job by
+// k_mc_shared_tab, sits in shared memory).
 // Per-item (count, mean, M2) go to scratch and are combined per stratum
 // (Chan et al.'s pairwise update) and then across strata in FP64 (eq. mc12
 // and its variance). A shard runs the strata m = shard + j n_shards only.
@@ -65,7 +66,7 @@ __device__ static mc_pref stratum_state(const bt_mc_job &J, uint64_t m) {
         D += lvl;
     }
     mc_pref s;
-    s.prob = pow(p, (double)k) * pow(1.0 - p, (double)(mb - k));
+    s.prob = J.prob_k[k];
     const double SP = J.S0 * exp((double)lvl * lnu);
     s.C = 0.0;
     switch (J.field) {
@@ -198,61 +199,54 @@ __device__ __forceinline__ void chan(float &n, float &mean, float &M2, float nb,
     M2 = M2 + M2b + delta * delta * (n * nb / nn);
     n = nn;
 }
-__device__ __forceinline__ void chan64(double &n, double &mean, double &M2, double nb, double meanb, double M2b) {
-    const double nn = n + nb;
-    if (nn == 0.0) return;
-    const double delta = meanb - mean;
-    mean = mean + delta * (nb / nn);
-    M2 = M2 + M2b + delta * delta * (n * nb / nn);
-    n = nn;
-}
 
-template <int FIELD, bool SHARED>
-__device__ void mc_item(const bt_mc_args &a, const bt_mc_job &J, int64_t item_local, const mc_pref *s_str,
-                        float3 *red) {
-    // item -> (stratum, first sample); shared mode has one "stratum" index 0
-    const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
-    const int64_t m = J.shard + (item_local / chunks) * J.n_shards;  // global stratum index
-    const int64_t i0 = (item_local % chunks) * BT_MC_ITEM;
-    float n = 0.0f, mean = 0.0f, M2 = 0.0f;
-    float tau = 0.0f, beta = 0.0f, C = 0.0f;
-    if (!SHARED) {
-        tau = (float)s_str[0].tau;
-        beta = (float)s_str[0].beta;
-        C = (float)s_str[0].C;
-    }
-#pragma unroll 1
-    for (int k = 0; k < BT_MC_ITEM / BT_THREADS; k += 2) {
-        const int64_t ia = i0 + threadIdx.x + (int64_t)k * BT_THREADS;
-        const int64_t ib = ia + BT_THREADS;
-        if (ia >= J.R) break;
-        const unsigned idx[2] = {(unsigned)ia, (unsigned)ib};
-        float f2[2];
-        simulate_w<FIELD, 2>(J, idx, SHARED ? 0u : (unsigned)m, f2, make_uint2(a.key_lo, a.key_hi));
+// The Shared-Sample estimator (the Remark of Section 4, eq. mc16): every suffix sample i is
+// scored under all 2^m prefixes, h_i = sum_m P(D_m) V(z_m, y_i). With
+// V = beta_m max(sign (tau_m + f_i), 0) + C_m, the C part is the per-job constant
+// s_pc = sum_m P(D_m) C_m and each (prefix, sample) pair costs an add, a clamp at 0 and a
+// multiply-add. Table entry m (shared memory) = (sign tau_m, sign tau_m, w_m, w_m) with
+// w_m = P(D_m) beta_m: the paired FP32 add and multiply-add (__fadd2_rn, __ffma2_rn) take two
+// samples in one instruction, and the clamps (FMNMX) run on the ALU pipe beside them. The sum over
+// prefixes runs in blocks of 64 (two-level summation: FP32 error under 64 + 2^m / 64 ulps).
+// A work item is BT_MC_ITEM = 4 x BT_THREADS samples: four per thread, walked together. The
+// item's (count, mean, M2) is combined over its warps in FP32 by warp 0 and stored in FP64.
+template <int FIELD>
+__device__ void mc_shared_item(const bt_mc_args &a, const bt_mc_job &J, int64_t item, const float4 *s_tab,
+                               float s_pc, float3 *red) {
+    static_assert(BT_MC_ITEM == 4 * BT_THREADS, "four samples per thread and item");
+    const int64_t i0 = item * BT_MC_ITEM + threadIdx.x;
+    unsigned idx[4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (h == 1 && ib >= J.R) break;
-            float v;
-            if (!SHARED) {
-                v = payoff_of(J, tau, beta, C, f2[h]);
-            } else {
-                // h_i = sum_m P(D_m) V(z_m, y_i): the same suffix under every prefix (eq. mc16)
-                float acc = 0.0f, accc = 0.0f;
-                for (int s = 0; s < (1 << J.mb); ++s) {
-                    const mc_pref P = s_str[s];
-                    const float term = (float)P.prob * payoff_of(J, (float)P.tau, (float)P.beta, (float)P.C, f2[h]);
-                    const float t = acc + term;  // Kahan-compensated sum over strata
-                    accc += (acc - t) + term;
-                    acc = t;
-                }
-                v = acc + accc;
-            }
-            // Welford update
-            n += 1.0f;
-            const float delta = v - mean;
-            mean += delta / n;
-            M2 += delta * (v - mean);
+    for (int w = 0; w < 4; ++w) idx[w] = (unsigned)(i0 + (int64_t)w * BT_THREADS);
+    float f[4];
+    simulate_w<FIELD, 4>(J, idx, 0u, f, make_uint2(a.key_lo, a.key_hi));
+    const float sg = J.sign > 0 ? 1.0f : -1.0f;
+    const float2 F01 = make_float2(sg * f[0], sg * f[1]), F23 = make_float2(sg * f[2], sg * f[3]);
+    float2 v01 = make_float2(0.0f, 0.0f), v23 = make_float2(0.0f, 0.0f);
+    const int M = 1 << J.mb;
+    for (int m0 = 0; m0 < M; m0 += 64) {
+        const int m1 = min(m0 + 64, M);
+        float2 a01 = make_float2(0.0f, 0.0f), a23 = make_float2(0.0f, 0.0f);
+#pragma unroll 8
+        for (int m = m0; m < m1; ++m) {
+            const float4 P = s_tab[m];
+            const float2 TT = make_float2(P.x, P.y), WW = make_float2(P.z, P.w);
+            const float2 y01 = __fadd2_rn(TT, F01), y23 = __fadd2_rn(TT, F23);
+            a01 = __ffma2_rn(WW, make_float2(fmaxf(y01.x, 0.0f), fmaxf(y01.y, 0.0f)), a01);
+            a23 = __ffma2_rn(WW, make_float2(fmaxf(y23.x, 0.0f), fmaxf(y23.y, 0.0f)), a23);
         }
+        v01 = __fadd2_rn(v01, a01);
+        v23 = __fadd2_rn(v23, a23);
+    }
+    const float v[4] = {v01.x + s_pc, v01.y + s_pc, v23.x + s_pc, v23.y + s_pc};
+    float n = 0.0f, mean = 0.0f, M2 = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        if (i0 + (int64_t)w * BT_THREADS >= J.R) break;
+        n += 1.0f;  // Welford update
+        const float delta = v[w] - mean;
+        mean += delta / n;
+        M2 += delta * (v[w] - mean);
     }
     // warp, then block combination (fixed shape)
     for (int o = 16; o > 0; o >>= 1) {
@@ -263,71 +257,106 @@ __device__ void mc_item(const bt_mc_args &a, const bt_mc_job &J, int64_t item_lo
     }
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float3(n, mean, M2);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double N_ = 0.0, MU = 0.0, Q = 0.0;
-        for (int w = 0; w < BT_THREADS / 32; ++w) chan64(N_, MU, Q, red[w].x, red[w].y, red[w].z);
-        a.item_stats[J.item_begin + item_local] = make_double4(N_, MU, Q, (double)m);
+    if (threadIdx.x < 32) {
+        static_assert(BT_THREADS / 32 <= 32, "one warp combines the block's warps");
+        const float3 r = threadIdx.x < BT_THREADS / 32 ? red[threadIdx.x] : make_float3(0.0f, 0.0f, 0.0f);
+        n = r.x, mean = r.y, M2 = r.z;
+        for (int o = BT_THREADS / 64; o > 0; o >>= 1) {
+            const float nb = __shfl_down_sync(0xffffffffu, n, o);
+            const float mb_ = __shfl_down_sync(0xffffffffu, mean, o);
+            const float M2b = __shfl_down_sync(0xffffffffu, M2, o);
+            chan(n, mean, M2, nb, mb_, M2b);
+        }
+        if (threadIdx.x == 0) a.item_stats[J.item_begin + item] = make_double4(n, mean, M2, 0.0);
     }
 }
 
-__global__ void __launch_bounds__(BT_THREADS, 2) k_mc(bt_mc_args a) {
-    __shared__ mc_pref s_str[1 << BT_MC_SHARED_MAX_BITS];
-    __shared__ float3 red[BT_THREADS / 32];
-    __shared__ int s_job;
-    __shared__ int64_t s_item;
+// Shared-Sample strata table of every job (one thread per stratum, BT_MC_TAB_BLOCKS blocks per
+// job): entry m = (sign tau_m, sign tau_m, P(D_m) beta_m, P(D_m) beta_m) in FP32, and each
+// block's FP64 partial sum of P(D_m) C_m. The FP64 strata states are computed once per job here,
+// not once per block of the sampling kernel.
+__global__ void __launch_bounds__(BT_MC_TAB_THREADS) k_mc_shared_tab(bt_mc_args a) {
+    __shared__ double s_w[BT_MC_TAB_THREADS / 32];
+    const int job = blockIdx.x / BT_MC_TAB_BLOCKS, blk = blockIdx.x % BT_MC_TAB_BLOCKS;
+    const bt_mc_job &J = a.jobs[job];
+    const int m = blk * BT_MC_TAB_THREADS + threadIdx.x;
+    double pc = 0.0;
+    if (m < (1 << J.mb)) {
+        const mc_pref P = stratum_state(J, (uint64_t)m);
+        const float t = (float)(J.sign > 0 ? P.tau : -P.tau), w = (float)(P.prob * P.beta);
+        a.shared_tab[(size_t)job * BT_MC_TAB_ENTRIES + m] = make_float4(t, t, w, w);
+        pc = P.prob * P.C;
+    }
+    for (int o = 16; o > 0; o >>= 1) pc += __shfl_down_sync(0xffffffffu, pc, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = pc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < BT_MC_TAB_THREADS / 32; ++w) t += s_w[w];
+        a.shared_pc[(size_t)job * BT_MC_TAB_BLOCKS + blk] = t;
+    }
+}
+
+// Claims the next work item for the block: (item, job), item -1 once all are taken.
+__device__ __forceinline__ void mc_claim(const bt_mc_args &a, int64_t *item, int *job) {
+    const unsigned long long i = atomicAdd(a.counter, 1ull);
+    if (i >= (unsigned long long)a.n_items) {
+        *item = -1;
+        return;
+    }
+    int lo = 0, hi = a.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.jobs[mid].item_begin <= (int64_t)i) lo = mid;
+        else hi = mid - 1;
+    }
+    *item = (int64_t)i;
+    *job = lo;
+}
+
+// Shared-Sample sampling kernel: blocks take work items (BT_MC_ITEM samples of one job) from a
+// global counter; a block loads a job's strata table into shared memory when it moves to that job.
+// Thread 0 claims item k + 1 while the block runs item k; the claim and the warp statistics are
+// double-buffered by the parity of k, so an item costs one block barrier (inside the item):
+// slot k & 1 is read before that barrier of item k and written again only after it, in item k + 1.
+__global__ void __launch_bounds__(BT_THREADS, 2) k_mc_shared(bt_mc_args a) {
+    __shared__ float4 s_tab[BT_MC_TAB_ENTRIES];
+    __shared__ float s_pc;
+    __shared__ float3 red[2][BT_THREADS / 32];
+    __shared__ int64_t s_item[2];
+    __shared__ int s_job[2];
     __shared__ bt_mc_job sJ;
+    if (threadIdx.x == 0) mc_claim(a, &s_item[0], &s_job[0]);
+    __syncthreads();
     int cur_job = -1;
-    int64_t cur_stratum = -1;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const unsigned long long i = atomicAdd(a.counter, 1ull);
-            s_item = i < (unsigned long long)a.n_items ? (int64_t)i : -1;
-            if (s_item >= 0) {
-                int lo = 0, hi = a.n_jobs - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (a.jobs[mid].item_begin <= s_item) lo = mid;
-                    else hi = mid - 1;
-                }
-                s_job = lo;
+    for (int k = 0;; ++k) {
+        const int64_t it = s_item[k & 1];
+        const int jb = s_job[k & 1];
+        if (it < 0) break;
+        if (threadIdx.x == 0) mc_claim(a, &s_item[(k + 1) & 1], &s_job[(k + 1) & 1]);
+        if (jb != cur_job) {
+            // every thread is past the barrier of item k - 1: the old table is no longer read
+            if (threadIdx.x == 0) {
+                sJ = a.jobs[jb];
+                double t = 0.0;
+                for (int b = 0; b < BT_MC_TAB_BLOCKS; ++b) t += a.shared_pc[(size_t)jb * BT_MC_TAB_BLOCKS + b];
+                s_pc = (float)t;
             }
-        }
-        __syncthreads();
-        if (s_item < 0) break;
-        if (s_job != cur_job) {
-            if (threadIdx.x == 0) sJ = a.jobs[s_job];
+            const int M = 1 << a.jobs[jb].mb;
+            const float4 *tab = a.shared_tab + (size_t)jb * BT_MC_TAB_ENTRIES;
+            for (int m = threadIdx.x; m < M; m += BT_THREADS) s_tab[m] = tab[m];
             __syncthreads();
+            cur_job = jb;
         }
         const bt_mc_job &J = sJ;
-        const int64_t item_local = s_item - J.item_begin;
-        if (J.shared) {
-            if (s_job != cur_job) {
-                for (int s = threadIdx.x; s < (1 << J.mb); s += BT_THREADS) s_str[s] = stratum_state(J, (uint64_t)s);
-                __syncthreads();
-            }
-        } else {
-            const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
-            const int64_t m = J.shard + (item_local / chunks) * J.n_shards;
-            if (s_job != cur_job || m != cur_stratum) {
-                __syncthreads();
-                if (threadIdx.x == 0) s_str[0] = stratum_state(J, (uint64_t)m);
-                __syncthreads();
-                cur_stratum = m;
-            }
-        }
-        cur_job = s_job;
-        switch (J.field * 2 + (J.shared ? 1 : 0)) {
-        case BT_F_ARITH * 2: mc_item<BT_F_ARITH, false>(a, J, item_local, s_str, red); break;
-        case BT_F_ARITH * 2 + 1: mc_item<BT_F_ARITH, true>(a, J, item_local, s_str, red); break;
-        case BT_F_GEO * 2: mc_item<BT_F_GEO, false>(a, J, item_local, s_str, red); break;
-        case BT_F_GEO * 2 + 1: mc_item<BT_F_GEO, true>(a, J, item_local, s_str, red); break;
-        case BT_F_EURO * 2: mc_item<BT_F_EURO, false>(a, J, item_local, s_str, red); break;
-        case BT_F_EURO * 2 + 1: mc_item<BT_F_EURO, true>(a, J, item_local, s_str, red); break;
-        case BT_F_LOOKMAX * 2: mc_item<BT_F_LOOKMAX, false>(a, J, item_local, s_str, red); break;
-        case BT_F_LOOKMAX * 2 + 1: mc_item<BT_F_LOOKMAX, true>(a, J, item_local, s_str, red); break;
-        case BT_F_LOOKMIN * 2: mc_item<BT_F_LOOKMIN, false>(a, J, item_local, s_str, red); break;
-        default: mc_item<BT_F_LOOKMIN, true>(a, J, item_local, s_str, red); break;
+        const int64_t item = it - J.item_begin;
+        float3 *rk = red[k & 1];
+        switch (J.field) {
+        case BT_F_ARITH: mc_shared_item<BT_F_ARITH>(a, J, item, s_tab, s_pc, rk); break;
+        case BT_F_GEO: mc_shared_item<BT_F_GEO>(a, J, item, s_tab, s_pc, rk); break;
+        case BT_F_EURO: mc_shared_item<BT_F_EURO>(a, J, item, s_tab, s_pc, rk); break;
+        case BT_F_LOOKMAX: mc_shared_item<BT_F_LOOKMAX>(a, J, item, s_tab, s_pc, rk); break;
+        default: mc_shared_item<BT_F_LOOKMIN>(a, J, item, s_tab, s_pc, rk); break;
         }
     }
 }
@@ -425,13 +454,41 @@ __global__ void __launch_bounds__(BT_MC_WARP_THREADS, BT_MC_MIN_BLOCKS) k_mc_war
     }
 }
 
-// Combination, first half: one warp per stratum combines the stratum's work items
-// (Chan et al.'s update, fixed lane order and a fixed shuffle tree).
+// Combination, first half: per stratum, its work items in two passes without a division per item
+// (FP64 division is slow on this part): N = sum n_i and S = sum n_i mean_i give mean = S / N, then
+// M2 = sum M2_i + n_i (mean_i - mean)^2, the exact decomposition of the sum of squares about the
+// stratum mean. One thread per stratum for up to 32 work items, one warp for up to
+// BT_MC_STRATA_BLOCK, one block above (the choice depends only on R, so a stratum's result does not
+// depend on the other strata of the call). Fixed lane order, fixed reduction trees. Writes per stratum
+// (mean, P(D_m), P(D_m)^2 s_m^2 / n_m, P(D_m) M2_m / n_m) with s_m^2 = M2_m / (n_m - 1), the
+// terms of eq. mc12, its variance and eq. mc14, and the per-stratum statistics when asked.
+__device__ __forceinline__ double warp_sum64(double x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+enum { MC_BY_THREAD, MC_BY_WARP, MC_BY_BLOCK };
+template <int BY>
+__device__ __forceinline__ double group_sum64(double x, double *sh) {
+    if (BY == MC_BY_THREAD) return x;
+    x = warp_sum64(x);
+    if (BY == MC_BY_WARP) return x;
+    __syncthreads();  // sh is free (its last readers are past this barrier)
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < BT_THREADS / 32; ++w) t += sh[w];
+    return t;
+}
+template <int BY>
 __global__ void k_mc_strata(const bt_mc_job *jobs, int n_jobs, const double4 *item_stats, int64_t n_strata,
-                            double4 *strata_nmq /* per stratum (n, mean, M2, prob) */) {
-    const int64_t g = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (g >= n_strata) return;
+                            double4 *strata_nmq, double *strata /* [n_strata][3] or null */) {
+    __shared__ double sh[BT_THREADS / 32];
+    const int64_t g = BY == MC_BY_BLOCK  ? (int64_t)blockIdx.x
+                      : BY == MC_BY_WARP ? (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)
+                                         : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = BY == MC_BY_BLOCK ? threadIdx.x : BY == MC_BY_WARP ? (threadIdx.x & 31) : 0;
+    const int width = BY == MC_BY_BLOCK ? BT_THREADS : BY == MC_BY_WARP ? 32 : 1;
+    if (g >= n_strata) return;  // uniform over the group that combines one stratum
     int lo = 0, hi = n_jobs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -442,79 +499,99 @@ __global__ void k_mc_strata(const bt_mc_job *jobs, int n_jobs, const double4 *it
     const int64_t m = g - J.strata_off;                // stratum of this run
     const int64_t mg = J.shard + m * J.n_shards;       // its global index
     const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
-    double n = 0.0, mu = 0.0, Q = 0.0;
-    for (int64_t c = lane; c < chunks; c += 32) {
-        const double4 s = item_stats[J.item_begin + m * chunks + c];
-        chan64(n, mu, Q, s.x, s.y, s.z);
+    const double4 *it = item_stats + J.item_begin + m * chunks;
+    double n = 0.0, S = 0.0;
+#pragma unroll 4
+    for (int64_t c = lane; c < chunks; c += width) {
+        const double4 s = it[c];
+        n += s.x;
+        S = fma(s.x, s.y, S);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        const double nb = __shfl_down_sync(0xffffffffu, n, o);
-        const double mb_ = __shfl_down_sync(0xffffffffu, mu, o);
-        const double Qb = __shfl_down_sync(0xffffffffu, Q, o);
-        chan64(n, mu, Q, nb, mb_, Qb);
+    n = group_sum64<BY>(n, sh);
+    S = group_sum64<BY>(S, sh);
+    const double mu = n > 0.0 ? S / n : 0.0;
+    double Q = 0.0;
+#pragma unroll 4
+    for (int64_t c = lane; c < chunks; c += width) {
+        const double4 s = it[c];
+        const double d = s.y - mu;
+        Q += s.z;
+        Q = fma(s.x * d, d, Q);
     }
-    if (lane == 0) strata_nmq[g] = make_double4(n, mu, Q, J.shared ? 1.0 : stratum_state(J, (uint64_t)mg).prob);
+    Q = group_sum64<BY>(Q, sh);
+    if (lane == 0) {
+        const double prob = J.shared ? 1.0 : J.prob_k[__popcll((unsigned long long)mg)];
+        const double s2 = n > 1.0 ? Q / (n - 1.0) : 0.0;
+        strata_nmq[g] = make_double4(mu, prob, n > 0.0 ? prob * prob * s2 / n : 0.0, n > 0.0 ? prob * Q / n : 0.0);
+        if (strata) {
+            strata[3 * g] = mu;
+            strata[3 * g + 1] = s2;
+            strata[3 * g + 2] = prob;
+        }
+    }
 }
 
-// Combination, second half: across strata, eq. mc12 and Var = sum_m P(D_m)^2 s_m^2 / R_m
-// (unbiased s_m^2); also the variance of one draw by the law of total variance
-// (eq. mc14), for plain-MC comparisons. One block per option.
-__global__ void k_mc_finalize(const bt_mc_job *jobs, int n_jobs, const double4 *strata_nmq, bt_result *out,
-                              double *strata /* [sum over jobs of 2^mb][3] or null */) {
-    const int j = blockIdx.x;
+// Combination, second half: across strata, eq. mc12 (theta = sum_m P(D_m) mean_m, Neumaier-
+// compensated), Var = sum_m P(D_m)^2 s_m^2 / n_m, and the variance of one plain draw by the law
+// of total variance (eq. mc14): sum_m P(D_m) M2_m / n_m + sum_m P(D_m) (mean_m - theta)^2. The
+// last sum is taken about c = mean_0 in one pass, from A = sum P (mean - c)^2, B = sum P (mean - c)
+// and P = sum P(D_m): sum P (mean - theta)^2 = A - 2 (theta - c) B + (theta - c)^2 P.
+// BT_MC_FIN_BLOCKS blocks per job each take a fixed contiguous range of its strata; one warp per
+// job then adds the blocks' partial sums in block order.
+__global__ void k_mc_fin_part(const bt_mc_job *jobs, int n_jobs, const double4 *strata_nmq, double *partials) {
+    const int j = blockIdx.x / BT_MC_FIN_BLOCKS, b = blockIdx.x % BT_MC_FIN_BLOCKS;
     if (j >= n_jobs) return;
-    const bt_mc_job J = jobs[j];
-    __shared__ double sh[3][BT_THREADS];
-    const int64_t M = J.M;
-    double th = 0.0, thc = 0.0, var = 0.0, ew = 0.0;
-    for (int64_t m = threadIdx.x; m < M; m += BT_THREADS) {
+    const bt_mc_job &J = jobs[j];
+    const int64_t M = J.M, m0 = M * b / BT_MC_FIN_BLOCKS, m1 = M * (b + 1) / BT_MC_FIN_BLOCKS;
+    const double c = strata_nmq[J.strata_off].x;
+    double th = 0.0, thc = 0.0, var = 0.0, ew = 0.0, A = 0.0, B = 0.0, P = 0.0;
+    for (int64_t m = m0 + threadIdx.x; m < m1; m += BT_THREADS) {
         const double4 s = strata_nmq[J.strata_off + m];
-        const double n = s.x, mu = s.y, Q = s.z, prob = s.w;
-        const double s2 = n > 1.0 ? Q / (n - 1.0) : 0.0;
+        const double mu = s.x, prob = s.y;
         const double x = prob * mu;
         const double t = th + x;
         thc += fabs(th) >= fabs(x) ? (th - t) + x : (x - t) + th;
         th = t;
-        var += prob * prob * s2 / n;
-        ew += prob * (n > 0.0 ? Q / n : 0.0);  // sum_m P_m Var[V|D_m] (population form)
-        if (strata) {
-            double *o = strata + 3 * (J.strata_off + m);
-            o[0] = mu;
-            o[1] = s2;
-            o[2] = prob;
-        }
+        var += s.z;
+        ew += s.w;
+        const double d = mu - c;
+        A = fma(prob * d, d, A);
+        B = fma(prob, d, B);
+        P += prob;
     }
-    sh[0][threadIdx.x] = th + thc;
-    sh[1][threadIdx.x] = var;
-    sh[2][threadIdx.x] = ew;
+    __shared__ double sh[6][BT_THREADS];
+    const double v[6] = {th + thc, var, ew, A, B, P};
+    for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] = v[q];
     __syncthreads();
     for (int w = BT_THREADS / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w)
-            for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+            for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
         __syncthreads();
     }
-    const double theta = sh[0][0], var_tot = sh[1][0], ew_tot = sh[2][0];
-    __syncthreads();
-    // Var_D E[V|D] = sum_m P_m (mu_m - theta)^2
-    double vb = 0.0;
-    for (int64_t m = threadIdx.x; m < M; m += BT_THREADS) {
-        const double4 s = strata_nmq[J.strata_off + m];
-        vb += s.w * (s.y - theta) * (s.y - theta);
+    if (threadIdx.x < 6) partials[((size_t)j * BT_MC_FIN_BLOCKS + b) * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_mc_finalize(const bt_mc_job *jobs, int n_jobs, const double4 *strata_nmq, const double *partials,
+                              bt_result *out) {
+    static_assert(BT_MC_FIN_BLOCKS <= 32, "one lane per partial");
+    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= n_jobs) return;
+    const bt_mc_job &J = jobs[j];
+    double v[6];
+    for (int q = 0; q < 6; ++q) {
+        const double x = lane < BT_MC_FIN_BLOCKS ? partials[((size_t)j * BT_MC_FIN_BLOCKS + lane) * 8 + q] : 0.0;
+        v[q] = warp_sum64(x);
     }
-    sh[0][threadIdx.x] = vb;
-    __syncthreads();
-    for (int w = BT_THREADS / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
+        const double theta = v[0], c = strata_nmq[J.strata_off].x, e = theta - c;
+        const double vb = v[3] - 2.0 * e * v[4] + e * e * v[5];
         bt_result r;
         r.value = J.disc * theta;
-        r.stderr_mc = J.disc * sqrt(var_tot);
+        r.stderr_mc = J.disc * sqrt(v[1]);
         // eq. mc14 needs the mean over all strata: only a run over all of them has it
-        r.var_plain = J.shared || J.n_shards > 1 ? 0.0 : ew_tot + sh[0][0];
+        r.var_plain = J.shared || J.n_shards > 1 ? 0.0 : v[2] + fmax(vb, 0.0);
         r.err_est = 0.0;
-        r.paths = (int64_t)M * J.R;
+        r.paths = (int64_t)J.M * J.R;
         out[J.out] = r;
     }
 }
@@ -522,8 +599,9 @@ __global__ void k_mc_finalize(const bt_mc_job *jobs, int n_jobs, const double4 *
 extern "C" int bt_launch_mc(const bt_mc_args *a, int shared, int grid, void *stream) {
     if (a->n_items <= 0) return 0;
     if (shared) {
+        k_mc_shared_tab<<<(unsigned)a->n_jobs * BT_MC_TAB_BLOCKS, BT_MC_TAB_THREADS, 0, (cudaStream_t)stream>>>(*a);
         if ((int64_t)grid > a->n_items) grid = (int)a->n_items;
-        k_mc<<<grid, BT_THREADS, 0, (cudaStream_t)stream>>>(*a);
+        k_mc_shared<<<grid, BT_THREADS, 0, (cudaStream_t)stream>>>(*a);
     } else {
         const int64_t warps = (int64_t)grid * (BT_MC_WARP_THREADS / 32);
         if (warps > a->n_items)
@@ -533,14 +611,23 @@ extern "C" int bt_launch_mc(const bt_mc_args *a, int shared, int grid, void *str
     return (int)cudaGetLastError();
 }
 
-extern "C" int bt_launch_mc_finalize(const bt_mc_job *jobs, int n_jobs, const double4 *item_stats,
-                                     int64_t n_strata, double4 *strata_nmq, bt_result *out, double *strata,
-                                     void *stream) {
+extern "C" int bt_launch_mc_finalize(const bt_mc_job *jobs, int n_jobs, int64_t chunks, const double4 *item_stats,
+                                     int64_t n_strata, double4 *strata_nmq, double *partials, bt_result *out,
+                                     double *strata, void *stream) {
     if (n_jobs <= 0) return 0;
+    cudaStream_t st = (cudaStream_t)stream;
     const int wpb = BT_THREADS / 32;
-    k_mc_strata<<<(unsigned)((n_strata + wpb - 1) / wpb), BT_THREADS, 0, (cudaStream_t)stream>>>(
-        jobs, n_jobs, item_stats, n_strata, strata_nmq);
-    k_mc_finalize<<<n_jobs, BT_THREADS, 0, (cudaStream_t)stream>>>(jobs, n_jobs, strata_nmq, out, strata);
+    if (chunks > BT_MC_STRATA_BLOCK)
+        k_mc_strata<MC_BY_BLOCK><<<(unsigned)n_strata, BT_THREADS, 0, st>>>(jobs, n_jobs, item_stats, n_strata,
+                                                                          strata_nmq, strata);
+    else if (chunks > 32)
+        k_mc_strata<MC_BY_WARP><<<(unsigned)((n_strata + wpb - 1) / wpb), BT_THREADS, 0, st>>>(
+            jobs, n_jobs, item_stats, n_strata, strata_nmq, strata);
+    else
+        k_mc_strata<MC_BY_THREAD><<<(unsigned)((n_strata + BT_THREADS - 1) / BT_THREADS), BT_THREADS, 0, st>>>(
+            jobs, n_jobs, item_stats, n_strata, strata_nmq, strata);
+    k_mc_fin_part<<<(unsigned)n_jobs * BT_MC_FIN_BLOCKS, BT_THREADS, 0, st>>>(jobs, n_jobs, strata_nmq, partials);
+    k_mc_finalize<<<(unsigned)((n_jobs + wpb - 1) / wpb), BT_THREADS, 0, st>>>(jobs, n_jobs, strata_nmq, partials, out);
     return (int)cudaGetLastError();
 }
 
@@ -552,7 +639,7 @@ extern "C" int bt_launch_philox_selftest(const uint4 *ctr, const uint2 *key, uin
 extern "C" int bt_mc_grid_size(int device, int shared) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    if (shared) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc, BT_THREADS, 0);
+    if (shared) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_shared, BT_THREADS, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_warp, BT_MC_WARP_THREADS, 0);
     if (per < 1) per = 1;
     return sms * per;

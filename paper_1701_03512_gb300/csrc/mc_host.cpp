@@ -71,6 +71,7 @@ static bt_status mc_run(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t s
         J.uf = (float)J.u;
         J.df = (float)J.d;
         J.lnu_f = (float)std::log(J.u);
+        for (int k = 0; k <= J.mb; ++k) J.prob_k[k] = std::pow(J.p, (double)k) * std::pow(1.0 - J.p, (double)(J.mb - k));
         const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
         J.shard = shard;
         J.n_shards = n_shards;
@@ -89,7 +90,11 @@ static bt_status mc_run(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t s
     const size_t o_out = off; off = up256(off + sizeof(bt_result) * n);
     const size_t o_str = off; off = up256(off + (strata_stats ? sizeof(double) * 3 * strata_total : 0));
     const size_t o_nmq = off; off = up256(off + sizeof(double4) * strata_total);
+    const size_t o_part = off; off = up256(off + sizeof(double) * 8 * BT_MC_FIN_BLOCKS * n);
     const size_t o_cnt = off; off = up256(off + sizeof(unsigned long long));
+    const bool sh = kind == BT_MC_SHARED;
+    const size_t o_tab = off; off = up256(off + (sh ? sizeof(float4) * BT_MC_TAB_ENTRIES * n : 0));
+    const size_t o_pc = off; off = up256(off + (sh ? sizeof(double) * BT_MC_TAB_BLOCKS * n : 0));
     cudaSetDevice(ctx->device);
     // the context's reusable scratch (no allocation per call once it is large enough)
     std::lock_guard<std::mutex> lock(ctx->cache_mu);
@@ -102,6 +107,7 @@ static bt_status mc_run(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t s
     bt_result *d_out = (bt_result *)(b + o_out);
     double *d_str = strata_stats ? (double *)(b + o_str) : nullptr;
     double4 *d_nmq = (double4 *)(b + o_nmq);
+    double *d_part = (double *)(b + o_part);
     unsigned long long *d_cnt = (unsigned long long *)(b + o_cnt);
     cudaStream_t st = ctx_stream(ctx, stream);
     bt_status rs = BT_OK;
@@ -118,11 +124,14 @@ static bt_status mc_run(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t s
         a.counter = d_cnt;
         a.key_lo = (uint32_t)(seed & 0xffffffffu);
         a.key_hi = (uint32_t)(seed >> 32);
+        a.shared_tab = sh ? (float4 *)(b + o_tab) : nullptr;
+        a.shared_pc = sh ? (double *)(b + o_pc) : nullptr;
         int le = bt_launch_mc(&a, kind == BT_MC_SHARED, bt_mc_grid_size(ctx->device, kind == BT_MC_SHARED), st);
         if (le) rs = bt_cuda_fail(le, "MC kernel");
     }
     if (rs == BT_OK) {
-        int le = bt_launch_mc_finalize(d_jobs, n, d_stats, strata_total, d_nmq, d_out, d_str, st);
+        const int64_t chunks = (samples_per_stratum + BT_MC_ITEM - 1) / BT_MC_ITEM;
+        int le = bt_launch_mc_finalize(d_jobs, n, chunks, d_stats, strata_total, d_nmq, d_part, d_out, d_str, st);
         if (le) rs = bt_cuda_fail(le, "MC finalize kernel");
     }
     if (rs == BT_OK) {

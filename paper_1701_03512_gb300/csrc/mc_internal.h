@@ -6,8 +6,13 @@
 
 #define BT_MC_ITEM 1024            // samples per work item (256 threads x 4)
 #define BT_MC_SHARED_MAX_BITS 10   // Shared-Sample strata live in shared memory
+#define BT_MC_TAB_ENTRIES (1 << BT_MC_SHARED_MAX_BITS)         // one table entry per stratum
+#define BT_MC_TAB_THREADS 64                                    // threads per block of the table kernel
+#define BT_MC_TAB_BLOCKS (BT_MC_TAB_ENTRIES / BT_MC_TAB_THREADS)
 #define BT_MC_MAX_N 4096
 #define BT_MC_MAX_BITS 24
+#define BT_MC_FIN_BLOCKS 32        // blocks per job of the across-strata combination
+#define BT_MC_STRATA_BLOCK 256     // work items per stratum above which a block (not a warp) combines them
 
 struct bt_mc_job {
     int32_t N, mb;                 // tree depth, strata bits (prefix length)
@@ -24,6 +29,7 @@ struct bt_mc_job {
     int32_t shard, n_shards;       // this run covers strata m = shard + j * n_shards
     int64_t M;                     // strata in this run (1 for Shared-Sample)
     int64_t item_begin, n_items, strata_off;
+    double prob_k[BT_MC_MAX_BITS + 1];  // P(D_m) of a stratum with k up moves: p^k (1 - p)^(mb - k)
 };
 
 struct bt_mc_args {
@@ -35,14 +41,20 @@ struct bt_mc_args {
     int64_t n_items;
     double4 *item_stats;           // per item: (count, mean, M2, stratum)
     unsigned long long *counter;
+    // Shared-Sample only: per job, the strata table the payoff loop reads (per stratum m,
+    // (sign tau_m, sign tau_m, P(D_m) beta_m / 2, P(D_m) beta_m)) and BT_MC_TAB_BLOCKS partial sums
+    // of P(D_m) C_m in FP64
+    float4 *shared_tab;            // [n_jobs][BT_MC_TAB_ENTRIES]
+    double *shared_pc;             // [n_jobs][BT_MC_TAB_BLOCKS]
 };
 
 #ifdef __cplusplus
 extern "C" {
 #endif
 int bt_launch_mc(const bt_mc_args *a, int shared, int grid, void *stream);
-int bt_launch_mc_finalize(const bt_mc_job *jobs, int n_jobs, const double4 *item_stats, int64_t n_strata,
-                          double4 *strata_nmq, bt_result *out, double *strata, void *stream);
+int bt_launch_mc_finalize(const bt_mc_job *jobs, int n_jobs, int64_t chunks, const double4 *item_stats,
+                          int64_t n_strata, double4 *strata_nmq, double *partials, bt_result *out, double *strata,
+                          void *stream);
 int bt_launch_philox_selftest(const uint4 *ctr, const uint2 *key, uint4 *out, int n, void *stream);
 int bt_mc_grid_size(int device, int shared);
 #ifdef __cplusplus

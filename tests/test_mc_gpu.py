@@ -43,7 +43,10 @@ def test_device_philox_matches_oracle(bt, ctx, oracle):
 
 
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("mb,R", [(0, 700), (1, 300), (2, 200), (3, 100), (4, 1500)])   # suffix tails 0, 3, 2, 1, 0
+# suffix tails 0, 3, 2, 1, 0; the last two have 41 and 301 work items of 1024 samples per stratum, so
+# a warp and a block combine each stratum's items (one thread does for the others)
+@pytest.mark.parametrize("mb,R", [(0, 700), (1, 300), (2, 200), (3, 100), (4, 1500), (2, 40 * 1024 + 17),
+                                  (1, 300 * 1024 + 3)])
 def test_same_draws_as_oracle(bt, ctx, oracle, kind, mb, R):
     opts = [W.opt(12, 100.0, 101.0, 0.04, 0.3, 1.0, pay, W.TREE_SEYDEL if pay % 3 == 0 else W.TREE_CRR)
             for pay in range(8)]
