@@ -53,7 +53,7 @@ struct mc_pref {
 
 __device__ static mc_pref stratum_state(const bt_mc_job &J, uint64_t m) {
     const int mb = J.mb, N = J.N, L = N - mb;
-    const double u = J.u, d = J.d, lnu = log(u), p = J.p;
+    const double u = J.u, d = J.d, lnu = log(u);
     int lvl = 0, mx = -BT_LVL_NONE, mn = BT_LVL_NONE, D = 0, k = 0;
     double R = 0.0;  // Sigma_P / S_P as sum_t u^{l_t - l_P}
     for (int t = 1; t <= mb; ++t) {
@@ -119,11 +119,30 @@ struct walker {
             rel *= up ? uf : df;
             f += rel;
         } else {
-            lvl += up ? 1 : -1;
-            if (FIELD == BT_F_GEO) D += lvl;
-            if (FIELD == BT_F_LOOKMAX) ext = lvl > ext ? lvl : ext;
-            if (FIELD == BT_F_LOOKMIN) ext = lvl < ext ? lvl : ext;
+            step_level(up);
         }
+    }
+    // The arithmetic step from the Philox word itself: up iff word < thr. The factor is applied by
+    // two predicated multiplies (FMA pipe) instead of a select (ALU pipe, the busier one here) and
+    // one multiply; the same IEEE product either way (BT_MC_SELECT_MUL builds the select form).
+    __device__ __forceinline__ void step_word(unsigned word, unsigned thr, float uf, float df) {
+#ifndef BT_MC_SELECT_MUL
+        if (FIELD == BT_F_ARITH) {
+            asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p mul.rn.f32 %0, %0, %3;\n\t"
+                "@!p mul.rn.f32 %0, %0, %4;\n\t}"
+                : "+f"(rel)
+                : "r"(word), "r"(thr), "f"(uf), "f"(df));
+            f += rel;
+            return;
+        }
+#endif
+        step(word < thr, uf, df);
+    }
+    __device__ __forceinline__ void step_level(bool up) {
+        lvl += up ? 1 : -1;
+        if (FIELD == BT_F_GEO) D += lvl;
+        if (FIELD == BT_F_LOOKMAX) ext = lvl > ext ? lvl : ext;
+        if (FIELD == BT_F_LOOKMIN) ext = lvl < ext ? lvl : ext;
     }
     // The per-suffix number f (see exact.cu): arithmetic sum_j u^{l'_j},
     // geometric u^{sum_j l'_j / N}, European u^{l'_L}, lookback u^{max/min l'_j};
@@ -154,10 +173,10 @@ __device__ __forceinline__ void simulate_w(const bt_mc_job &J, const unsigned (&
         for (int w = 0; w < W; ++w) r[w] = philox4x32_10(make_uint4((unsigned)(j0 >> 2), idx[w], c2, J.stream), key);
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            A[w].step(r[w].x < J.thr, J.uf, J.df);
-            A[w].step(r[w].y < J.thr, J.uf, J.df);
-            A[w].step(r[w].z < J.thr, J.uf, J.df);
-            A[w].step(r[w].w < J.thr, J.uf, J.df);
+            A[w].step_word(r[w].x, J.thr, J.uf, J.df);
+            A[w].step_word(r[w].y, J.thr, J.uf, J.df);
+            A[w].step_word(r[w].z, J.thr, J.uf, J.df);
+            A[w].step_word(r[w].w, J.thr, J.uf, J.df);
         }
     }
     if (j0 < L) {  // the last one to three steps: words 0..L-j0-1 of the final block
