@@ -156,9 +156,8 @@ def options_array(opts) -> np.ndarray:
     if isinstance(opts, dict):
         opts = [opts]
     a = np.zeros(len(opts), dtype=OPTION_DTYPE)
-    for i, o in enumerate(opts):
-        for k in ("N", "tree_kind", "payoff", "S0", "K", "rate", "sigma", "T", "u", "d", "p"):
-            a[i][k] = o.get(k, 0)
+    for k in ("N", "tree_kind", "payoff", "S0", "K", "rate", "sigma", "T", "u", "d", "p"):
+        a[k] = [o.get(k, 0) for o in opts]   # one column at a time (per-element writes cost ~10 us each)
     return a
 
 
