@@ -83,20 +83,25 @@ def main():
         os._exit(3)   # leaves between steps, nothing in flight
     res = {}
     try:
+        # a failing rank does its share of the work first and then returns NaN, so that it reaches
+        # the exchange no earlier than its peers (a peer still computing past the exchange's
+        # time limit would be reported missing instead)
         if mode == "bench":
             import bench
-            part = oracle_exact_part(rank, world) if fail != "nan" else np.full(len(EXACT_OPTS), np.nan)
+            part = oracle_exact_part(rank, world)
+            if fail == "nan":
+                part = np.full_like(part, np.nan)
             res["value"] = bench.split_combine(ex, part).tolist()
         elif mode == "exact":
             local = oracle_exact_part if provider == "oracle" else None
             if fail == "nan":
-                local = lambda r, w: np.full(len(EXACT_OPTS), np.nan)  # noqa: E731
+                local = lambda r, w: np.full_like(oracle_exact_part(r, w), np.nan)  # noqa: E731
             v = S.price_exact_sharded(ex, EXACT_OPTS, 1, ctx.h if ctx else None, local)
             res["value"] = v.tolist()
         else:
             local = oracle_mc_part if provider == "oracle" else None
             if fail == "nan":
-                local = lambda r, w: np.full((1, 3), np.nan)  # noqa: E731
+                local = lambda r, w: np.full_like(oracle_mc_part(r, w), np.nan)  # noqa: E731
             v, se, n = S.price_mc_sharded(ex, [MC_OPT], MC_BITS, MC_R, MC_SEED, ctx.h if ctx else None, local)
             res.update(value=v.tolist(), stderr=se.tolist(), samples=n.tolist())
     except S.ShardError as e:
