@@ -167,6 +167,22 @@ def test_strata_shards_add_up(bt, ctx, n_shards):
     assert paths == full[0]["paths"]
 
 
+@pytest.mark.parametrize("pay,R", [(W.ASIAN_ARITH_CALL, 4096 + 333), (W.ASIAN_GEO_PUT, 2048 + 5)])
+def test_shared_sample_at_the_benchmark_strata(bt, ctx, oracle, pay, R):
+    """The Shared-Sample kernel at the benchmark's N=64 and 2^10 prefixes (the whole per-job strata
+    table, 16 blocks of 64 prefixes in the pair loop), with a ragged last work item, against the
+    oracle's estimator on the same Philox draws. Tolerances: the FP32 suffix walk (under 1e-6
+    relative at N=64) and the blocked FP32 sum over 1024 prefixes (under 80 ulps)."""
+    o = W.opt(64, 100.0, 100.0, 0.05, 0.2, 1.0, pay)
+    seed = 11
+    got = bt.bt_price_mc_ex(ctx.h, [o], 10, R, seed, bt.BT_MC_SHARED)[0]
+    th, var = oracle.mc(o, 10, R, seed, stream=0, shared=True)
+    disc = oracle.discount(o)
+    assert got["value"] == pytest.approx(disc * th, rel=2e-5), (got["value"], disc * th)
+    assert got["stderr_mc"] == pytest.approx(disc * math.sqrt(var), rel=5e-4)
+    assert got["paths"] == R
+
+
 def test_full_size_strata_sampled_against_the_oracle(bt, ctx, oracle):
     """The benchmark's Monte Carlo configuration at full size (N=252, 2^16
     strata x 2^14 samples): sampled strata recomputed one by one by the
