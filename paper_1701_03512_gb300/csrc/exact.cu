@@ -763,17 +763,20 @@ __device__ __forceinline__ void neu_add(neu &a, double x) {
 
 __global__ void k_finalize(const bt_job *jobs, const bt_jparams *prm, int n_jobs, const double2 *partials,
                            int prec, bt_result *out) {
-    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+    // one block per job: thread t adds items t, t + BT_THREADS, ... (Neumaier), then a fixed-shape
+    // tree over the lanes of each warp and over the warps (many warps keep the FP64 pipe busy where
+    // a job has many items)
+    __shared__ double sh[4][BT_THREADS / 32];
+    const int j = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (j >= n_jobs) return;
     const bt_job J = jobs[j];
     neu c = {0.0, 0.0}, p = {0.0, 0.0};
-    for (int i = lane; i < J.n_items; i += 32) {
+    for (int64_t i = threadIdx.x; i < J.n_items; i += BT_THREADS) {
         double2 v = partials[J.part_off + i];
         neu_add(c, v.x);
         neu_add(p, v.y);
     }
-    // fixed-shape tree over lanes
     for (int o = 16; o > 0; o >>= 1) {
         double cs = __shfl_down_sync(0xffffffffu, c.s, o), cc = __shfl_down_sync(0xffffffffu, c.c, o);
         double ps = __shfl_down_sync(0xffffffffu, p.s, o), pc = __shfl_down_sync(0xffffffffu, p.c, o);
@@ -783,6 +786,21 @@ __global__ void k_finalize(const bt_job *jobs, const bt_jparams *prm, int n_jobs
         p.c += pc;
     }
     if (lane == 0) {
+        sh[0][warp] = c.s;
+        sh[1][warp] = c.c;
+        sh[2][warp] = p.s;
+        sh[3][warp] = p.c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < BT_THREADS / 32; ++w) {
+            neu_add(c, sh[0][w]);
+            c.c += sh[1][w];
+            neu_add(p, sh[2][w]);
+            p.c += sh[3][w];
+        }
+    }
+    if (threadIdx.x == 0) {
         const bt_jparams &P = prm[J.prm_off];
         const double disc = P.disc;
         // stated error: FP64 1e-12; FP32_COMP 1e-9. The host gives the FP32
@@ -890,8 +908,6 @@ extern "C" int bt_launch_finalize(const bt_job *d_jobs, const bt_jparams *d_prm,
     (void)shard;
     (void)n_shards;
     if (n_jobs <= 0) return 0;
-    const int warps = 4;
-    k_finalize<<<(n_jobs + warps - 1) / warps, 32 * warps, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, n_jobs,
-                                                                                       partials, prec, d_out);
+    k_finalize<<<n_jobs, BT_THREADS, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, n_jobs, partials, prec, d_out);
     return (int)cudaGetLastError();
 }
