@@ -78,6 +78,42 @@ def test_all_strata_is_exact(bt, ctx, oracle):
         assert got["stderr_mc"][i] == 0.0
 
 
+def test_shared_sample_over_all_prefixes_is_exact(bt, ctx, oracle):
+    """Shared-Sample with 2^N prefixes: the suffixes are empty, every sample scores the whole tree,
+    h_i = sum_x p(x) V(x) for each i (eq. mc16 with L = 0). The FP32 strata table and the blocked
+    FP32 sum over 1024 prefixes bound the error near 80 ulps of the sum."""
+    opts = [W.opt(10, 100.0, 100.0, 0.05, 0.3, 1.0, pay) for pay in range(8)]
+    got = bt.bt_price_mc_ex(ctx.h, opts, 10, 300, 7, bt.BT_MC_SHARED)
+    for i, o in enumerate(opts):
+        ex = oracle.price_exhaustive(o, 1)
+        assert got["value"][i] == pytest.approx(ex, rel=1e-5, abs=1e-9), (i, got["value"][i], ex)
+        assert got["stderr_mc"][i] <= 1e-12 * max(abs(ex), 1.0)
+        assert got["paths"][i] == 300
+
+
+def test_maximum_strata_bits(bt, ctx, oracle):
+    """2^24 strata (the largest Partitioned stratification) at N=24, one sample each: every
+    stratum is one whole path, so the estimator is the exact sum over the 2^24 paths."""
+    o = W.opt(24, 100.0, 98.0, 0.05, 0.25, 1.0, W.ASIAN_ARITH_CALL)
+    got = bt.bt_price_mc(ctx.h, [o], 24, 1, 3)[0]
+    ex = oracle.price_exhaustive(o, 16)
+    assert got["value"] == pytest.approx(ex, rel=1e-6)
+    assert got["paths"] == 1 << 24
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_maximum_depth(bt, ctx, oracle, kind):
+    """N = 4096, the deepest tree the Monte Carlo path takes, against the oracle on the same draws.
+    The FP32 walk of 4094 steps (a running product and a running sum of 4096 terms) departs from
+    the oracle's FP64 walk by up to about N 2^-24 relative, so the check is at 1e-3."""
+    o = W.opt(4096, 100.0, 100.0, 0.05, 0.2, 1.0, W.ASIAN_ARITH_CALL)
+    got = bt.bt_price_mc_ex(ctx.h, [o], 2, 64, 21, kind)[0]
+    th, var = oracle.mc(o, 2, 64, 21, stream=0, shared=bool(kind))
+    disc = oracle.discount(o)
+    assert got["value"] == pytest.approx(disc * th, rel=1e-3)
+    assert got["stderr_mc"] == pytest.approx(disc * math.sqrt(var), rel=1e-2)
+
+
 def test_unbiased_at_n30_and_stderr_calibrated(bt, ctx, oracle):
     """N=30, 2^10 strata x 2^10 samples: within 3 SE of the exact value; the
     spread over seeds matches the reported standard error."""
