@@ -720,6 +720,8 @@ def summary(line):
     if isinstance(mc, dict):
         out["mc_n252_samples_per_s"] = mc.get("samples_per_s")
         out["mc_frac_of_issue_peak"] = mc.get("frac_of_issue_peak")
+        out["mc_shared_n64_pairs_per_s"] = g(mc, "shared_sample", "prefix_suffix_pairs_per_s")
+        out["mc_shared_frac_of_issue_peak"] = g(mc, "shared_sample", "frac_of_issue_peak")
     gr = line.get("greeks")
     if isinstance(gr, dict):
         out["greeks_n28_ms"] = gr.get("ms")
