@@ -345,6 +345,7 @@ def serving_bench(bt, W, ctx, n_req, loads):
 # ---------------------------------------------------------------------------
 MC_OPS_PER_STEP = 14   # Philox-4x32-10 per 4 steps: 10 rounds x (2 wide multiplies + 2 three-input xors) = 40
                        # (the key schedule is the same for every thread); + compare, select, multiply, add
+MC_IMAD_PER_STEP = 8    # integer multiplies per simulated step (see heavy_pipe_bound)
 # Shared-Sample pair (prefix m, suffix i): FADD sign tau_m + sign f_i, FMNMX with 0, FFMA into the sum
 # with the folded weight P(D_m) beta_m
 SHARED_OPS_PER_PAIR = 3
@@ -440,7 +441,13 @@ def mc_bench(bt, W, ctx, sms, fmax, reps=3, with_cpu=True):
             "value": float(r[0]["value"]), "stderr": float(r[0]["stderr_mc"]),
             "plain_mc_same_draws": {"value": float(plain["value"]), "stderr": float(plain["stderr_mc"]),
                                     "variance_ratio": float((plain["stderr_mc"] / r[0]["stderr_mc"]) ** 2)},
-            "ops_per_step": MC_OPS_PER_STEP, "frac_of_issue_peak": MC_OPS_PER_STEP * steps / t / peak}
+            "ops_per_step": MC_OPS_PER_STEP, "frac_of_issue_peak": MC_OPS_PER_STEP * steps / t / peak,
+            # the unit that binds: integer multiplies run only on the FMA-heavy pipe (16 lanes per SM
+            # sub-partition, 64 per SM); Philox-4x32-10 needs 2 products x (high, low) x 10 rounds per
+            # 4 steps, 8 per step once the warp-uniform products of the first rounds are shared
+            "heavy_pipe_bound": {"imad_per_step": MC_IMAD_PER_STEP,
+                                 "peak_steps_per_s": sms * 64 * fmax * 1e6 / MC_IMAD_PER_STEP,
+                                 "frac": steps / t / (sms * 64 * fmax * 1e6 / MC_IMAD_PER_STEP)}}
 
 
 # ---------------------------------------------------------------------------
@@ -720,6 +727,7 @@ def summary(line):
     if isinstance(mc, dict):
         out["mc_n252_samples_per_s"] = mc.get("samples_per_s")
         out["mc_frac_of_issue_peak"] = mc.get("frac_of_issue_peak")
+        out["mc_frac_of_heavy_pipe_bound"] = g(mc, "heavy_pipe_bound", "frac")
         out["mc_shared_n64_pairs_per_s"] = g(mc, "shared_sample", "prefix_suffix_pairs_per_s")
         out["mc_shared_frac_of_issue_peak"] = g(mc, "shared_sample", "frac_of_issue_peak")
     gr = line.get("greeks")
