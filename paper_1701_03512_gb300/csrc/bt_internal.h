@@ -22,6 +22,9 @@
 #define BT_ARITH_CLS_MAX_L 12  // ... with at most 2^12 classes of 16 bytes in shared memory
 #define BT_LOW_BITS 10         // a work item covers 2^10 consecutive prefixes
 #define BT_MIN_ITEM_BITS 5     // the split keeps >= 2^5 work items per option where it can
+#ifndef BT_MIN_ITEM_BITS_FP64
+#define BT_MIN_ITEM_BITS_FP64 7  // the FP64 pass keeps >= 2^7 (below N = 30: the FP64 pipe is slow, one
+#endif                           // option should reach most SMs; measured best of 5, 7, 8, 9)
 #define BT_THREADS 256         // threads per block of the path-sum kernels
 #define BT_PT 4                // prefixes per thread (FP32 kernel): 256 * 4 = 2^10
 #define BT_PT64 4              // prefixes per thread (FP64 kernel)

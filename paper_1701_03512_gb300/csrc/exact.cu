@@ -77,78 +77,94 @@ __device__ static double ipow(double x, int n) {
     return r;
 }
 
+// One warp per job: the record is zeroed, then lane 0 writes the scalars and the lanes write the
+// weight tables entry by entry (lane k: p^k (1-p)^(L-k), ...), so that the slow FP64 powers run
+// side by side instead of one after another. Each entry has the same formula as in a serial loop.
+static_assert(sizeof(bt_jparams) % sizeof(double) == 0, "bt_jparams is zeroed in doubles");
 __global__ void k_params(const bt_option *opts, const bt_job *jobs, bt_jparams *prm, int n_jobs) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (j >= n_jobs) return;
-    const bt_job J = jobs[j];
+    const bt_job &J = jobs[j];
     const bt_option o = opts[J.opt];
-    bt_jparams P;
-    memset(&P, 0, sizeof(P));
-    P.ok = dev_tree(o, &P.u, &P.d, &P.p);
-    P.disc = exp(-o.rate * o.T);
-    P.lnu = log(P.u);
-    P.S0 = o.S0;
-    P.K = o.K;
-    P.NKoS0 = (double)J.N * o.K / o.S0;
-    P.KoS0 = o.K / o.S0;
-    P.S0oN = o.S0 / (double)J.N;
-    const double u = P.u, lnu = P.lnu;
+    bt_jparams *P = prm + J.prm_off;
+    double *z = reinterpret_cast<double *>(P);
+    for (int i = lane; i < (int)(sizeof(bt_jparams) / sizeof(double)); i += 32) z[i] = 0.0;
+    __syncwarp();
+    double u, d, p;
+    const int ok = dev_tree(o, &u, &d, &p);   // every lane, the same values
+    const double q = 1.0 - p;
     const int L = J.L;
+    const int plo = J.P < BT_LOW_BITS ? J.P : BT_LOW_BITS;
+    const int phi = J.P - plo;
+    static_assert(BT_MAX_L < 32 && BT_LOW_BITS < 32 && BT_MAX_N_EXACT - 1 - BT_LOW_BITS < 32, "one lane per entry");
+    if (lane <= L) {
+        P->W[lane] = ipow(p, lane) * ipow(q, L - lane);
+        P->W2[lane] = split2(P->W[lane]);
+    }
+    if (lane <= plo) {
+        P->wl[lane] = ipow(p, lane) * ipow(q, plo - lane);
+        P->wl2[lane] = split2(P->wl[lane]);
+    }
+    if (lane <= phi) P->wh[lane] = pow(p, (double)lane) * pow(q, (double)(phi - lane));
+    if (lane != 0) return;
+    P->ok = ok;
+    P->u = u;
+    P->d = d;
+    P->p = p;
+    P->disc = exp(-o.rate * o.T);
+    const double lnu = log(u);
+    P->lnu = lnu;
+    P->S0 = o.S0;
+    P->K = o.K;
+    P->NKoS0 = (double)J.N * o.K / o.S0;
+    P->KoS0 = o.K / o.S0;
+    P->S0oN = o.S0 / (double)J.N;
+    double fmin, fmax;
     switch (J.field) {
     case BT_F_ARITH: {
         double a = 0.0, b = 0.0, ru = 1.0, rd = 1.0;
         for (int i = 1; i <= L; ++i) {
             ru *= u;
-            rd *= P.d;
+            rd *= d;
             a += rd;
             b += ru;
         }
-        P.fmin = a;
-        P.fmax = b;
+        fmin = a;
+        fmax = b;
         break;
     }
     case BT_F_GEO: {
         double e = (double)L * (double)(L + 1) / (2.0 * (double)J.N);
-        P.fmin = exp(-e * lnu);
-        P.fmax = exp(e * lnu);
+        fmin = exp(-e * lnu);
+        fmax = exp(e * lnu);
         break;
     }
     case BT_F_EURO:
-        P.fmin = exp(-(double)L * lnu);
-        P.fmax = exp((double)L * lnu);
+        fmin = exp(-(double)L * lnu);
+        fmax = exp((double)L * lnu);
         break;
     case BT_F_LOOKMAX:
-        P.fmin = exp(-lnu);
-        P.fmax = exp((double)L * lnu);
+        fmin = exp(-lnu);
+        fmax = exp((double)L * lnu);
         break;
     default:
-        P.fmin = exp(-(double)L * lnu);
-        P.fmax = exp(lnu);
+        fmin = exp(-(double)L * lnu);
+        fmax = exp(lnu);
         break;
     }
-    const double p = P.p, q = 1.0 - P.p;
-    for (int k = 0; k <= L; ++k) {
-        P.W[k] = ipow(p, k) * ipow(q, L - k);
-        P.W2[k] = split2(P.W[k]);
-    }
-    const int plo = J.P < BT_LOW_BITS ? J.P : BT_LOW_BITS;
-    const int phi = J.P - plo;
-    for (int c = 0; c <= plo; ++c) {
-        P.wl[c] = ipow(p, c) * ipow(q, plo - c);
-        P.wl2[c] = split2(P.wl[c]);
-    }
-    for (int c = 0; c <= phi; ++c) P.wh[c] = pow(p, (double)c) * pow(q, (double)(phi - c));
-    P.NKoS0_2 = split2(P.NKoS0);
-    P.KoS0_2 = split2(P.KoS0);
-    P.S0oN_2 = split2(P.S0oN);
-    P.S0_2 = split2(P.S0);
-    P.K_2 = split2(P.K);
-    P.fmin_f = (float)P.fmin;
-    P.fmax_f = (float)P.fmax;
+    P->fmin = fmin;
+    P->fmax = fmax;
+    P->NKoS0_2 = split2((double)J.N * o.K / o.S0);
+    P->KoS0_2 = split2(o.K / o.S0);
+    P->S0oN_2 = split2(o.S0 / (double)J.N);
+    P->S0_2 = split2(o.S0);
+    P->K_2 = split2(o.K);
+    P->fmin_f = (float)fmin;
+    P->fmax_f = (float)fmax;
     int ef;
-    frexp(P.fmax, &ef);  // fmax <= 2^ef
-    P.gexp = ef - 10;
-    prm[J.prm_off] = P;
+    frexp(fmax, &ef);  // fmax <= 2^ef
+    P->gexp = ef - 10;
 }
 
 // ---------------------------------------------------------------------------
@@ -837,7 +853,7 @@ __global__ void k_finalize(const bt_job *jobs, const bt_jparams *prm, int n_jobs
 extern "C" int bt_launch_params(const bt_option *d_opts, const bt_job *d_jobs, bt_jparams *d_prm, int n_jobs,
                                 void *stream) {
     if (n_jobs <= 0) return 0;
-    k_params<<<(n_jobs + 63) / 64, 64, 0, (cudaStream_t)stream>>>(d_opts, d_jobs, d_prm, n_jobs);
+    k_params<<<(n_jobs + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d_opts, d_jobs, d_prm, n_jobs);   // a warp per job
     return (int)cudaGetLastError();
 }
 

@@ -234,6 +234,9 @@ void payoff_field(int payoff, int *field, int *mode) {
 // leaving at least 2^15 prefixes (32 work items) where the tree has them, so
 // that even one small option spreads over the SMs.
 int exact_split_L(int N) { return std::max(1, std::min(BT_MAX_L, N - BT_LOW_BITS - BT_MIN_ITEM_BITS)); }
+int exact_split_L_fp64(int N) {
+    return std::max(1, std::min(BT_MAX_L, N - BT_LOW_BITS - BT_MIN_ITEM_BITS_FP64));
+}
 
 // Recombined suffix classes. For the geometric, European and lookback
 // payoffs the suffix factor f_s depends on the suffix only through one
@@ -299,7 +302,7 @@ void fill_job_shape(bt_job &J, int N, int field, int mode, int prec, bool skewed
     const bool arith_cls =
         prec == BT_PREC_FP32_COMP && field == BT_F_ARITH && (N <= BT_ARITH_CLS_MAX_N || skewed);
     J.N = N;
-    J.L = exact_split_L(N);
+    J.L = prec == BT_PREC_FP64 ? exact_split_L_fp64(N) : exact_split_L(N);
     if (arith_cls) J.L = std::min(J.L, BT_ARITH_CLS_MAX_L);
     J.P = N - J.L;
     J.M = (J.P + 1) / 2;

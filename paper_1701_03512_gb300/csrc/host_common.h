@@ -31,6 +31,7 @@ bt_status ctx_scratch(bt_ctx *c, size_t bytes, void **p);
 bt_status host_tree(const bt_option *o, double *u, double *d, double *p);
 bt_status validate_option(const bt_option *o, int idx, int max_n);
 int exact_split_L(int N);
+int exact_split_L_fp64(int N);
 void payoff_field(int payoff, int *field, int *mode);
 // true if the tree has fewer than 2^BT_PER_PATH_MIN_NEFF_LOG2 effective
 // paths (the per-path FP32 pass then does not meet 1e-9; the option takes a

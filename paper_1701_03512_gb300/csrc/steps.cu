@@ -105,36 +105,44 @@ __device__ static double suffix_f(int field, const sblock &b, int N) {
 // Parameters of move-by-move jobs: scalars and the suffix f range (every f_s is
 // non-decreasing in each step's factor, so the smallest and the largest
 // factors of every step bound it).
+// One warp per job: the record is zeroed, lanes 0 and 1 walk the suffix extremes (the slow FP64
+// work) side by side, lane 0 writes the scalars.
 __global__ void k_steps_params(const bt_option *opts, const bt_job *jobs, const double *steps, bt_jparams *prm,
                                int n_jobs) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (j >= n_jobs) return;
-    const bt_job J = jobs[j];
+    const bt_job &J = jobs[j];
     const bt_option o = opts[J.opt];
-    bt_jparams P;
-    memset(&P, 0, sizeof(P));
-    P.ok = 1;
-    P.disc = exp(-o.rate * o.T);
-    P.S0 = o.S0;
-    P.K = o.K;
-    P.NKoS0 = (double)J.N * o.K / o.S0;
-    P.KoS0 = o.K / o.S0;
-    P.S0oN = o.S0 / (double)J.N;
+    bt_jparams *P = prm + J.prm_off;
+    double *z = reinterpret_cast<double *>(P);
+    for (int i = lane; i < (int)(sizeof(bt_jparams) / sizeof(double)); i += 32) z[i] = 0.0;
+    __syncwarp();
     const int b = J.branches;
     const double *st = steps + 2 * b * (J.off_pow + J.P);
-    P.fmin = suffix_f(J.field, walk_steps(0, J.L, b, st, -1), J.N);
-    P.fmax = suffix_f(J.field, walk_steps(0, J.L, b, st, +1), J.N);
-    P.NKoS0_2 = split2(P.NKoS0);
-    P.KoS0_2 = split2(P.KoS0);
-    P.S0oN_2 = split2(P.S0oN);
-    P.S0_2 = split2(P.S0);
-    P.K_2 = split2(P.K);
-    P.fmin_f = (float)P.fmin;
-    P.fmax_f = (float)P.fmax;
+    double fv = 0.0;
+    if (lane < 2) fv = suffix_f(J.field, walk_steps(0, J.L, b, st, lane == 0 ? -1 : +1), J.N);
+    const double fmin = __shfl_sync(0xffffffffu, fv, 0), fmax = __shfl_sync(0xffffffffu, fv, 1);
+    if (lane != 0) return;
+    P->ok = 1;
+    P->disc = exp(-o.rate * o.T);
+    P->S0 = o.S0;
+    P->K = o.K;
+    P->NKoS0 = (double)J.N * o.K / o.S0;
+    P->KoS0 = o.K / o.S0;
+    P->S0oN = o.S0 / (double)J.N;
+    P->fmin = fmin;
+    P->fmax = fmax;
+    P->NKoS0_2 = split2((double)J.N * o.K / o.S0);
+    P->KoS0_2 = split2(o.K / o.S0);
+    P->S0oN_2 = split2(o.S0 / (double)J.N);
+    P->S0_2 = split2(o.S0);
+    P->K_2 = split2(o.K);
+    P->fmin_f = (float)fmin;
+    P->fmax_f = (float)fmax;
     int ef;
-    frexp(P.fmax, &ef);  // fmax <= 2^ef
-    P.gexp = ef - 10;
-    prm[J.prm_off] = P;
+    frexp(fmax, &ef);  // fmax <= 2^ef
+    P->gexp = ef - 10;
 }
 
 __device__ static bt_spentry make_spentry(const sblock &b, double e) {
@@ -546,7 +554,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_steps64(bt_exact_args a, cons
 extern "C" int bt_launch_steps_params(const bt_option *d_opts, const bt_job *d_jobs, const double *d_steps,
                                       bt_jparams *d_prm, int n_jobs, void *stream) {
     if (n_jobs <= 0) return 0;
-    k_steps_params<<<(n_jobs + 63) / 64, 64, 0, (cudaStream_t)stream>>>(d_opts, d_jobs, d_steps, d_prm, n_jobs);
+    k_steps_params<<<(n_jobs + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d_opts, d_jobs, d_steps, d_prm, n_jobs);   // a warp per job
     return (int)cudaGetLastError();
 }
 

@@ -109,15 +109,17 @@ def test_options_array_roundtrip(bt):
 def test_exact_split_needs_no_device(bt):
     """The pass's prefix/suffix split (Section 3's rank bits as the prefix),
     queried on the host: L = N - 15 (at least 1, at most 13) suffix steps, so
-    an option keeps 2^5 work items of 2^10 prefixes where it can; FP32
-    arithmetic Asians up to N = 27 sum each suffix as a class, with at most 12."""
+    an option keeps 2^5 work items of 2^10 prefixes where it can, and
+    L = N - 17 for the FP64 pass (2^7 items); FP32 arithmetic Asians up to
+    N = 27 sum each suffix as a class, with at most 12."""
     cases = [  # (N, payoff, precision) -> (P, L)
         ((36, W.ASIAN_ARITH_CALL, bt.BT_PREC_FP32_COMP), (23, 13)),
         ((28, W.ASIAN_ARITH_PUT, bt.BT_PREC_FP32_COMP), (15, 13)),
         ((27, W.ASIAN_ARITH_PUT, bt.BT_PREC_FP32_COMP), (15, 12)),
-        ((26, W.ASIAN_ARITH_PUT, bt.BT_PREC_FP64), (15, 11)),
+        ((26, W.ASIAN_ARITH_PUT, bt.BT_PREC_FP64), (17, 9)),
+        ((30, W.ASIAN_ARITH_PUT, bt.BT_PREC_FP64), (17, 13)),
         ((30, W.ASIAN_GEO_CALL, bt.BT_PREC_FP32_COMP), (17, 13)),
-        ((20, W.ASIAN_ARITH_CALL, bt.BT_PREC_FP64), (15, 5)),
+        ((20, W.ASIAN_ARITH_CALL, bt.BT_PREC_FP64), (17, 3)),
         ((5, W.EURO_PUT, bt.BT_PREC_FP64), (4, 1)),
     ]
     for (N, pay, prec), (P, L) in cases:
@@ -142,7 +144,7 @@ def test_skewed_trees_route_to_the_class_pass(bt):
                      (0.996, 12)):
             o = W.opt(N, 100.0, 100.0, 0.0, 0.2, 1.0, W.ASIAN_ARITH_CALL, W.TREE_EXPLICIT, u=u, d=1 / u, p=p)
             assert bt.bt_exact_split(o, bt.BT_PREC_FP32_COMP)["L"] == L, (N, p)
-            assert bt.bt_exact_split(o, bt.BT_PREC_FP64)["L"] == 13
+            assert bt.bt_exact_split(o, bt.BT_PREC_FP64)["L"] == min(13, N - 17)
             g = dict(o, payoff=W.ASIAN_GEO_CALL)
             assert bt.bt_exact_split(g, bt.BT_PREC_FP32_COMP)["L"] == 13
 
@@ -163,4 +165,4 @@ def test_plain_c_client(bt, tmp_path):
                     "-Wl,-rpath," + libdir, "-o", exe], check=True)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
-    assert "split P=15 L=5" in r.stdout
+    assert "split P=17 L=3" in r.stdout   # FP64 at N=20: 2^7 work items of 2^10 prefixes
