@@ -7,7 +7,8 @@
 
 #define BT_MAX_N_EXACT 40
 #define BT_MAX_L 13            // suffix steps held in a shared-memory table (lattice passes)
-#define BT_STEPS_MAX_L 12      // b^L <= 2^12 suffixes for trees given move by move (16-byte entries)
+#define BT_STEPS_MAX_L 12      // b^L <= 2^12 suffixes for trees given move by move, FP64 pass (16-byte entries)
+#define BT_STEPS32_MAX_L 13    // b^L <= 2^13 for the FP32 pass (12 bytes a suffix: three float arrays)
 #define BT_ARITH_CLS_MAX_N 27  // FP32 arithmetic-Asian jobs up to this depth sum each suffix as a class
 // The FP32 passes that round every path once average those roundings over
 // the tree's effective number of paths, n_eff = 1 / sum_x p(x)^2 (2^N for a

@@ -43,11 +43,10 @@ __device__ __forceinline__ double2 block_sum2(double x, double y, double2 *red) 
     return r;
 }
 
-// Loads the next work item and (if it changed) its job into shared memory.
-// Returns false when the run has no items left.
-template <typename SufT>
-__device__ __forceinline__ bool next_item(const bt_exact_args &a, smem_job &sj, SufT *s_suf, const SufT *g_suf,
-                                          int &cur_job) {
+// Loads the next work item and (if it changed) its job into shared memory; `load(J)` copies
+// the job's suffix table (all threads take part). Returns false when the run has no items left.
+template <typename Load>
+__device__ __forceinline__ bool next_item_with(const bt_exact_args &a, smem_job &sj, int &cur_job, Load load) {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long i = atomicAdd(a.counter, 1ull);
@@ -63,11 +62,20 @@ __device__ __forceinline__ bool next_item(const bt_exact_args &a, smem_job &sj, 
             sj.P = a.prm[sj.J.prm_off];
         }
         __syncthreads();
-        const SufT *src = g_suf + sj.J.off_suf;
-        for (int i = threadIdx.x; i < sj.J.suf_len; i += BT_THREADS) s_suf[i] = src[i];
+        load(sj.J);
         __syncthreads();
     }
     return true;
+}
+
+// The same with the suffix table copied entry by entry.
+template <typename SufT>
+__device__ __forceinline__ bool next_item(const bt_exact_args &a, smem_job &sj, SufT *s_suf, const SufT *g_suf,
+                                          int &cur_job) {
+    return next_item_with(a, sj, cur_job, [&](const bt_job &J) {
+        const SufT *src = g_suf + J.off_suf;
+        for (int i = threadIdx.x; i < J.suf_len; i += BT_THREADS) s_suf[i] = src[i];
+    });
 }
 
 // The FP32 per-prefix scale of the rounding design (exact.cu header):

@@ -23,9 +23,10 @@
 // pairs), composed per prefix in pair arithmetic. The FP32 path keeps the
 // rounding design of exact.cu (scaled affine form, exact lambda f_hi + A_hi,
 // one rounding per payoff). The weight enters as one FP32 number per suffix,
-// rounded from FP64 by error diffusion along ascending f_s (k_steps_weights):
-// the rounding residuals r_s = w_s - w32_s then have every partial sum over
-// a run of consecutive f_s bounded by one FP32 ulp of the largest weight, and
+// rounded from FP64 by error diffusion along ascending f_s (k_steps_weights, in
+// 8 interleaved subsequences): the rounding residuals r_s = w_s - w32_s then
+// have every partial sum over a run of consecutive f_s bounded by 8 FP32 ulps
+// of the largest weight, and
 // because a payoff is max(+-(tau + f_s), 0) -- an integral over thresholds of
 // the indicator of f_s above (below) the threshold -- sum_s r_s payoff_s is
 // bounded by that ulp times the payoff range (summation by parts) instead
@@ -216,18 +217,25 @@ __global__ void k_steps_tables(const bt_job *jobs, const bt_jparams *prm, const 
 // the entries (f_hi, -f_lo, w_hi, w_lo) written by k_steps_tables are sorted
 // by f = f_hi + f_lo (bitonic sort in shared memory on the bit patterns of the
 // FP64 values, which order like the values since every f_s > 0; padding keys
-// after every suffix), then one thread walks them in ascending f carrying the
-// rounding residual: w32 = RN_f32(w + carry), carry = w + carry - w32, with
-// w the FP32 pair (w_hi, w_lo) and the carry kept exactly by error-free sums
-// (TwoSum, Fast2Sum), so that the residuals of any run of consecutive f
-// telescope to the difference of two carries, each at most half an FP32 ulp.
-// A weight of 0 (a branch of probability 0) stays 0. The entry keeps
+// after every suffix), then BT_DIFFUSE_LANES lanes of one warp each walk one of
+// the interleaved subsequences r = lane, lane + BT_DIFFUSE_LANES, ... (each in
+// ascending f) carrying the rounding residual: w32 = RN_f32(w + carry),
+// carry = w + carry - w32, with w the FP32 pair (w_hi, w_lo) and the carry kept
+// exactly by error-free sums (TwoSum, Fast2Sum), so that the residuals of any
+// run of consecutive f telescope, per subsequence, to the difference of two
+// carries, each at most half an FP32 ulp: BT_DIFFUSE_LANES ulps at most over
+// the run. A weight of 0 (a branch of probability 0) stays 0. The entry keeps
 // (f_hi, -f_lo, w32, 0).
-#define BT_SORT_N (1 << BT_STEPS_MAX_L)
+#ifndef BT_DIFFUSE_LANES
+#define BT_DIFFUSE_LANES 8
+#endif
+static_assert(BT_DIFFUSE_LANES >= 1 && BT_DIFFUSE_LANES <= 32, "diffusion lanes of one warp");
+#define BT_SORT_N (1 << BT_STEPS32_MAX_L)
+#define BT_SORT_SMEM ((size_t)BT_SORT_N * (sizeof(unsigned long long) + sizeof(int16_t)))
 __global__ void __launch_bounds__(1024) k_steps_weights(const bt_job *jobs, float4 *suf32) {
     const bt_job J = jobs[blockIdx.x];
-    __shared__ unsigned long long key[BT_SORT_N];
-    __shared__ int16_t idx[BT_SORT_N];
+    extern __shared__ unsigned long long key[];   // [BT_SORT_N], then idx
+    int16_t *idx = reinterpret_cast<int16_t *>(key + BT_SORT_N);
     const int n = (int)J.n_suffix;
     int np = 1;
     while (np < n) np <<= 1;
@@ -266,9 +274,9 @@ __global__ void __launch_bounds__(1024) k_steps_weights(const bt_job *jobs, floa
         wp[r] = make_float2(e.z, e.w);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < BT_DIFFUSE_LANES) {
         float carry = 0.0f;
-        for (int r = 0; r < n; ++r) {
+        for (int r = threadIdx.x; r < n; r += BT_DIFFUSE_LANES) {
             const float2 w = wp[r];
             if (w.x == 0.0f) continue;               // probability 0: weight 0, carry kept
             const df32 t = two_sum(w.x, carry);      // w_hi + carry, exactly
@@ -341,15 +349,35 @@ __device__ __forceinline__ sstate steps_state(const bt_job &J, const bt_jparams 
 // y = lambda f_hi + A_hi (exact), c = lambda (-f_lo) - A_lo, z = sat(+-(y - c))
 // (call: y - c, put: c - y), accumulated as w32 z by a chain of FMAs; a
 // call and a put share y and c.
+// The FP32 suffix table in shared memory: three arrays of BT_STEPS32_SUF floats (f_hi, -f_lo, w32)
+// read four suffixes per 16-byte load.
+#define BT_STEPS32_SUF (1 << BT_STEPS32_MAX_L)
+#define BT_STEPS32_SMEM ((size_t)3 * BT_STEPS32_SUF * sizeof(float))
+struct suf_soa {
+    const float *fh, *nfl, *w;
+};
+struct suf8 {
+    float fh[BT_UNROLL], nfl[BT_UNROLL], w[BT_UNROLL];
+};
+static_assert(BT_UNROLL == 8, "two float4 loads per array and chain");
+__device__ __forceinline__ void load8(const suf_soa &t, int s, suf8 &v) {
+    // s is a multiple of 8 (the table is padded to whole chains), so the float4 loads are aligned
+    *reinterpret_cast<float4 *>(&v.fh[0]) = *reinterpret_cast<const float4 *>(t.fh + s);
+    *reinterpret_cast<float4 *>(&v.fh[4]) = *reinterpret_cast<const float4 *>(t.fh + s + 4);
+    *reinterpret_cast<float4 *>(&v.nfl[0]) = *reinterpret_cast<const float4 *>(t.nfl + s);
+    *reinterpret_cast<float4 *>(&v.nfl[4]) = *reinterpret_cast<const float4 *>(t.nfl + s + 4);
+    *reinterpret_cast<float4 *>(&v.w[0]) = *reinterpret_cast<const float4 *>(t.w + s);
+    *reinterpret_cast<float4 *>(&v.w[4]) = *reinterpret_cast<const float4 *>(t.w + s + 4);
+}
 template <int MODE>
-__device__ __forceinline__ void wchain8(const float4 *f4, float B, float Ah, float nAl, float &tc, float &tp) {
+__device__ __forceinline__ void wchain8(const suf8 &v, float B, float Ah, float nAl, float &tc, float &tp) {
     float ac = 0.0f, ap = 0.0f;
 #pragma unroll
     for (int i = 0; i < BT_UNROLL; ++i) {
-        const float y = __fmaf_rn(B, f4[i].x, Ah);
-        const float c = __fmaf_rn(B, f4[i].y, nAl);
-        if (MODE & BT_MODE_CALL) ac = __fmaf_rn(f4[i].z, __saturatef(__fsub_rn(y, c)), ac);
-        if (MODE & BT_MODE_PUT) ap = __fmaf_rn(f4[i].z, __saturatef(__fsub_rn(c, y)), ap);
+        const float y = __fmaf_rn(B, v.fh[i], Ah);
+        const float c = __fmaf_rn(B, v.nfl[i], nAl);
+        if (MODE & BT_MODE_CALL) ac = __fmaf_rn(v.w[i], __saturatef(__fsub_rn(y, c)), ac);
+        if (MODE & BT_MODE_PUT) ap = __fmaf_rn(v.w[i], __saturatef(__fsub_rn(c, y)), ap);
     }
     tc = ac;
     tp = ap;
@@ -367,7 +395,7 @@ __device__ __forceinline__ void fast_acc_s(float &g, float &e, float t) {
 // combined in pairs (w beta / lambda and C recomputed after the loop), the
 // block in FP64.
 template <int MODE>
-__device__ __forceinline__ void item_steps32(const bt_exact_args &a, const smem_job &sj, const float4 *s_suf,
+__device__ __forceinline__ void item_steps32(const bt_exact_args &a, const smem_job &sj, const suf_soa &s_suf,
                                              const bt_spentry *tab, double2 *red) {
     const bt_job &J = sj.J;
     const bt_jparams &P = sj.P;
@@ -398,13 +426,12 @@ __device__ __forceinline__ void item_steps32(const bt_exact_args &a, const smem_
         for (int j = 0; j < BT_PT; ++j) tc[j] = tp[j] = 0.0f;
 #pragma unroll 2
         for (int r = 0; r < 8; ++r) {
-            float4 f4[BT_UNROLL];
-#pragma unroll
-            for (int i = 0; i < BT_UNROLL; ++i) f4[i] = s_suf[s + r * BT_UNROLL + i];
+            suf8 v;
+            load8(s_suf, s + r * BT_UNROLL, v);
 #pragma unroll
             for (int j = 0; j < BT_PT; ++j) {
                 float uc, up;
-                wchain8<MODE>(f4, B[j], Ah[j], nAl[j], uc, up);
+                wchain8<MODE>(v, B[j], Ah[j], nAl[j], uc, up);
                 if (MODE & BT_MODE_CALL) tc[j] = __fadd_rn(tc[j], uc);
                 if (MODE & BT_MODE_PUT) tp[j] = __fadd_rn(tp[j], up);
             }
@@ -416,13 +443,12 @@ __device__ __forceinline__ void item_steps32(const bt_exact_args &a, const smem_
         }
     }
     for (; s < J.suf_len; s += BT_UNROLL) {
-        float4 f4[BT_UNROLL];
-#pragma unroll
-        for (int i = 0; i < BT_UNROLL; ++i) f4[i] = s_suf[s + i];
+        suf8 v;
+        load8(s_suf, s, v);
 #pragma unroll
         for (int j = 0; j < BT_PT; ++j) {
             float uc, up;
-            wchain8<MODE>(f4, B[j], Ah[j], nAl[j], uc, up);
+            wchain8<MODE>(v, B[j], Ah[j], nAl[j], uc, up);
             if (MODE & BT_MODE_CALL) fast_acc_s(gc[j], ec[j], uc);
             if (MODE & BT_MODE_PUT) fast_acc_s(gp[j], ep[j], up);
         }
@@ -519,15 +545,27 @@ __device__ __forceinline__ void item_steps64(const bt_exact_args &a, const smem_
 }
 
 __global__ void __launch_bounds__(BT_THREADS, 2) k_steps32(bt_exact_args a, const bt_spentry *tab) {
-    extern __shared__ float4 s_suf4[];
+    extern __shared__ float4 s_suf4[];   // BT_STEPS32_SMEM bytes: f_hi, -f_lo, w32 arrays
+    float *const s_f = reinterpret_cast<float *>(s_suf4);
+    const suf_soa t = {s_f, s_f + BT_STEPS32_SUF, s_f + 2 * BT_STEPS32_SUF};
     __shared__ smem_job sj;
     __shared__ double2 red[BT_THREADS / 32];
     int cur_job = -1;
-    while (next_item<float4>(a, sj, s_suf4, reinterpret_cast<const float4 *>(a.suf32), cur_job)) {
+    const float4 *g_suf = reinterpret_cast<const float4 *>(a.suf32);
+    // the job's (f_hi, -f_lo, w32, 0) entries split into the three arrays
+    auto load = [&](const bt_job &J) {
+        for (int i = threadIdx.x; i < J.suf_len; i += BT_THREADS) {
+            const float4 e = g_suf[J.off_suf + i];
+            s_f[i] = e.x;
+            s_f[BT_STEPS32_SUF + i] = e.y;
+            s_f[2 * BT_STEPS32_SUF + i] = e.z;
+        }
+    };
+    while (next_item_with(a, sj, cur_job, load)) {
         switch (sj.J.mode) {
-        case BT_MODE_CALL: item_steps32<BT_MODE_CALL>(a, sj, s_suf4, tab, red); break;
-        case BT_MODE_PUT: item_steps32<BT_MODE_PUT>(a, sj, s_suf4, tab, red); break;
-        default: item_steps32<BT_MODE_BOTH>(a, sj, s_suf4, tab, red); break;
+        case BT_MODE_CALL: item_steps32<BT_MODE_CALL>(a, sj, t, tab, red); break;
+        case BT_MODE_PUT: item_steps32<BT_MODE_PUT>(a, sj, t, tab, red); break;
+        default: item_steps32<BT_MODE_BOTH>(a, sj, t, tab, red); break;
         }
     }
 }
@@ -567,7 +605,12 @@ extern "C" int bt_launch_steps_tables(const bt_job *d_jobs, const bt_jparams *d_
     if (bx < 1) bx = 1;
     dim3 grid(bx, n_jobs);
     k_steps_tables<<<grid, 256, 0, (cudaStream_t)stream>>>(d_jobs, d_prm, d_steps, prec, suf32, suf64, tab);
-    if (prec == BT_PREC_FP32_COMP) k_steps_weights<<<n_jobs, 1024, 0, (cudaStream_t)stream>>>(d_jobs, suf32);
+    if (prec == BT_PREC_FP32_COMP) {
+        cudaError_t e = cudaFuncSetAttribute(k_steps_weights, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)BT_SORT_SMEM);
+        if (e != cudaSuccess) return (int)e;
+        k_steps_weights<<<n_jobs, 1024, BT_SORT_SMEM, (cudaStream_t)stream>>>(d_jobs, suf32);
+    }
     return (int)cudaGetLastError();
 }
 
@@ -575,18 +618,19 @@ extern "C" int bt_launch_steps_tables(const bt_job *d_jobs, const bt_jparams *d_
 extern "C" int bt_launch_steps(const bt_exact_args *a, const bt_spentry *tab, int prec, int device, void *stream) {
     if (a->n_run_items <= 0) return 0;
     const void *k = prec == BT_PREC_FP64 ? (const void *)k_steps64 : (const void *)k_steps32;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BT_STEPS_SMEM);
+    const size_t smem = prec == BT_PREC_FP64 ? BT_STEPS_SMEM : BT_STEPS32_SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BT_THREADS, BT_STEPS_SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BT_THREADS, smem);
     if (e != cudaSuccess) return (int)e;
     if (per < 1) per = 1;
     int64_t grid = (int64_t)sms * per;
     if (grid > a->n_run_items) grid = a->n_run_items;
     if (prec == BT_PREC_FP64)
-        k_steps64<<<(unsigned)grid, BT_THREADS, BT_STEPS_SMEM, (cudaStream_t)stream>>>(*a, tab);
+        k_steps64<<<(unsigned)grid, BT_THREADS, smem, (cudaStream_t)stream>>>(*a, tab);
     else
-        k_steps32<<<(unsigned)grid, BT_THREADS, BT_STEPS_SMEM, (cudaStream_t)stream>>>(*a, tab);
+        k_steps32<<<(unsigned)grid, BT_THREADS, smem, (cudaStream_t)stream>>>(*a, tab);
     return (int)cudaGetLastError();
 }

@@ -44,13 +44,14 @@ static bt_status validate_moves(const double *mv, int N, int b, int idx, int pre
     return BT_OK;
 }
 
-// Suffix steps of a move-by-move job: b^L <= 2^12 entries in shared memory,
-// leaving at least 2^15 prefixes where the tree has them (binomial: the
-// lattice split).
-static int moves_split_L(int N, int b) {
+// Suffix steps of a move-by-move job: b^L <= 2^13 entries in shared memory for the FP32 pass
+// (2^12 for FP64), leaving at least 2^15 prefixes where the tree has them (binomial: the lattice
+// split).
+static int moves_split_L(int N, int b, bt_precision prec) {
+    const int max_l = prec == BT_PREC_FP64 ? BT_STEPS_MAX_L : BT_STEPS32_MAX_L;
     int L = 0;
     int64_t nsuf = 1;
-    while (L < N && nsuf * b <= (1 << BT_STEPS_MAX_L) &&
+    while (L < N && nsuf * b <= (1 << max_l) &&
            (L == 0 || (b == 2 ? L < exact_split_L(N)
                               : std::pow((double)b, (double)(N - L - 1)) >=
                                     (double)(1 << (BT_LOW_BITS + BT_MIN_ITEM_BITS))))) {
@@ -108,7 +109,7 @@ static bt_status price_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int 
         }
         J.N = opts[i].N;
         J.branches = b;
-        const int L = moves_split_L(J.N, b);
+        const int L = moves_split_L(J.N, b, prec);
         int64_t nsuf = 1;
         for (int t = 0; t < L; ++t) nsuf *= b;
         J.L = L;
@@ -222,7 +223,7 @@ static bt_status price_moves(bt_ctx *ctx, const bt_option *opts, int32_t n, int 
 // neighbours differ by more than 1e-12 relative; more than eight suffixes
 // per distinct value on average counts as repeating. A recombining tree (the
 // same moves at every step) repeats end prices, level sums and extremes
-// hundreds of times (13 end prices for 4096 binomial suffixes); a lookback on
+// hundreds of times (14 end prices for 8192 binomial suffixes); a lookback on
 // a tree that does not recombine repeats its running extreme a few times
 // (over the continuations that stay inside it: 2 to 4 suffixes per value on
 // the trees tested), which the FP32 pass keeps.
@@ -230,7 +231,7 @@ static bool suffix_values_repeat(const bt_option &o, int b, const double *mv) {
     int field, mode;
     payoff_field(o.payoff, &field, &mode);
     if (field == BT_F_ARITH) return false;
-    const int N = o.N, L = moves_split_L(N, b), P = N - L;
+    const int N = o.N, L = moves_split_L(N, b, BT_PREC_FP32_COMP), P = N - L;   // the FP32 pass's split
     int64_t nsuf = 1;
     for (int t = 0; t < L; ++t) nsuf *= b;
     std::vector<double> f((size_t)nsuf);
