@@ -174,10 +174,14 @@ __device__ __forceinline__ void greeks8(const float4 *f4, const float4 *d4, floa
         const float y = __fmaf_rn(B, fh[i], Ah);
         const float c = __fmaf_rn(B, fl[i], nAl);
         z[i] = (MODE & BT_MODE_CALL) ? __saturatef(__fsub_rn(y, c)) : __saturatef(__fsub_rn(c, y));
-        // in the money (the NaN padding saturates to 0 and is never selected)
-        const bool itm = z[i] > 0.0f;
-        cn += itm ? 1.0f : 0.0f;
-        t[i] = itm ? fd[i] : 0.0f;
+        // in the money as a number, on the FMA pipe (a compare and two selects would load the ALU
+        // pipe, the busier one in this loop): sat(z 2^126) is 1 for every positive normal z and 0
+        // out of the money; the NaN padding saturates to 0. Only a positive z below 2^-126 (a
+        // cancellation of y - c to 1e-38) would count as a fraction of a path, far below the
+        // derivatives' stated accuracy.
+        const float ind = __saturatef(__fmul_rn(z[i], 0x1p126f));
+        cn = __fadd_rn(cn, ind);
+        t[i] = __fmul_rn(ind, fd[i]);
     }
 #pragma unroll
     for (int w = 1; w < BT_UNROLL; w *= 2)
