@@ -222,16 +222,21 @@ __device__ __forceinline__ void chan(float &n, float &mean, float &M2, float nb,
 // The Shared-Sample estimator (the Remark of Section 4, eq. mc16): every suffix sample i is
 // scored under all 2^m prefixes, h_i = sum_m P(D_m) V(z_m, y_i). With
 // V = beta_m max(sign (tau_m + f_i), 0) + C_m, the C part is the per-job constant
-// s_pc = sum_m P(D_m) C_m and each (prefix, sample) pair costs an add, a clamp at 0 and a
-// multiply-add. Table entry m (shared memory) = (sign tau_m, sign tau_m, w_m, w_m) with
-// w_m = P(D_m) beta_m: the paired FP32 add and multiply-add (__fadd2_rn, __ffma2_rn) take two
-// samples in one instruction, and the clamps (FMNMX) run on the ALU pipe beside them. The sum over
-// prefixes runs in blocks of 64 (two-level summation: FP32 error under 64 + 2^m / 64 ulps).
-// A work item is BT_MC_ITEM = 4 x BT_THREADS samples: four per thread, walked together. The
-// item's (count, mean, M2) is combined over its warps in FP32 by warp 0 and stored in FP64.
+// s_pc = sum_m P(D_m) C_m and each (prefix, sample) pair costs a clamped add and a multiply-add.
+// The block holds the job's table as (t_m, t_m, w_m, w_m) with t_m = sign tau_m 2^-k and
+// w_m = P(D_m) beta_m 2^k, where 2^k >= 2 max_{m,i} sign (tau_m + f_i) (the largest sign tau_m
+// plus a bound of sign f), k >= 0: then t_m + sign f_i 2^-k < 1 and the saturating add
+// sat(t_m + sign f_i 2^-k) is max(sign (tau_m + f_i), 0) 2^-k exactly (the scale is a power of
+// 2), so the clamp runs on the FMA pipe instead of the ALU pipe, and w_m sat(.) is the unscaled
+// term, the same FP32 number as without the scale. (scale_k = -1: an unscaled table for bounds
+// beyond 2^60, clamped with max(., 0).) Two samples share each
+// paired multiply-add (__ffma2_rn). The sum over prefixes runs in blocks of 64 (two-level
+// summation: FP32 error under 64 + 2^mb / 64 ulps). A work item is BT_MC_ITEM = 4 x BT_THREADS
+// samples: four per thread, walked together. The item's (count, mean, M2) is combined over its
+// warps in FP32 by warp 0 and stored in FP64.
 template <int FIELD>
 __device__ void mc_shared_item(const bt_mc_args &a, const bt_mc_job &J, int64_t item, const float4 *s_tab,
-                               float s_pc, float3 *red) {
+                               float s_pc, int scale_k, float3 *red) {
     static_assert(BT_MC_ITEM == 4 * BT_THREADS, "four samples per thread and item");
     const int64_t i0 = item * BT_MC_ITEM + threadIdx.x;
     unsigned idx[4];
@@ -239,20 +244,32 @@ __device__ void mc_shared_item(const bt_mc_args &a, const bt_mc_job &J, int64_t 
     for (int w = 0; w < 4; ++w) idx[w] = (unsigned)(i0 + (int64_t)w * BT_THREADS);
     float f[4];
     simulate_w<FIELD, 4>(J, idx, 0u, f, make_uint2(a.key_lo, a.key_hi));
-    const float sg = J.sign > 0 ? 1.0f : -1.0f;
-    const float2 F01 = make_float2(sg * f[0], sg * f[1]), F23 = make_float2(sg * f[2], sg * f[3]);
+    const float down = scale_k >= 0 ? scalbnf(1.0f, -scale_k) : 1.0f;
+    const float sg = J.sign > 0 ? down : -down;   // sign 2^-k
+    const float fa = sg * f[0], fb = sg * f[1], fc = sg * f[2], fd = sg * f[3];
     float2 v01 = make_float2(0.0f, 0.0f), v23 = make_float2(0.0f, 0.0f);
     const int M = 1 << J.mb;
     for (int m0 = 0; m0 < M; m0 += 64) {
         const int m1 = min(m0 + 64, M);
         float2 a01 = make_float2(0.0f, 0.0f), a23 = make_float2(0.0f, 0.0f);
+        if (scale_k >= 0) {
 #pragma unroll 8
-        for (int m = m0; m < m1; ++m) {
-            const float4 P = s_tab[m];
-            const float2 TT = make_float2(P.x, P.y), WW = make_float2(P.z, P.w);
-            const float2 y01 = __fadd2_rn(TT, F01), y23 = __fadd2_rn(TT, F23);
-            a01 = __ffma2_rn(WW, make_float2(fmaxf(y01.x, 0.0f), fmaxf(y01.y, 0.0f)), a01);
-            a23 = __ffma2_rn(WW, make_float2(fmaxf(y23.x, 0.0f), fmaxf(y23.y, 0.0f)), a23);
+            for (int m = m0; m < m1; ++m) {
+                const float4 P = s_tab[m];
+                const float2 WW = make_float2(P.z, P.w);
+                a01 = __ffma2_rn(WW, make_float2(__saturatef(__fadd_rn(P.x, fa)), __saturatef(__fadd_rn(P.y, fb))),
+                                 a01);
+                a23 = __ffma2_rn(WW, make_float2(__saturatef(__fadd_rn(P.x, fc)), __saturatef(__fadd_rn(P.y, fd))),
+                                 a23);
+            }
+        } else {   // unscaled table (suffix quantities beyond 2^60): the clamp as max(., 0)
+#pragma unroll 8
+            for (int m = m0; m < m1; ++m) {
+                const float4 P = s_tab[m];
+                const float2 WW = make_float2(P.z, P.w);
+                a01 = __ffma2_rn(WW, make_float2(fmaxf(__fadd_rn(P.x, fa), 0.0f), fmaxf(__fadd_rn(P.y, fb), 0.0f)), a01);
+                a23 = __ffma2_rn(WW, make_float2(fmaxf(__fadd_rn(P.x, fc), 0.0f), fmaxf(__fadd_rn(P.y, fd), 0.0f)), a23);
+            }
         }
         v01 = __fadd2_rn(v01, a01);
         v23 = __fadd2_rn(v23, a23);
@@ -341,6 +358,8 @@ __device__ __forceinline__ void mc_claim(const bt_mc_args &a, int64_t *item, int
 __global__ void __launch_bounds__(BT_THREADS, 2) k_mc_shared(bt_mc_args a) {
     __shared__ float4 s_tab[BT_MC_TAB_ENTRIES];
     __shared__ float s_pc;
+    __shared__ float s_max[BT_THREADS / 32];
+    __shared__ int s_k;
     __shared__ float3 red[2][BT_THREADS / 32];
     __shared__ int64_t s_item[2];
     __shared__ int s_job[2];
@@ -363,19 +382,43 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_mc_shared(bt_mc_args a) {
             }
             const int M = 1 << a.jobs[jb].mb;
             const float4 *tab = a.shared_tab + (size_t)jb * BT_MC_TAB_ENTRIES;
-            for (int m = threadIdx.x; m < M; m += BT_THREADS) s_tab[m] = tab[m];
+            float tmax = -3.0e38f;
+            for (int m = threadIdx.x; m < M; m += BT_THREADS) {
+                s_tab[m] = tab[m];
+                tmax = fmaxf(tmax, tab[m].x);
+            }
+            // the pair loop's scale: 2^k >= 2 (max_m t_m + bound of sign f), k >= 0; beyond 2^60
+            // (k = -1) the table stays unscaled and the loop clamps with max(., 0)
+            for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+            if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = tmax;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float t = s_max[0];
+                for (int w = 1; w < BT_THREADS / 32; ++w) t = fmaxf(t, s_max[w]);
+                const double B = (double)t + a.jobs[jb].fbound;
+                s_k = B < 0.5 ? 0 : B < 0x1p60 ? ilogb(B) + 2 : -1;
+            }
+            __syncthreads();
+            if (s_k > 0) {
+                const float down = scalbnf(1.0f, -s_k), up = scalbnf(1.0f, s_k);
+                for (int m = threadIdx.x; m < M; m += BT_THREADS) {
+                    const float4 e = s_tab[m];
+                    s_tab[m] = make_float4(e.x * down, e.y * down, e.z * up, e.w * up);
+                }
+            }
             __syncthreads();
             cur_job = jb;
         }
         const bt_mc_job &J = sJ;
         const int64_t item = it - J.item_begin;
         float3 *rk = red[k & 1];
+        const int sk = s_k;
         switch (J.field) {
-        case BT_F_ARITH: mc_shared_item<BT_F_ARITH>(a, J, item, s_tab, s_pc, rk); break;
-        case BT_F_GEO: mc_shared_item<BT_F_GEO>(a, J, item, s_tab, s_pc, rk); break;
-        case BT_F_EURO: mc_shared_item<BT_F_EURO>(a, J, item, s_tab, s_pc, rk); break;
-        case BT_F_LOOKMAX: mc_shared_item<BT_F_LOOKMAX>(a, J, item, s_tab, s_pc, rk); break;
-        default: mc_shared_item<BT_F_LOOKMIN>(a, J, item, s_tab, s_pc, rk); break;
+        case BT_F_ARITH: mc_shared_item<BT_F_ARITH>(a, J, item, s_tab, s_pc, sk, rk); break;
+        case BT_F_GEO: mc_shared_item<BT_F_GEO>(a, J, item, s_tab, s_pc, sk, rk); break;
+        case BT_F_EURO: mc_shared_item<BT_F_EURO>(a, J, item, s_tab, s_pc, sk, rk); break;
+        case BT_F_LOOKMAX: mc_shared_item<BT_F_LOOKMAX>(a, J, item, s_tab, s_pc, sk, rk); break;
+        default: mc_shared_item<BT_F_LOOKMIN>(a, J, item, s_tab, s_pc, sk, rk); break;
         }
     }
 }

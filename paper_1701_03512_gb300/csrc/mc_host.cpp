@@ -25,6 +25,22 @@ static void mc_payoff(int payoff, int *field, int *sign) {
     }
 }
 
+// The largest suffix quantity f a call can draw over L steps (the path that only goes up):
+// arithmetic sum_j u^j, geometric u^(L(L+1)/(2N)), European and lookback u^L; 0 for a put,
+// whose clamp only needs -f <= 0.
+static double suffix_f_bound(int field, int sign, int L, int N, double u) {
+    if (sign < 0 || L == 0) return 0.0;
+    switch (field) {
+    case BT_F_ARITH: {
+        double f = 0.0, r = 1.0;
+        for (int j = 1; j <= L; ++j) f += (r *= u);
+        return f;
+    }
+    case BT_F_GEO: return std::pow(u, (double)L * (double)(L + 1) / (2.0 * (double)N));
+    default: return std::pow(u, (double)L);
+    }
+}
+
 // round(p 2^32) clamped to [1, 2^32 - 1]: the word comparison draws x_t = 1
 // with probability thr / 2^32.
 static uint32_t bernoulli_threshold(double p) {
@@ -72,6 +88,7 @@ static bt_status mc_run(bt_ctx *ctx, const bt_option *opts, int32_t n, int32_t s
         J.df = (float)J.d;
         J.lnu_f = (float)std::log(J.u);
         for (int k = 0; k <= J.mb; ++k) J.prob_k[k] = std::pow(J.p, (double)k) * std::pow(1.0 - J.p, (double)(J.mb - k));
+        J.fbound = suffix_f_bound(J.field, J.sign, J.N - J.mb, J.N, J.u);
         const int64_t chunks = (J.R + BT_MC_ITEM - 1) / BT_MC_ITEM;
         J.shard = shard;
         J.n_shards = n_shards;

@@ -24,6 +24,8 @@ struct bt_mc_job {
     uint32_t thr;                  // up iff the 32-bit word < thr = round(p 2^32)
     int32_t out;                   // result slot
     double u, d, p, S0, K, disc;
+    double fbound;                 // Shared-Sample: an upper bound of the suffix quantity f of a call
+                                   // (sign +1; 0 for a put), sizing the pair loop's power-of-2 scale
     float uf, df, lnu_f;
     int32_t pad;
     int32_t shard, n_shards;       // this run covers strata m = shard + j * n_shards
@@ -42,7 +44,7 @@ struct bt_mc_args {
     double4 *item_stats;           // per item: (count, mean, M2, stratum)
     unsigned long long *counter;
     // Shared-Sample only: per job, the strata table the payoff loop reads (per stratum m,
-    // (sign tau_m, sign tau_m, P(D_m) beta_m / 2, P(D_m) beta_m)) and BT_MC_TAB_BLOCKS partial sums
+    // (sign tau_m, sign tau_m, P(D_m) beta_m, P(D_m) beta_m)) and BT_MC_TAB_BLOCKS partial sums
     // of P(D_m) C_m in FP64
     float4 *shared_tab;            // [n_jobs][BT_MC_TAB_ENTRIES]
     double *shared_pc;             // [n_jobs][BT_MC_TAB_BLOCKS]
