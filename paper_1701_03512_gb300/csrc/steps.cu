@@ -215,9 +215,9 @@ __global__ void k_steps_tables(const bt_job *jobs, const bt_jparams *prm, const 
 
 // FP32 suffix weights by error diffusion (one block per job, FP32 tables):
 // the entries (f_hi, -f_lo, w_hi, w_lo) written by k_steps_tables are sorted
-// by f = f_hi + f_lo (bitonic sort in shared memory on the bit patterns of the
-// FP64 values, which order like the values since every f_s > 0; padding keys
-// after every suffix), then BT_DIFFUSE_LANES lanes of one warp each walk one of
+// by f = f_hi + f_lo (bitonic sort on the bit patterns of the FP64 values, which
+// order like the values since every f_s > 0, with the suffix index in the low 13
+// bits; padding keys after every suffix), then BT_DIFFUSE_LANES lanes of one warp each walk one of
 // the interleaved subsequences r = lane, lane + BT_DIFFUSE_LANES, ... (each in
 // ascending f) carrying the rounding residual: w32 = RN_f32(w + carry),
 // carry = w + carry - w32, with w the FP32 pair (w_hi, w_lo) and the carry kept
@@ -226,6 +226,22 @@ __global__ void k_steps_tables(const bt_job *jobs, const bt_jparams *prm, const 
 // carries, each at most half an FP32 ulp: BT_DIFFUSE_LANES ulps at most over
 // the run. A weight of 0 (a branch of probability 0) stays 0. The entry keeps
 // (f_hi, -f_lo, w32, 0).
+// Compare-exchange of a thread's eight keys at distance J < 8 (element 8t + r against 8t + (r ^ J)),
+// ascending where the element's bit k is clear.
+template <int J>
+__device__ __forceinline__ void sort_in_thread(unsigned long long (&v)[8], int k) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        if ((r ^ J) > r) {
+            const bool asc = ((8 * (int)threadIdx.x + r) & k) == 0;
+            const unsigned long long a = v[r], b = v[r ^ J];
+            const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
+            v[r] = asc ? lo : hi;
+            v[r ^ J] = asc ? hi : lo;
+        }
+    }
+}
+
 #ifndef BT_DIFFUSE_LANES
 #define BT_DIFFUSE_LANES 8
 #endif
@@ -237,37 +253,57 @@ __global__ void __launch_bounds__(1024) k_steps_weights(const bt_job *jobs, floa
     extern __shared__ unsigned long long key[];   // [BT_SORT_N], then idx
     int16_t *idx = reinterpret_cast<int16_t *>(key + BT_SORT_N);
     const int n = (int)J.n_suffix;
-    int np = 1;
-    while (np < n) np <<= 1;
     float4 *tab = suf32 + J.off_suf;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        if (i < n) {
-            const float4 e = tab[i];
-            key[i] = (unsigned long long)__double_as_longlong((double)e.x - (double)e.y);  // f, exact in FP64
+    // Bitonic sort of BT_SORT_N keys, eight per thread in registers (thread t holds elements
+    // 8t..8t+7): compare-exchange partners 8 or more apart but in the same warp come by shuffle,
+    // those 256 or more apart through shared memory, the rest are in the same thread. A key is the
+    // bit pattern of f (which orders like f, every f > 0) with its low 13 bits replaced by the
+    // suffix index (so ties and f within 2^-39 relative of each other order by index); padding
+    // keys are all ones.
+    static_assert(BT_SORT_N == 8 * 1024 && BT_SORT_N <= (1 << 13), "eight keys per thread, 13-bit index");
+    constexpr unsigned long long IDX = (1ull << 13) - 1;
+    unsigned long long v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int e = 8 * threadIdx.x + r;
+        if (e < n) {
+            const float4 t = tab[e];
+            v[r] = ((unsigned long long)__double_as_longlong((double)t.x - (double)t.y) & ~IDX) | (unsigned long long)e;
         } else {
-            key[i] = ~0ull;
+            v[r] = ~0ull;
         }
-        idx[i] = (int16_t)i;
     }
-    __syncthreads();
-    for (int k = 2; k <= np; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < np; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l <= i) continue;
-                const unsigned long long a = key[i], c = key[l];
-                const bool asc = (i & k) == 0;
-                if (asc ? a > c : a < c) {
-                    key[i] = c;
-                    key[l] = a;
-                    const int16_t t = idx[i];
-                    idx[i] = idx[l];
-                    idx[l] = t;
+    for (int k = 2; k <= BT_SORT_N; k <<= 1) {
+        for (int j = k >> 1; j >= 8; j >>= 1) {
+            if (j >= 256) {
+                __syncthreads();   // the previous exchange's reads are done
+#pragma unroll
+                for (int r = 0; r < 8; ++r) key[8 * threadIdx.x + r] = v[r];
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int e = 8 * threadIdx.x + r;
+                    const unsigned long long w = key[e ^ j];
+                    const bool keep_min = ((e & k) == 0) == ((e & j) == 0);
+                    v[r] = keep_min ? (v[r] < w ? v[r] : w) : (v[r] > w ? v[r] : w);
+                }
+            } else if (j >= 8) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int e = 8 * threadIdx.x + r;
+                    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v[r], j >> 3);
+                    const bool keep_min = ((e & k) == 0) == ((e & j) == 0);
+                    v[r] = keep_min ? (v[r] < w ? v[r] : w) : (v[r] > w ? v[r] : w);
                 }
             }
-            __syncthreads();
         }
+        if (k >= 8) sort_in_thread<4>(v, k);   // j < 8: the partner is a register of this thread
+        if (k >= 4) sort_in_thread<2>(v, k);
+        sort_in_thread<1>(v, k);
     }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) idx[8 * threadIdx.x + r] = (int16_t)(v[r] & IDX);
+    __syncthreads();   // every exchange read of key[] is done before it holds the weights
     float2 *wp = reinterpret_cast<float2 *>(key);   // the keys are no longer needed
     for (int r = threadIdx.x; r < n; r += blockDim.x) {   // the weights in ascending f
         const float4 e = tab[idx[r]];
