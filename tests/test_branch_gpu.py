@@ -150,12 +150,13 @@ def test_affine_moves_probability_floor(bt, ctx, oracle):
     assert abs(v32 - v64) <= 1e-9 * abs(v64) + 1e-12 * ob["S0"], (v32, v64)
 
 
-@pytest.mark.parametrize("b,N", [(3, 18), (4, 14)])   # 3.9e8 and 2.7e8 paths
+@pytest.mark.parametrize("b,N", [(3, 18), (4, 14), (6, 11)])   # 3.9e8, 2.7e8, 3.6e8 paths
 def test_affine_moves_fp32_pass_against_the_oracle_at_full_size(bt, ctx, oracle, b, N):
     """From 2^28 paths FP32_COMP runs the FP32 pass: every payoff at two
     strikes on one non-recombining b-ary tree (call and put of one field
     adjacent, sharing a pass) against the oracle's enumeration of all b^N
-    paths, at the 1e-9 contract and within the stated error."""
+    paths, at the 1e-9 contract and within the stated error. The senary
+    tree fills the suffix table nearly to its 2^13 entries (6^5 = 7776)."""
     opts = [W.opt(N, 100.0, K, 0.03, 0.2, 1.0, pay) for K in (95.0, 105.0) for pay in range(8)]
     mv = W.branch_moves(700 + 10 * b, N, b, 0.01, 0.05, 50.0)
     assert not np.any((mv[:, b:] > 0) & (mv[:, b:] < 0.004))   # above the FP32 pass's probability floor
