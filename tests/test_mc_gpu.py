@@ -78,6 +78,20 @@ def test_all_strata_is_exact(bt, ctx, oracle):
         assert got["stderr_mc"][i] == 0.0
 
 
+@pytest.mark.parametrize("sigma", [5.0, 10.0])
+def test_shared_sample_at_extreme_volatility(bt, ctx, oracle, sigma):
+    """The Shared-Sample pair loop scales its table by 2^k with 2^k >= 2 max(sign (tau + f)); at
+    sigma = 5 (a bound of f near 2^55) the scale is 2^57, at sigma = 10 (2^109) the table stays
+    unscaled and the loop clamps with max. Both against the oracle on the same draws."""
+    for pay in (W.ASIAN_ARITH_CALL, W.ASIAN_ARITH_PUT, W.LOOKBACK_FIXED_CALL):
+        o = W.opt(64, 100.0, 100.0, 0.05, sigma, 1.0, pay)
+        got = bt.bt_price_mc_ex(ctx.h, [o], 4, 300, 17, bt.BT_MC_SHARED)[0]
+        th, var = oracle.mc(o, 4, 300, 17, stream=0, shared=True)
+        disc = oracle.discount(o)
+        assert got["value"] == pytest.approx(disc * th, rel=2e-5), (sigma, pay, got["value"], disc * th)
+        assert got["stderr_mc"] == pytest.approx(disc * math.sqrt(var), rel=2e-4)
+
+
 def test_shared_sample_over_all_prefixes_is_exact(bt, ctx, oracle):
     """Shared-Sample with 2^N prefixes: the suffixes are empty, every sample scores the whole tree,
     h_i = sum_x p(x) V(x) for each i (eq. mc16 with L = 0). The FP32 strata table and the blocked
